@@ -1,0 +1,274 @@
+"""FP64 CPU oracle of the M1 radiative-transfer step (test infrastructure).
+
+Thin ctypes/numpy wrapper around ``m1_oracle.c``.  Only the test-suite, the
+smoke check and the CPU-baseline leg of the benchmark import this package;
+the GPU library never does, and this package imports nothing from it.
+
+The physics (Aubert, Deparis & Ocvirk, arXiv:1508.07888, Secs. 2.2.3-2.2.4)
+lives entirely in the C file; this module only marshals arrays.
+
+State layout (all float64, C order):
+    U    [G, nz, ny, nx, 4]  = (N/nunit, Fx/(c nunit), Fy/(c nunit), Fz/(c nunit))
+    xHI  [nz, ny, nx]        neutral fraction 1 - x
+    T    [nz, ny, nx]        K
+    n0   [nz, ny, nx]        total hydrogen density, cm^-3
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+from typing import Sequence
+
+import numpy as np
+
+from . import build as _build
+
+MAXG = 4
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+ERR_NONFINITE, ERR_SUBCYCLE = 1, 4
+NDIAG = 5
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("G", C.c_int),
+        ("sigN", C.c_double * MAXG),
+        ("sigE", C.c_double * MAXG),
+        ("Eavg", C.c_double * MAXG),
+        ("frac", C.c_double * MAXG),
+        ("c", C.c_double),
+        ("cfl", C.c_double),
+        ("ots", C.c_int),
+        ("isothermal", C.c_int),
+        ("nsub", C.c_int),
+        ("rates_const", C.c_int),
+        ("alphaA", C.c_double),
+        ("alphaB", C.c_double),
+        ("beta", C.c_double),
+        ("bc", C.c_int * 6),
+        ("max_halvings", C.c_int),
+    ]
+
+
+@dataclass
+class Params:
+    """Oracle run parameters (mirrors ``orc_params``)."""
+    sigN: Sequence[float]
+    sigE: Sequence[float]
+    Eavg: Sequence[float]          # erg
+    frac: Sequence[float]
+    c: float                       # cm/s, the (reduced) speed of light
+    cfl: float = 0.9
+    ots: bool = False
+    isothermal: bool = False
+    nsub: int = 0
+    rates_const: bool = False
+    alphaA: float = 0.0
+    alphaB: float = 0.0
+    beta: float = 0.0
+    bc: Sequence[int] = field(default_factory=lambda: [BC_PERIODIC] * 6)
+    max_halvings: int = 30
+
+    @property
+    def G(self) -> int:
+        return len(self.sigN)
+
+    def to_c(self) -> _Params:
+        p = _Params()
+        p.G = self.G
+        for i in range(self.G):
+            p.sigN[i] = self.sigN[i]
+            p.sigE[i] = self.sigE[i]
+            p.Eavg[i] = self.Eavg[i]
+            p.frac[i] = self.frac[i]
+        p.c = self.c
+        p.cfl = self.cfl
+        p.ots = int(self.ots)
+        p.isothermal = int(self.isothermal)
+        p.nsub = int(self.nsub)
+        p.rates_const = int(self.rates_const)
+        p.alphaA, p.alphaB, p.beta = self.alphaA, self.alphaB, self.beta
+        for k in range(6):
+            p.bc[k] = int(self.bc[k])
+        p.max_halvings = int(self.max_halvings)
+        return p
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        PP = C.POINTER(_Params)
+        sig = {
+            "orc_timestep": (C.c_double, [PP, C.c_double]),
+            "orc_courant_number": (C.c_double, [PP, C.c_double]),
+            "orc_closure": (C.c_double, [_dp, _dp, _dp, _dp]),
+            "orc_glf_flux": (None, [C.c_int, _dp, _dp, _dp]),
+            "orc_transport": (None, [PP, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp]),
+            "orc_alphaA": (C.c_double, [C.c_double]),
+            "orc_alphaB": (C.c_double, [C.c_double]),
+            "orc_beta": (C.c_double, [C.c_double]),
+            "orc_cool_recA": (C.c_double, [C.c_double]),
+            "orc_cool_recB": (C.c_double, [C.c_double]),
+            "orc_cool_colion": (C.c_double, [C.c_double]),
+            "orc_cool_colexc": (C.c_double, [C.c_double]),
+            "orc_cool_brems": (C.c_double, [C.c_double]),
+            "orc_cooling": (C.c_double, [PP, C.c_double, C.c_double, C.c_double]),
+            "orc_chem_cell": (C.c_int, [PP, C.c_double, C.c_double, C.c_double, _dp, _dp,
+                                        _dp, _dp, C.POINTER(C.c_int)]),
+            "orc_source_field": (None, [PP, C.c_int64, C.c_int, _i64p, _dp, C.c_double,
+                                        C.c_double, _dp]),
+            "orc_run": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                  _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _i64p]),
+            "orc_sigma_HI": (C.c_double, [C.c_double]),
+            "orc_set_threads": (None, [C.c_int]),
+            "orc_get_threads": (C.c_int, []),
+            "orc_group_table": (None, [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp]),
+            "orc_group_table_w": (None, [C.c_int, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags.c_contiguous
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_dp)
+    if a.dtype == np.int64:
+        return a.ctypes.data_as(_i64p)
+    raise TypeError(a.dtype)
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's cell loops (results are bit-identical for any n)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return lib().orc_get_threads()
+
+
+# ---------------------------------------------------------------- pieces
+def timestep(p: Params, dx: float) -> float:
+    return lib().orc_timestep(C.byref(p.to_c()), dx)
+
+
+def courant_number(p: Params, dx: float) -> float:
+    return lib().orc_courant_number(C.byref(p.to_c()), dx)
+
+
+def closure(U4) -> tuple[np.ndarray, float, float, float]:
+    """Returns (P6 = Nhat*D as xx,xy,xz,yy,yz,zz ; chi ; a ; g)."""
+    U = np.ascontiguousarray(U4, dtype=np.float64)
+    P = np.zeros(6)
+    a, g = C.c_double(), C.c_double()
+    chi = lib().orc_closure(_ptr(U), _ptr(P), C.byref(a), C.byref(g))
+    return P, chi, a.value, g.value
+
+
+def glf_flux(d: int, L, R) -> np.ndarray:
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    out = np.zeros(4)
+    lib().orc_glf_flux(d, _ptr(L), _ptr(R), _ptr(out))
+    return out
+
+
+def transport(p: Params, U: np.ndarray, lam: float) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    G, nz, ny, nx, four = U.shape
+    assert four == 4 and G == p.G
+    out = np.empty_like(U)
+    lib().orc_transport(C.byref(p.to_c()), nx, ny, nz, lam, _ptr(U), _ptr(out))
+    return out
+
+
+RATE_NAMES = ("alphaA", "alphaB", "beta", "cool_recA", "cool_recB",
+              "cool_colion", "cool_colexc", "cool_brems")
+
+
+def rate(name: str, T: float) -> float:
+    assert name in RATE_NAMES
+    return getattr(lib(), "orc_" + name)(float(T))
+
+
+def cooling(p: Params, n0: float, xHI: float, T: float) -> float:
+    return lib().orc_cooling(C.byref(p.to_c()), n0, xHI, T)
+
+
+def chem_cell(p: Params, dt: float, nunit: float, n0: float, S, U, xHI: float, T: float):
+    """Thermochemistry of one cell over dt.  Returns (U, xHI, T, ncycles, err)."""
+    Uc = np.ascontiguousarray(np.asarray(U, dtype=np.float64).reshape(p.G * 4)).copy()
+    Sc = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(p.G))
+    x, t = C.c_double(xHI), C.c_double(T)
+    ncyc = C.c_int()
+    err = lib().orc_chem_cell(C.byref(p.to_c()), dt, nunit, n0, _ptr(Sc), _ptr(Uc),
+                              C.byref(x), C.byref(t), C.byref(ncyc))
+    return Uc.reshape(p.G, 4), x.value, t.value, ncyc.value, err
+
+
+def source_field(p: Params, shape, cells, Q, dx: float, nunit: float) -> np.ndarray:
+    nz, ny, nx = shape
+    ncell = nx * ny * nz
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    S = np.zeros((p.G, ncell))
+    lib().orc_source_field(C.byref(p.to_c()), ncell, len(cells), _ptr(cells), _ptr(Q),
+                           dx, nunit, _ptr(S))
+    return S
+
+
+@dataclass
+class RunResult:
+    U: np.ndarray
+    xHI: np.ndarray
+    T: np.ndarray
+    hist: np.ndarray
+    err: int
+    nclamp: int
+
+
+def run(p: Params, U, xHI, T, n0, dx: float, nunit: float, nsteps: int,
+        S: np.ndarray | None = None) -> RunResult:
+    """nsteps full steps (transport, chemistry, diagnostics); inputs are copied."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    xHI = np.array(xHI, dtype=np.float64, order="C", copy=True)
+    T = np.array(T, dtype=np.float64, order="C", copy=True)
+    n0 = np.ascontiguousarray(n0, dtype=np.float64)
+    G, nz, ny, nx, _ = U.shape
+    assert G == p.G and xHI.shape == (nz, ny, nx) == T.shape == n0.shape
+    hist = np.zeros((nsteps, NDIAG))
+    ncl = C.c_int64()
+    Sp = _ptr(np.ascontiguousarray(S, dtype=np.float64)) if S is not None else None
+    if S is not None:
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        assert S.shape == (G, nx * ny * nz)
+        Sp = _ptr(S)
+    err = lib().orc_run(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
+                        _ptr(T), _ptr(n0), Sp, nsteps, _ptr(hist), C.byref(ncl))
+    return RunResult(U, xHI, T, hist, err, ncl.value)
+
+
+def sigma_HI(E_eV: float) -> float:
+    return lib().orc_sigma_HI(float(E_eV))
+
+
+def group_table(edges_eV: Sequence[float], T_bb: float, use_sigma: bool = True):
+    """Group averages over a black-body photon spectrum.
+    Returns dict(sigN, sigE, Eavg [erg], frac), each an array of G floats."""
+    e = np.ascontiguousarray(edges_eV, dtype=np.float64)
+    G = len(e) - 1
+    out = [np.zeros(G) for _ in range(4)]
+    lib().orc_group_table_w(G, _ptr(e), float(T_bb), int(use_sigma),
+                            *[_ptr(o) for o in out])
+    return dict(zip(("sigN", "sigE", "Eavg", "frac"), out))

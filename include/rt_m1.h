@@ -1,0 +1,176 @@
+/*
+ * rt_m1.h -- C ABI of the B300 M1 radiative-transfer library (librt_m1.so).
+ *
+ * One call of rt_step advances every box of a handle by explicit M1
+ * radiative-transfer steps as described by Aubert, Deparis & Ocvirk,
+ * "EMMA: an AMR cosmological simulation code with radiative transfer"
+ * (arXiv:1508.07888):
+ *   1. dt from the radiative Courant condition (Sec. 2.2.3, Sec. 2.3),
+ *      read in 3-D as dt = cfl dx / (3 c);
+ *   2. per photon group: Levermore M1 closure, GLF intercell fluxes and the
+ *      unsplit conservative update (Sec. 2.2.3, Eqs. e:pdert1i, e:pdert2i,
+ *      e:uprt, e:glf) with the boundary ghosts of Sec. 4.2;
+ *   3. per cell: sub-cycled hydrogen thermochemistry -- sources and implicit
+ *      absorption, ionisation and energy updates in the paper's order, with
+ *      the 10% energy rule (Sec. 2.2.4, Eqs. e:therm1-e:therm4, e:therm1g,
+ *      e:therm2g, e:g2, e:g3);
+ *   4. per box: diagnostics (volume-weighted ionised fraction, photon
+ *      total, max |F|/(cN), count of cells with xHI < 0.5 -- the front
+ *      definition of Sec. 6.4 -- and mean chemistry sub-cycles per cell).
+ *
+ * Conventions
+ *   - All functions return RT_OK (0) or a negative rt_status; no C++
+ *     exception crosses this boundary.  rt_last_error() gives a message.
+ *   - Device memory of the state belongs to the caller; the library never
+ *     frees it.  The library allocates only its own scratch (the
+ *     post-transport radiation state, source tables, reduction partials,
+ *     the error word) and frees it in rt_destroy.
+ *   - Work is ordered on the CUDA stream given to rt_create.  rt_step
+ *     returns after the stream has drained (it reads the device error word).
+ *   - Radiation state in the stored variables Nhat = N/nunit and
+ *     Fhat = F/(c_red nunit) (photons/cm^3 scaled by the box's nunit), so
+ *     the flux limit reads |Fhat| <= Nhat.
+ *   - Layouts are C order: U[g][z][y][x][4] = (Nhat, Fhat_x, Fhat_y, Fhat_z),
+ *     scalars [z][y][x]; linear cell index = (z*ny + y)*nx + x.
+ */
+#ifndef RT_M1_H
+#define RT_M1_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RT_API __attribute__((visibility("default")))
+#else
+#define RT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_MAX_GROUPS 4
+#define RT_NDIAG 5          /* ionised fraction, photons, max f, n(xHI<0.5), mean sub-cycles */
+
+typedef enum rt_status {
+    RT_OK = 0,
+    RT_ERR_ARG = -1,            /* invalid argument (message in rt_last_error) */
+    RT_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    RT_ERR_NONFINITE = -3,      /* a cell's xHI or T became NaN/Inf */
+    RT_ERR_REALIZABILITY = -4,  /* |F| > 1.01 cN after transport */
+    RT_ERR_SUBCYCLE = -5,       /* 10% rule needed more than max_halvings halvings,
+                                   or a cell exceeded 1e6 sub-cycles in one step */
+    RT_ERR_TIMEOUT = -6,        /* reserved: a bounded device wait gave up */
+    RT_ERR_STATE = -7           /* call out of order (e.g. on a destroyed handle) */
+} rt_status;
+
+typedef enum rt_precision {
+    RT_PREC_SPLIT = 0,       /* FP32 transport (float U, float n0), FP64 chemistry */
+    RT_PREC_FP64 = 1,        /* FP64 everywhere (double U, double n0) */
+    RT_PREC_FP64_STRICT = 2  /* FP64, no fused multiply-add, the operation order of a
+                                plain IEEE evaluation of the equations (bit-reproducible
+                                against such an evaluation when rates_const is set) */
+} rt_precision;
+
+typedef enum rt_bc {
+    RT_BC_PERIODIC = 0,      /* Sec. 4.2 default */
+    RT_BC_TRANSMISSIVE = 1,  /* ghost = copy of the boundary cell */
+    RT_BC_REFLECTIVE = 2     /* ghost = copy with the normal flux component inverted */
+} rt_bc;
+
+typedef struct rt_params {
+    int    ngroups;                      /* 1..RT_MAX_GROUPS */
+    double sigN[RT_MAX_GROUPS];          /* cm^2, number-weighted group cross-section (Eq. e:siggroup) */
+    double sigE[RT_MAX_GROUPS];          /* cm^2, energy-weighted group cross-section (Sec. 2.2.4) */
+    double Eavg[RT_MAX_GROUPS];          /* erg, mean photon energy of the group */
+    double frac[RT_MAX_GROUPS];          /* share of each source's photons in the group (Eq. e:sgroup) */
+    double c_red;                        /* cm/s, reduced speed of light (Sec. 2.2.3) */
+    double cfl;                          /* Courant factor C in dt = C dx/(3 c_red); (0, 1] */
+    int    ots;                          /* on-the-spot: alpha_A -> alpha_B, no recombination photons */
+    int    isothermal;                   /* T held fixed (one chemistry sub-cycle per step) */
+    int    nsub;                         /* 0: adaptive dtau = min(rest, |e/(H-Lambda)|);
+                                            >0: dt split in nsub equal intervals */
+    int    rates_const;                  /* 1: alpha_A, alpha_B, beta below, no cooling
+                                            (requires isothermal); 0: temperature fits */
+    double alphaA, alphaB, beta;         /* cm^3/s, used when rates_const */
+    int    bc[6];                        /* faces -x,+x,-y,+y,-z,+z, rt_bc values */
+    int    max_halvings;                 /* cap of the 10% rule (e.g. 30) */
+    int    precision;                    /* rt_precision */
+} rt_params;
+
+typedef struct rt_box {
+    int     nx, ny, nz;                  /* cells per axis, each >= 1 */
+    double  dx;                          /* cm, cell size */
+    double  nunit;                       /* photons/cm^3 per stored unit of N (> 0) */
+    void   *U;                           /* device, G*ncell*4 float (SPLIT) or double, read/write */
+    double *xHI;                         /* device, ncell, neutral fraction, read/write */
+    double *T;                           /* device, ncell, K, read/write */
+    const void *n0;                      /* device, ncell, cm^-3, float (SPLIT) or double, read only */
+} rt_box;
+
+typedef struct rt_stats {
+    int64_t steps;                       /* steps run since rt_create */
+    int64_t realizability_clamps;        /* post-transport cells with |F| > cN (1 + tol),
+                                            tol 1e-12 (FP64) or 1e-5 (FP32), summed over steps */
+    int     error_bits;                  /* OR of device error bits seen (1 nonfinite, 2 realizability,
+                                            4 sub-cycle cap) */
+    int     nboxes;
+    int64_t cells;                       /* cells over all boxes */
+    double  last_diag[RT_NDIAG];         /* diagnostics of box 0 after the last step */
+} rt_stats;
+
+typedef struct rt_handle rt_handle;
+
+/* Create a solver over nboxes independent boxes that share p.  Validates
+ * every argument, copies p and the box descriptors, allocates scratch on the
+ * current device and orders all later work on `stream` (a cudaStream_t, NULL =
+ * legacy default stream).  *h is set only on success. */
+RT_API int rt_create(rt_handle **h, const rt_params *p, const rt_box *boxes, int nboxes, void *stream);
+
+/* Point sources of box `box` (Sec. 2.2.4, source term S of Eq. e:therm1g):
+ * nsrc host arrays, cell = linear cell index in [0, ncell), Q = photons/s of
+ * the whole spectrum, split over groups by p->frac.  The per-cell source term
+ * is S_i = (sum_k Q_k frac_i) / (dx^3 nunit), duplicates summed in list order.
+ * Replaces the box's previous sources; nsrc = 0 removes them. */
+RT_API int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *cell, const double *Q);
+
+/* Advance all boxes by nsteps (>= 0) steps, in place.  hist: device pointer to
+ * nsteps*nboxes*RT_NDIAG doubles ([step][box][diag]) or NULL.  Returns the
+ * most severe device error of the call (RT_ERR_SUBCYCLE, RT_ERR_NONFINITE,
+ * RT_ERR_REALIZABILITY) after completing all steps. */
+RT_API int rt_step(rt_handle *h, int nsteps, double *hist);
+
+/* Copy host arrays into the device state of `box` (any argument may be NULL
+ * to skip it; U in the precision's element type; n0 overwrites the caller's
+ * density buffer).  Ordered on the handle's stream; returns after the copy. */
+RT_API int rt_upload(rt_handle *h, int box, const void *U, const double *xHI, const double *T,
+              const void *n0);
+
+/* Copy the device state of `box` into host arrays (NULL skips an array). */
+RT_API int rt_download(rt_handle *h, int box, void *U, double *xHI, double *T);
+
+/* Counters and the last diagnostics; never launches work. */
+RT_API int rt_query(rt_handle *h, rt_stats *st);
+
+/* Message of the last failing call on h (or of the last failing rt_create
+ * when h is NULL).  Never NULL. */
+RT_API const char *rt_last_error(rt_handle *h);
+
+/* Free the scratch and the handle (h may be NULL). */
+RT_API void rt_destroy(rt_handle *h);
+
+/* Host helper: dt of the radiative Courant condition (Sec. 2.2.3, 3-D
+ * reading dt = cfl dx / (3 c_red)); returns a negative value on bad input. */
+RT_API double rt_timestep(const rt_params *p, double dx);
+
+/* Host helper: group averages of the hydrogen photo-ionisation cross-section
+ * over a black-body photon spectrum of temperature T_bb (Eq. e:siggroup and
+ * the sigma_E, <E> definitions of Sec. 2.2.4; Eq. e:sgroup for frac).
+ * edges_eV: ngroups+1 increasing energies (eV, first >= 13.6).  Outputs
+ * ngroups values each: sigN, sigE (cm^2), Eavg (erg), frac (sums to 1). */
+RT_API int rt_group_table(int ngroups, const double *edges_eV, double T_bb,
+                   double *sigN, double *sigE, double *Eavg, double *frac);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_M1_H */

@@ -1,0 +1,37 @@
+// launch.h -- host-side launchers of the kernels in rt_kernels.cuh
+// (internal to librt_m1).  "fast" launchers live in k_fast.cu (default
+// contraction), "strict" ones in k_strict.cu (compiled with --fmad=false).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "rt_device.h"
+
+namespace rtl {
+
+// element types of a precision form: 0 = SPLIT (float U, float n0),
+// 1 = FP64 (double U, double n0)
+struct Launch {
+    const rtd::BoxDev *boxes;
+    int nboxes;
+    int64_t nitems;
+    int grid;
+    cudaStream_t stream;
+};
+
+cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl);
+cudaError_t transport_strict(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl);
+cudaError_t chem_fast(bool fp64, int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
+                      double *partials);
+cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
+                        double *partials);
+cudaError_t finalize(const rtd::BoxDev *boxes, int nboxes, const double *partials, rtd::Ctl *ctl,
+                     double *lastdiag, cudaStream_t stream);
+
+// resident blocks per SM of each kernel (for persistent grid sizing)
+int transport_occupancy(bool fp64, bool strict);
+int chem_occupancy(bool fp64, bool strict, int G);
+
+}  // namespace rtl

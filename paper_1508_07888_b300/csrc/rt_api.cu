@@ -1,0 +1,466 @@
+// rt_api.cu -- host side of the C ABI declared in include/rt_m1.h.
+//
+// Every call validates its arguments, returns an rt_status and never lets a
+// C++ exception out.  All device work is ordered on a private non-blocking
+// stream that is joined to the caller's stream with events at the start and
+// end of each call, so the caller may pass the legacy default stream.  The
+// per-step kernel sequence (transport, chemistry, diagnostics) is captured
+// once into a CUDA graph of RT_GRAPH_STEPS steps and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rt_m1.h"
+#include "launch.h"
+#include "rt_device.h"
+
+#define RT_GRAPH_STEPS 16
+
+struct rt_handle {
+    rt_params p;
+    rtd::Phys ph;
+    int nboxes = 0;
+    bool fp64 = false, strict = false;
+    size_t esize = 4;                        // bytes of one state scalar
+    std::vector<rt_box> box;
+    std::vector<rtd::BoxDev> bdev;           // host mirror
+    rtd::BoxDev *d_boxes = nullptr;
+    std::vector<void *> d_us;                // post-transport scratch per box
+    std::vector<int64_t *> d_src_cell;
+    std::vector<double *> d_src_S;
+    double *d_partials = nullptr;
+    double *d_lastdiag = nullptr;
+    rtd::Ctl *d_ctl = nullptr;
+    rtd::Ctl *h_ctl = nullptr;               // pinned mirror
+    double *h_lastdiag = nullptr;            // pinned
+    int64_t ntitems = 0, ncitems = 0;
+    int zc = 32;
+    int tgrid = 1, cgrid = 1;
+    cudaStream_t user = nullptr, s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int64_t steps_done = 0;
+    unsigned long long nclamp = 0;
+    int error_bits = 0;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(rt_handle *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_err = buf;
+    return code;
+}
+
+#define CU(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), RT_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+static void release(rt_handle *h)
+{
+    if (!h) return;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (void *p : h->d_us) cudaFree(p);
+    for (auto *p : h->d_src_cell) cudaFree(p);
+    for (auto *p : h->d_src_S) cudaFree(p);
+    cudaFree(h->d_boxes);
+    cudaFree(h->d_partials);
+    cudaFree(h->d_lastdiag);
+    cudaFree(h->d_ctl);
+    cudaFreeHost(h->h_ctl);
+    cudaFreeHost(h->h_lastdiag);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->s) cudaStreamDestroy(h->s);
+    delete h;
+}
+
+static int check_params(const rt_params *p)
+{
+    if (!p) return fail(nullptr, RT_ERR_ARG, "params is NULL");
+    if (p->ngroups < 1 || p->ngroups > RT_MAX_GROUPS)
+        return fail(nullptr, RT_ERR_ARG, "ngroups=%d outside [1,%d]", p->ngroups, RT_MAX_GROUPS);
+    for (int i = 0; i < p->ngroups; i++) {
+        if (!(p->sigN[i] >= 0) || !(p->sigE[i] >= 0) || !(p->Eavg[i] >= 0) || !(p->frac[i] >= 0) ||
+            !std::isfinite(p->sigN[i]) || !std::isfinite(p->sigE[i]) ||
+            !std::isfinite(p->Eavg[i]) || !std::isfinite(p->frac[i]))
+            return fail(nullptr, RT_ERR_ARG, "group %d table entries must be finite and >= 0", i);
+    }
+    if (!(p->c_red > 0) || !std::isfinite(p->c_red))
+        return fail(nullptr, RT_ERR_ARG, "c_red must be > 0");
+    if (!(p->cfl > 0 && p->cfl <= 1))
+        return fail(nullptr, RT_ERR_ARG, "cfl=%g outside (0, 1]", p->cfl);
+    if (p->nsub < 0) return fail(nullptr, RT_ERR_ARG, "nsub must be >= 0");
+    if (p->max_halvings < 0 || p->max_halvings > 60)
+        return fail(nullptr, RT_ERR_ARG, "max_halvings outside [0, 60]");
+    if (p->precision < RT_PREC_SPLIT || p->precision > RT_PREC_FP64_STRICT)
+        return fail(nullptr, RT_ERR_ARG, "unknown precision %d", p->precision);
+    for (int f = 0; f < 6; f++)
+        if (p->bc[f] < RT_BC_PERIODIC || p->bc[f] > RT_BC_REFLECTIVE)
+            return fail(nullptr, RT_ERR_ARG, "bc[%d]=%d unknown", f, p->bc[f]);
+    for (int d = 0; d < 3; d++)
+        if ((p->bc[2 * d] == RT_BC_PERIODIC) != (p->bc[2 * d + 1] == RT_BC_PERIODIC))
+            return fail(nullptr, RT_ERR_ARG, "axis %d: periodic on one face only", d);
+    if (p->rates_const && !p->isothermal)
+        return fail(nullptr, RT_ERR_ARG, "rates_const requires isothermal (no cooling fits)");
+    if (p->rates_const && (!(p->alphaA >= 0) || !(p->alphaB >= 0) || !(p->beta >= 0)))
+        return fail(nullptr, RT_ERR_ARG, "constant rates must be >= 0");
+    return RT_OK;
+}
+
+extern "C" double rt_timestep(const rt_params *p, double dx)
+{
+    if (!p || !(p->c_red > 0) || !(p->cfl > 0) || !(dx > 0)) return -1.0;
+    // radiative Courant condition c <= dx/dt (Sec. 2.2.3) for the unsplit
+    // 3-D update: dt = C dx / (3 c)
+    return p->cfl * dx / (3.0 * p->c_red);
+}
+
+extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *boxes, int nboxes,
+                         void *stream)
+{
+    try {
+        if (!hout) return fail(nullptr, RT_ERR_ARG, "handle pointer is NULL");
+        int rc = check_params(p);
+        if (rc) return rc;
+        if (nboxes < 1 || !boxes) return fail(nullptr, RT_ERR_ARG, "need at least one box");
+        const bool fp64 = p->precision != RT_PREC_SPLIT;
+        const size_t es = fp64 ? 8 : 4;
+        for (int b = 0; b < nboxes; b++) {
+            const rt_box &B = boxes[b];
+            if (B.nx < 1 || B.ny < 1 || B.nz < 1)
+                return fail(nullptr, RT_ERR_ARG, "box %d: sizes must be >= 1", b);
+            if ((int64_t)B.nx * B.ny * B.nz > ((int64_t)1 << 40))
+                return fail(nullptr, RT_ERR_ARG, "box %d too large", b);
+            if (!(B.dx > 0) || !std::isfinite(B.dx) || !(B.nunit > 0) || !std::isfinite(B.nunit))
+                return fail(nullptr, RT_ERR_ARG, "box %d: dx and nunit must be > 0", b);
+            if (!B.U || !B.xHI || !B.T || !B.n0)
+                return fail(nullptr, RT_ERR_ARG, "box %d: NULL state pointer", b);
+            if (((uintptr_t)B.U % 16) || ((uintptr_t)B.xHI % 8) || ((uintptr_t)B.T % 8) ||
+                ((uintptr_t)B.n0 % es))
+                return fail(nullptr, RT_ERR_ARG, "box %d: misaligned state pointer", b);
+            for (const void *q : {(const void *)B.U, (const void *)B.xHI, (const void *)B.T, B.n0}) {
+                cudaPointerAttributes a;
+                if (cudaPointerGetAttributes(&a, q) != cudaSuccess ||
+                    (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+                    cudaGetLastError();
+                    return fail(nullptr, RT_ERR_ARG, "box %d: state pointer is not device memory", b);
+                }
+            }
+        }
+        rt_handle *h = new (std::nothrow) rt_handle;
+        if (!h) return fail(nullptr, RT_ERR_ARG, "out of host memory");
+        h->p = *p;
+        h->nboxes = nboxes;
+        h->fp64 = fp64;
+        h->strict = p->precision == RT_PREC_FP64_STRICT;
+        h->esize = es;
+        h->box.assign(boxes, boxes + nboxes);
+        h->user = (cudaStream_t)stream;
+        auto bail = [&](int code) { g_create_err = h->err; release(h); return code; };
+
+        rtd::Phys &ph = h->ph;
+        std::memset(&ph, 0, sizeof ph);
+        ph.G = p->ngroups;
+        ph.ots = p->ots;
+        ph.isothermal = p->isothermal;
+        ph.nsub = p->nsub;
+        ph.rates_const = p->rates_const;
+        ph.max_halvings = p->max_halvings;
+        ph.c = p->c_red;
+        for (int i = 0; i < p->ngroups; i++) {
+            ph.csig[i] = p->c_red * p->sigN[i];
+            ph.SigE[i] = p->sigE[i] * p->Eavg[i] - p->sigN[i] * (13.6 * rtd::EV);
+        }
+        ph.alphaA = p->alphaA;
+        ph.alphaB = p->alphaB;
+        ph.beta = p->beta;
+        const double fit_scale[5] = {0.522, 2.740, 0.354, 0.541, 2.250};
+        for (int k = 0; k < 5; k++) ph.lnfit[k] = std::log(fit_scale[k]);
+        ph.ln2THI = std::log(2.0 * rtd::T_HI);
+        for (int f = 0; f < 6; f++) ph.bc[f] = p->bc[f];
+
+        if ((rc = [&]() -> int {
+                CU(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+                CU(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+                CU(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+                const int G = p->ngroups;
+                int64_t titem = 0, citem = 0;
+                h->bdev.resize(nboxes);
+                h->d_us.assign(nboxes, nullptr);
+                h->d_src_cell.assign(nboxes, nullptr);
+                h->d_src_S.assign(nboxes, nullptr);
+                for (int b = 0; b < nboxes; b++) {
+                    const rt_box &B = boxes[b];
+                    rtd::BoxDev &D = h->bdev[b];
+                    std::memset(&D, 0, sizeof D);
+                    D.nx = B.nx; D.ny = B.ny; D.nz = B.nz;
+                    D.ncell = (int64_t)B.nx * B.ny * B.nz;
+                    D.tiles_x = (B.nx + RTD_TX - 1) / RTD_TX;
+                    D.tiles_y = (B.ny + RTD_TY - 1) / RTD_TY;
+                    D.zchunks = (B.nz + h->zc - 1) / h->zc;
+                    D.dx = B.dx;
+                    D.nunit = B.nunit;
+                    D.dt = p->cfl * B.dx / (3.0 * p->c_red);
+                    D.lam = p->c_red * D.dt / B.dx;
+                    D.U = B.U;
+                    D.xHI = B.xHI;
+                    D.T = B.T;
+                    D.n0 = B.n0;
+                    CU(h, cudaMalloc(&h->d_us[b], (size_t)G * D.ncell * 4 * es));
+                    D.Us = h->d_us[b];
+                    D.titem0 = titem;
+                    D.ntitems = (int64_t)G * D.tiles_x * D.tiles_y * D.zchunks;
+                    titem += D.ntitems;
+                    D.citem0 = citem;
+                    D.ncitems = (D.ncell + RTD_CHEM_BLOCK - 1) / RTD_CHEM_BLOCK;
+                    citem += D.ncitems;
+                }
+                h->ntitems = titem;
+                h->ncitems = citem;
+                CU(h, cudaMalloc(&h->d_boxes, sizeof(rtd::BoxDev) * nboxes));
+                CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * nboxes,
+                                 cudaMemcpyHostToDevice));
+                CU(h, cudaMalloc(&h->d_partials, sizeof(double) * RTD_NDIAG * citem));
+                CU(h, cudaMalloc(&h->d_lastdiag, sizeof(double) * RTD_NDIAG * nboxes));
+                CU(h, cudaMemset(h->d_lastdiag, 0, sizeof(double) * RTD_NDIAG * nboxes));
+                CU(h, cudaMalloc(&h->d_ctl, sizeof(rtd::Ctl)));
+                CU(h, cudaMallocHost(&h->h_ctl, sizeof(rtd::Ctl)));
+                CU(h, cudaMallocHost(&h->h_lastdiag, sizeof(double) * RTD_NDIAG * nboxes));
+                std::memset(h->h_lastdiag, 0, sizeof(double) * RTD_NDIAG * nboxes);
+                int dev = 0, nsm = 1;
+                CU(h, cudaGetDevice(&dev));
+                CU(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+                const int to = rtl::transport_occupancy(fp64, h->strict);
+                const int co = rtl::chem_occupancy(fp64, h->strict, G);
+                h->tgrid = (int)std::min<int64_t>(titem, (int64_t)to * nsm);
+                h->cgrid = (int)std::min<int64_t>(citem, (int64_t)co * nsm);
+                return RT_OK;
+            }()))
+            return bail(rc);
+        *hout = h;
+        return RT_OK;
+    } catch (...) {
+        return fail(nullptr, RT_ERR_ARG, "unexpected host exception in rt_create");
+    }
+}
+
+extern "C" int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *cell, const double *Q)
+{
+    if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
+    try {
+        if (box < 0 || box >= h->nboxes) return fail(h, RT_ERR_ARG, "box %d out of range", box);
+        if (nsrc < 0 || (nsrc > 0 && (!cell || !Q))) return fail(h, RT_ERR_ARG, "bad source arrays");
+        rtd::BoxDev &D = h->bdev[box];
+        const int G = h->p.ngroups;
+        for (int k = 0; k < nsrc; k++) {
+            if (cell[k] < 0 || cell[k] >= D.ncell)
+                return fail(h, RT_ERR_ARG, "source %d: cell %lld outside [0, %lld)", k,
+                            (long long)cell[k], (long long)D.ncell);
+            if (!(Q[k] >= 0) || !std::isfinite(Q[k]))
+                return fail(h, RT_ERR_ARG, "source %d: luminosity must be finite and >= 0", k);
+        }
+        // merge duplicates in list order: S_i = (sum_k Q_k frac_i) / (dx^3 nunit)
+        std::vector<int> order(nsrc);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return cell[a] < cell[b]; });
+        std::vector<int64_t> ucell;
+        std::vector<double> sums;
+        for (int j = 0; j < nsrc; j++) {
+            const int k = order[j];
+            if (ucell.empty() || ucell.back() != cell[k]) {
+                ucell.push_back(cell[k]);
+                sums.insert(sums.end(), G, 0.0);
+            }
+            double *s = &sums[(ucell.size() - 1) * G];
+            for (int i = 0; i < G; i++) s[i] += Q[k] * h->p.frac[i];
+        }
+        const double vol = D.dx * D.dx * D.dx;
+        for (double &v : sums) v = v / (vol * D.nunit);
+        CU(h, cudaStreamSynchronize(h->s));
+        cudaFree(h->d_src_cell[box]);
+        cudaFree(h->d_src_S[box]);
+        h->d_src_cell[box] = nullptr;
+        h->d_src_S[box] = nullptr;
+        const int nu = (int)ucell.size();
+        if (nu > 0) {
+            CU(h, cudaMalloc(&h->d_src_cell[box], sizeof(int64_t) * nu));
+            CU(h, cudaMalloc(&h->d_src_S[box], sizeof(double) * nu * G));
+            CU(h, cudaMemcpy(h->d_src_cell[box], ucell.data(), sizeof(int64_t) * nu,
+                             cudaMemcpyHostToDevice));
+            CU(h, cudaMemcpy(h->d_src_S[box], sums.data(), sizeof(double) * nu * G,
+                             cudaMemcpyHostToDevice));
+        }
+        D.src_cell = h->d_src_cell[box];
+        D.src_S = h->d_src_S[box];
+        D.nsrc = nu;
+        CU(h, cudaMemcpy(h->d_boxes + box, &D, sizeof D, cudaMemcpyHostToDevice));
+        return RT_OK;
+    } catch (...) {
+        return fail(h, RT_ERR_ARG, "unexpected host exception in rt_set_sources");
+    }
+}
+
+// one step of the hot path on stream s: transport, chemistry, diagnostics
+static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s)
+{
+    rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s};
+    rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
+    cudaError_t e;
+    if (h->strict) {
+        e = rtl::transport_strict(Lt, h->zc, h->ph, h->d_ctl);
+        if (e != cudaSuccess) return e;
+        e = rtl::chem_strict(h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials);
+    } else {
+        e = rtl::transport_fast(h->fp64, Lt, h->zc, h->ph, h->d_ctl);
+        if (e != cudaSuccess) return e;
+        e = rtl::chem_fast(h->fp64, h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials);
+    }
+    if (e != cudaSuccess) return e;
+    return rtl::finalize(h->d_boxes, h->nboxes, h->d_partials, h->d_ctl, h->d_lastdiag, s);
+}
+
+static int build_graph(rt_handle *h)
+{
+    cudaGraph_t g = nullptr;
+    CU(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < RT_GRAPH_STEPS && e == cudaSuccess; k++) e = enqueue_step(h, h->s);
+    cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(h, RT_ERR_CUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, RT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    return RT_OK;
+}
+
+extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
+{
+    if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
+    if (nsteps < 0) return fail(h, RT_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return RT_OK;
+    if (hist) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, hist) != cudaSuccess ||
+            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(h, RT_ERR_ARG, "hist must be device memory or NULL");
+        }
+    }
+    rtd::Ctl *c = h->h_ctl;
+    c->hist = hist;
+    c->step = -1;
+    c->nboxes = h->nboxes;
+    c->err = 0;
+    c->nclamp = 0;
+    CU(h, cudaEventRecord(h->ev_in, h->user));
+    CU(h, cudaStreamWaitEvent(h->s, h->ev_in, 0));
+    CU(h, cudaMemcpyAsync(h->d_ctl, c, sizeof(rtd::Ctl), cudaMemcpyHostToDevice, h->s));
+    if (!h->graph && nsteps >= RT_GRAPH_STEPS) {
+        int rc = build_graph(h);
+        if (rc) return rc;
+    }
+    int done = 0;
+    if (h->graph)
+        for (; done + RT_GRAPH_STEPS <= nsteps; done += RT_GRAPH_STEPS)
+            CU(h, cudaGraphLaunch(h->graph, h->s));
+    for (; done < nsteps; done++) CU(h, enqueue_step(h, h->s));
+    CU(h, cudaMemcpyAsync(c, h->d_ctl, sizeof(rtd::Ctl), cudaMemcpyDeviceToHost, h->s));
+    CU(h, cudaMemcpyAsync(h->h_lastdiag, h->d_lastdiag, sizeof(double) * RTD_NDIAG * h->nboxes,
+                          cudaMemcpyDeviceToHost, h->s));
+    CU(h, cudaEventRecord(h->ev_out, h->s));
+    CU(h, cudaStreamWaitEvent(h->user, h->ev_out, 0));
+    CU(h, cudaStreamSynchronize(h->s));
+    h->steps_done += nsteps;
+    h->nclamp += c->nclamp;
+    h->error_bits |= (int)c->err;
+    if (c->err & RTD_ERR_SUBCYCLE)
+        return fail(h, RT_ERR_SUBCYCLE, "chemistry sub-cycle cap reached (10%% rule)");
+    if (c->err & RTD_ERR_NONFINITE) return fail(h, RT_ERR_NONFINITE, "non-finite xHI or T");
+    if (c->err & RTD_ERR_REALIZ) return fail(h, RT_ERR_REALIZABILITY, "|F| > 1.01 cN after transport");
+    return RT_OK;
+}
+
+static int copy_state(rt_handle *h, int box, bool up, void *U, double *xHI, double *T, void *n0)
+{
+    if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
+    if (box < 0 || box >= h->nboxes) return fail(h, RT_ERR_ARG, "box %d out of range", box);
+    const rtd::BoxDev &D = h->bdev[box];
+    const size_t nU = (size_t)h->p.ngroups * D.ncell * 4 * h->esize;
+    const size_t nS = (size_t)D.ncell * sizeof(double);
+    const cudaMemcpyKind k = up ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    CU(h, cudaEventRecord(h->ev_in, h->user));
+    CU(h, cudaStreamWaitEvent(h->s, h->ev_in, 0));
+    if (U) CU(h, up ? cudaMemcpyAsync(D.U, U, nU, k, h->s) : cudaMemcpyAsync(U, D.U, nU, k, h->s));
+    if (xHI) CU(h, up ? cudaMemcpyAsync(D.xHI, xHI, nS, k, h->s) : cudaMemcpyAsync(xHI, D.xHI, nS, k, h->s));
+    if (T) CU(h, up ? cudaMemcpyAsync(D.T, T, nS, k, h->s) : cudaMemcpyAsync(T, D.T, nS, k, h->s));
+    if (n0 && up)
+        CU(h, cudaMemcpyAsync(const_cast<void *>(D.n0), n0, (size_t)D.ncell * h->esize, k, h->s));
+    CU(h, cudaEventRecord(h->ev_out, h->s));
+    CU(h, cudaStreamWaitEvent(h->user, h->ev_out, 0));
+    CU(h, cudaStreamSynchronize(h->s));
+    return RT_OK;
+}
+
+extern "C" int rt_upload(rt_handle *h, int box, const void *U, const double *xHI, const double *T,
+                         const void *n0)
+{
+    return copy_state(h, box, true, const_cast<void *>(U), const_cast<double *>(xHI),
+                      const_cast<double *>(T), const_cast<void *>(n0));
+}
+
+extern "C" int rt_download(rt_handle *h, int box, void *U, double *xHI, double *T)
+{
+    return copy_state(h, box, false, U, xHI, T, nullptr);
+}
+
+extern "C" int rt_query(rt_handle *h, rt_stats *st)
+{
+    if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
+    if (!st) return fail(h, RT_ERR_ARG, "stats pointer is NULL");
+    std::memset(st, 0, sizeof *st);
+    st->steps = h->steps_done;
+    st->realizability_clamps = (int64_t)h->nclamp;
+    st->error_bits = h->error_bits;
+    st->nboxes = h->nboxes;
+    for (const auto &D : h->bdev) st->cells += D.ncell;
+    for (int k = 0; k < RT_NDIAG; k++) st->last_diag[k] = h->h_lastdiag[k];
+    return RT_OK;
+}
+
+extern "C" const char *rt_last_error(rt_handle *h)
+{
+    return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" void rt_destroy(rt_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->s);
+    release(h);
+}

@@ -1,0 +1,71 @@
+// rt_device.h -- descriptors shared by the host side of librt_m1 and its
+// kernels (internal; the public ABI is include/rt_m1.h).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#define RTD_MAXG 4
+#define RTD_NDIAG 5
+
+// transport tile: TX x TY threads, one (x, y) column each, marching in z
+#define RTD_TX 32
+#define RTD_TY 8
+// chemistry: cells per block (one thread per cell)
+#define RTD_CHEM_BLOCK 256
+
+// device error bits (OR-ed into Ctl::err)
+#define RTD_ERR_NONFINITE 1u
+#define RTD_ERR_REALIZ 2u
+#define RTD_ERR_SUBCYCLE 4u
+
+#define RTD_MAXCYC 1000000   // sub-cycles per cell and step before giving up
+
+namespace rtd {
+
+// physical constants (cgs)
+constexpr double KB = 1.380649e-16;         // erg/K
+constexpr double EV = 1.602176634e-12;      // erg
+constexpr double T_HI = 157807.0;           // K, temperature scale of the rate fits
+
+// Parameters shared by every box (kernel argument, by value).
+struct Phys {
+    int G;
+    int ots, isothermal, nsub, rates_const, max_halvings;
+    double c;                     // reduced speed of light, cm/s
+    double csig[RTD_MAXG];        // c * sigma_N,i
+    double SigE[RTD_MAXG];        // Sigma_E,i = sigma_E,i <E>_i - sigma_N,i E_13.6 (Sec. 2.2.4)
+    double alphaA, alphaB, beta;  // rates_const values
+    double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250
+    double ln2THI;                // ln(2 T_HI)
+    int bc[6];                    // -x,+x,-y,+y,-z,+z
+};
+
+// One box (array in device memory, indexed by work items).
+struct BoxDev {
+    int nx, ny, nz;
+    int tiles_x, tiles_y, zchunks;   // transport tiling
+    int64_t ncell;
+    double dx, nunit, dt, lam;        // lam = c dt / dx (Courant number)
+    void *U;                          // caller's state, [G][nz][ny][nx][4]
+    void *Us;                         // post-transport state (library scratch)
+    double *xHI, *T;
+    const void *n0;
+    const int64_t *src_cell;          // sorted unique source cells (nsrc)
+    const double *src_S;              // [nsrc][G] source term, stored units per second
+    int nsrc;
+    int64_t titem0, ntitems;          // transport work items of this box
+    int64_t citem0, ncitems;          // chemistry work items of this box
+};
+
+// Per-call control block in device memory.
+struct Ctl {
+    double *hist;                     // caller's [step][box][RTD_NDIAG] or nullptr
+    int step;                         // step index within the current rt_step call
+    int nboxes;
+    unsigned int err;                 // RTD_ERR_* bits
+    unsigned long long nclamp;        // post-transport flux-limit clamps
+};
+
+}  // namespace rtd

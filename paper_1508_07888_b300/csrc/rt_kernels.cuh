@@ -1,0 +1,621 @@
+// rt_kernels.cuh -- the hot path of one M1 radiative-transfer step
+// (Aubert, Deparis & Ocvirk, arXiv:1508.07888, Secs. 2.2.3 and 2.2.4).
+//
+// This header is compiled twice:
+//   k_fast.cu    default flags: fused multiply-add, reciprocal-multiply in
+//                place of some divisions (FP32 transport + FP64 chemistry,
+//                and the all-FP64 form);
+//   k_strict.cu  --fmad=false: every operation is one IEEE-rounded +, -, *,
+//                /, sqrt in the order written, which makes the FP64 path
+//                bit-reproducible against a plain IEEE evaluation of the same
+//                expressions (with constant rates; the rate fits call exp/log).
+// The STRICT template flag selects the division forms; the compiler flag
+// removes the contractions.
+#pragma once
+
+#include <cstdint>
+
+#include "rt_device.h"
+
+namespace rtk {
+
+using rtd::BoxDev;
+using rtd::Ctl;
+using rtd::Phys;
+
+// ------------------------------------------------------------- vector I/O
+template <typename R>
+struct V4 {
+    R x, y, z, w;
+};
+
+__device__ __forceinline__ V4<float> ld4(const V4<float> *p)
+{
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ void st4(V4<float> *p, const V4<float> &v)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v.x, v.y, v.z, v.w);
+}
+__device__ __forceinline__ V4<double> ld4(const V4<double> *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = q[0], b = q[1];
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st4(V4<double> *p, const V4<double> &v)
+{
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = make_double2(v.x, v.y);
+    q[1] = make_double2(v.z, v.w);
+}
+
+__device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
+__device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
+
+// ------------------------------------------------------------- M1 closure
+// Levermore closure, P = Nhat D with D = (1-chi)/2 I + (3chi-1)/2 n n
+// (Sec. 2.2.3; the printed coefficients are swapped, the diffusive limit
+// fixes the order), chi = (3+4f^2)/(5+2 sqrt(4-3f^2)), f = |Fhat|/Nhat
+// clamped to 1, evaluated as (3chi-1)/2 = f^2 g, g = (6 + 3/(2+s))/(5+2s),
+// s = sqrt(4-3f^2).  P = (xx, xy, xz, yy, yz, zz).
+template <typename R, bool STRICT>
+__device__ __forceinline__ void closure(const V4<R> &u, R P[6])
+{
+    const R N = u.x;
+    if (N > R(0)) {
+        R ux, uy, uz;
+        if (STRICT) {
+            ux = u.y / N; uy = u.z / N; uz = u.w / N;
+        } else {
+            const R rN = R(1) / N;
+            ux = u.y * rN; uy = u.z * rN; uz = u.w * rN;
+        }
+        R f2 = ux * ux + uy * uy + uz * uz;
+        if (f2 > R(1)) {                       // rounding guard of |F| <= cN
+            const R f = rsqrt_(f2);
+            if (STRICT) {
+                ux = ux / f; uy = uy / f; uz = uz / f;
+            } else {
+                const R rf = R(1) / f;
+                ux *= rf; uy *= rf; uz *= rf;
+            }
+            f2 = R(1);
+        }
+        const R s = rsqrt_(R(4) - R(3) * f2);
+        R a, g;
+        if (STRICT) {
+            a = ((R(1) + s) - R(2) * f2) / (R(5) + R(2) * s);
+            g = (R(6) + R(3) / (R(2) + s)) / (R(5) + R(2) * s);
+        } else {
+            const R r5 = R(1) / (R(5) + R(2) * s);
+            a = ((R(1) + s) - R(2) * f2) * r5;
+            g = (R(6) + R(3) / (R(2) + s)) * r5;
+        }
+        P[0] = N * (a + g * (ux * ux));
+        P[1] = N * (g * (ux * uy));
+        P[2] = N * (g * (ux * uz));
+        P[3] = N * (a + g * (uy * uy));
+        P[4] = N * (g * (uy * uz));
+        P[5] = N * (a + g * (uz * uz));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; k++) P[k] = R(0);
+    }
+}
+
+__device__ __forceinline__ constexpr int pidx(int d, int j)
+{
+    return d == 0 ? j : (d == 1 ? (j == 0 ? 1 : (j == 1 ? 3 : 4)) : (j == 0 ? 2 : (j == 1 ? 4 : 5)));
+}
+
+template <typename R>
+__device__ __forceinline__ R comp(const V4<R> &u, int m)
+{
+    return m == 0 ? u.x : (m == 1 ? u.y : (m == 2 ? u.z : u.w));
+}
+
+// GLF flux (Eq. e:glf) along axis d between left (uL, PL) and right (uR, PR):
+// Phi = 0.5 ((G_d(L) + G_d(R)) - (R - L)), G_d = (Fhat_d, P_d.)
+template <typename R, int d>
+__device__ __forceinline__ void glf(const V4<R> &uL, const R PL[6], const V4<R> &uR,
+                                    const R PR[6], R Phi[4])
+{
+    const R GL0 = comp(uL, 1 + d), GR0 = comp(uR, 1 + d);
+    Phi[0] = R(0.5) * ((GL0 + GR0) - (uR.x - uL.x));
+    Phi[1] = R(0.5) * ((PL[pidx(d, 0)] + PR[pidx(d, 0)]) - (uR.y - uL.y));
+    Phi[2] = R(0.5) * ((PL[pidx(d, 1)] + PR[pidx(d, 1)]) - (uR.z - uL.z));
+    Phi[3] = R(0.5) * ((PL[pidx(d, 2)] + PR[pidx(d, 2)]) - (uR.w - uL.w));
+}
+
+// ghost state beyond a box face (Sec. 4.2): transmissive copies the cell,
+// reflective copies it with the normal flux component inverted
+template <typename R>
+__device__ __forceinline__ V4<R> ghost_of(const V4<R> &own, int bc, int d)
+{
+    V4<R> g = own;
+    if (bc == 2) {
+        if (d == 0) g.y = -g.y;
+        else if (d == 1) g.z = -g.z;
+        else g.w = -g.w;
+    }
+    return g;
+}
+
+__device__ __forceinline__ int find_box(const BoxDev *boxes, int nboxes, int64_t item, bool chem)
+{
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int64_t s = chem ? boxes[mid].citem0 : boxes[mid].titem0;
+        if (s <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------- transport
+// One work item = (box, group, z-chunk, y-tile, x-tile).  A block of
+// TX x TY threads owns TX x TY columns and marches through the z-chunk:
+// the plane z (with its x/y halo) is staged in shared memory, each cell's
+// closure is evaluated once per plane, the z-face flux is carried in
+// registers from one plane to the next (each z-face evaluated once).
+// Update (Eq. e:uprt, unsplit): U* = U - lam ((dPhi_x + dPhi_y) + dPhi_z).
+template <typename R, bool STRICT>
+__global__ void __launch_bounds__(RTD_TX *RTD_TY)
+k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, int zc, Phys ph,
+            Ctl *ctl)
+{
+    constexpr int TX = RTD_TX, TY = RTD_TY;
+    __shared__ V4<R> sU[TY + 2][TX + 2];
+    __shared__ R sP[6][TY + 2][TX + 2];
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (blockIdx.x == 0 && tx == 0 && ty == 0) ctl->step += 1;
+
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int b = find_box(boxes, nboxes, it, false);
+        const BoxDev &B = boxes[b];
+        int64_t loc = it - B.titem0;
+        const int ix = (int)(loc % B.tiles_x); loc /= B.tiles_x;
+        const int iy = (int)(loc % B.tiles_y); loc /= B.tiles_y;
+        const int iz = (int)(loc % B.zchunks);
+        const int g = (int)(loc / B.zchunks);
+        const int nx = B.nx, ny = B.ny, nz = B.nz;
+        const int x = ix * TX + tx, y = iy * TY + ty;
+        const bool act = (x < nx) && (y < ny);
+        const int z0 = iz * zc, z1 = min(z0 + zc, nz);
+        const V4<R> *Ug = reinterpret_cast<const V4<R> *>(B.U) + (int64_t)g * B.ncell;
+        V4<R> *Og = reinterpret_cast<V4<R> *>(B.Us) + (int64_t)g * B.ncell;
+        const R lam = (R)B.lam;
+        const int64_t sxy = (int64_t)nx * ny;
+
+        V4<R> uc = {}, un = {};
+        R Pc[6], Pn[6], Fzm[4];
+        if (act) {
+            const int64_t col = (int64_t)y * nx + x;
+            uc = ld4(Ug + z0 * sxy + col);
+            V4<R> up;
+            if (z0 > 0) up = ld4(Ug + (z0 - 1) * sxy + col);
+            else if (ph.bc[4] == 0) up = ld4(Ug + (nz - 1) * sxy + col);
+            else up = ghost_of(uc, ph.bc[4], 2);
+            R Pp[6];
+            closure<R, STRICT>(up, Pp);
+            closure<R, STRICT>(uc, Pc);
+            glf<R, 2>(up, Pp, uc, Pc, Fzm);
+        }
+        for (int z = z0; z < z1; z++) {
+            const int64_t pl = (int64_t)z * sxy;
+            if (act) {
+                const int64_t col = (int64_t)y * nx + x;
+                if (z + 1 < nz) un = ld4(Ug + pl + sxy + col);
+                else if (ph.bc[5] == 0) un = ld4(Ug + col);
+                else un = ghost_of(uc, ph.bc[5], 2);
+                closure<R, STRICT>(un, Pn);
+
+                sU[ty + 1][tx + 1] = uc;
+#pragma unroll
+                for (int k = 0; k < 6; k++) sP[k][ty + 1][tx + 1] = Pc[k];
+                // x halo
+                if (tx == 0) {
+                    V4<R> h;
+                    if (x > 0) h = ld4(Ug + pl + (int64_t)y * nx + x - 1);
+                    else if (ph.bc[0] == 0) h = ld4(Ug + pl + (int64_t)y * nx + nx - 1);
+                    else h = ghost_of(uc, ph.bc[0], 0);
+                    R Ph[6];
+                    closure<R, STRICT>(h, Ph);
+                    sU[ty + 1][0] = h;
+#pragma unroll
+                    for (int k = 0; k < 6; k++) sP[k][ty + 1][0] = Ph[k];
+                }
+                if (tx == TX - 1 || x == nx - 1) {
+                    V4<R> h;
+                    if (x + 1 < nx) h = ld4(Ug + pl + (int64_t)y * nx + x + 1);
+                    else if (ph.bc[1] == 0) h = ld4(Ug + pl + (int64_t)y * nx);
+                    else h = ghost_of(uc, ph.bc[1], 0);
+                    R Ph[6];
+                    closure<R, STRICT>(h, Ph);
+                    sU[ty + 1][tx + 2] = h;
+#pragma unroll
+                    for (int k = 0; k < 6; k++) sP[k][ty + 1][tx + 2] = Ph[k];
+                }
+                // y halo
+                if (ty == 0) {
+                    V4<R> h;
+                    if (y > 0) h = ld4(Ug + pl + (int64_t)(y - 1) * nx + x);
+                    else if (ph.bc[2] == 0) h = ld4(Ug + pl + (int64_t)(ny - 1) * nx + x);
+                    else h = ghost_of(uc, ph.bc[2], 1);
+                    R Ph[6];
+                    closure<R, STRICT>(h, Ph);
+                    sU[0][tx + 1] = h;
+#pragma unroll
+                    for (int k = 0; k < 6; k++) sP[k][0][tx + 1] = Ph[k];
+                }
+                if (ty == TY - 1 || y == ny - 1) {
+                    V4<R> h;
+                    if (y + 1 < ny) h = ld4(Ug + pl + (int64_t)(y + 1) * nx + x);
+                    else if (ph.bc[3] == 0) h = ld4(Ug + pl + x);
+                    else h = ghost_of(uc, ph.bc[3], 1);
+                    R Ph[6];
+                    closure<R, STRICT>(h, Ph);
+                    sU[ty + 2][tx + 1] = h;
+#pragma unroll
+                    for (int k = 0; k < 6; k++) sP[k][ty + 2][tx + 1] = Ph[k];
+                }
+            }
+            __syncthreads();
+            if (act) {
+                R Pl[6], Pr[6], Pd[6], Pu[6];
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    Pl[k] = sP[k][ty + 1][tx];
+                    Pr[k] = sP[k][ty + 1][tx + 2];
+                    Pd[k] = sP[k][ty][tx + 1];
+                    Pu[k] = sP[k][ty + 2][tx + 1];
+                }
+                const V4<R> ul = sU[ty + 1][tx], ur = sU[ty + 1][tx + 2];
+                const V4<R> ud = sU[ty][tx + 1], uu = sU[ty + 2][tx + 1];
+                R Fxm[4], Fxp[4], Fym[4], Fyp[4], Fzp[4];
+                glf<R, 0>(ul, Pl, uc, Pc, Fxm);
+                glf<R, 0>(uc, Pc, ur, Pr, Fxp);
+                glf<R, 1>(ud, Pd, uc, Pc, Fym);
+                glf<R, 1>(uc, Pc, uu, Pu, Fyp);
+                glf<R, 2>(uc, Pc, un, Pn, Fzp);
+                R o[4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    const R dxf = Fxp[m] - Fxm[m];
+                    const R dyf = Fyp[m] - Fym[m];
+                    const R dzf = Fzp[m] - Fzm[m];
+                    o[m] = comp(uc, m) - lam * ((dxf + dyf) + dzf);
+                    Fzm[m] = Fzp[m];
+                }
+                st4(Og + pl + (int64_t)y * nx + x, V4<R>{o[0], o[1], o[2], o[3]});
+                uc = un;
+#pragma unroll
+                for (int k = 0; k < 6; k++) Pc[k] = Pn[k];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------- rates
+// Temperature fits (cgs).  Recombination, collisional ionisation and
+// recombination cooling: Hui & Gnedin (1997) fits in lambda = 2 T_HI / T;
+// collisional excitation cooling exp(-118348/T)/(1 + sqrt(T/1e5)) (Cen 1992);
+// bremsstrahlung 1.42e-27 g_ff sqrt(T), g_ff = 1.3.  Written with one log of
+// lambda and exp/log1p of it.
+struct Rates {
+    double aA, aB, beta;   // cm^3/s
+    double kR;             // cooling per n_e n_HII: recombination + bremsstrahlung
+    double kC;             // cooling per n_e n_HI: collisional ionisation + excitation
+};
+
+__device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
+{
+    Rates r;
+    if (ph.rates_const) {
+        r.aA = ph.alphaA; r.aB = ph.alphaB; r.beta = ph.beta;
+        r.kR = 0.0; r.kC = 0.0;
+        return r;
+    }
+    const double l = 2.0 * rtd::T_HI / T;
+    const double ll = log(l);
+    // ln of the fit scales 0.522, 2.740, 0.354, 0.541, 2.250 (host-computed)
+    const double L0522 = ph.lnfit[0], L2740 = ph.lnfit[1], L0354 = ph.lnfit[2],
+                 L0541 = ph.lnfit[3], L2250 = ph.lnfit[4];
+    r.aB = 2.753e-14 * exp(1.500 * ll - 2.242 * log1p(exp(0.407 * (ll - L2740))));
+    r.aA = ph.ots ? r.aB
+                  : 1.269e-13 * exp(1.503 * ll - 1.923 * log1p(exp(0.470 * (ll - L0522))));
+    const double lnT = ph.ln2THI - ll;
+    r.beta = 21.11 * exp(-1.5 * lnT - 0.5 * l - 1.089 * ll
+                         - 1.101 * log1p(exp(0.874 * (ll - L0354))));
+    const double crec = ph.ots
+        ? 3.435e-30 * T * exp(1.970 * ll - 3.720 * log1p(exp(0.376 * (ll - L2250))))
+        : 1.778e-29 * T * exp(1.965 * ll - 2.697 * log1p(exp(0.502 * (ll - L0541))));
+    const double sT = sqrt(T);
+    const double cff = 1.42e-27 * 1.3 * sT;
+    const double cci = rtd::KB * rtd::T_HI * r.beta;
+    const double cce = 7.5e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1.0e5));
+    r.kR = crec + cff;
+    r.kC = cci + cce;
+    return r;
+}
+
+// cooling Lambda(n0, x, T) of Eq. e:therm4, erg/cm^3/s
+__device__ __forceinline__ double cooling(const Rates &r, double n0, double xHI)
+{
+    const double x = 1.0 - xHI;
+    const double ne = x * n0, nHII = x * n0, nHI = xHI * n0;
+    return ne * nHII * r.kR + ne * nHI * r.kC;
+}
+
+// e = (3/2)(1 + x) n0 kB T  (pure hydrogen, gamma = 5/3)
+__device__ __forceinline__ double eint(double xHI, double n0, double T)
+{
+    return 1.5 * (1.0 + (1.0 - xHI)) * n0 * rtd::KB * T;
+}
+
+// ------------------------------------------------------------- chemistry
+template <int G>
+struct Cell {
+    double N[G], F[G][3];
+    double xHI, T;
+};
+
+// one trial of length dtau from s into o, in the paper's order
+// N -> F -> x -> e (Sec. 2.2.4 semi-implicit update; dtau restored in the
+// absorption denominators); returns e^p and e^{p+1}
+template <int G, bool STRICT>
+__device__ __forceinline__ void chem_trial(const Phys &ph, double nunit, double n0, const double *S,
+                                           const Rates &r, double alpha, const Cell<G> &s,
+                                           double dtau, Cell<G> &o, double &ep, double &e1)
+{
+    const double x = 1.0 - s.xHI;
+#pragma unroll
+    for (int i = 0; i < G; i++) {
+        const double den = 1.0 + ph.csig[i] * s.xHI * n0 * dtau;
+        double src = S[i];
+        if (i == 0 && !ph.ots) src = src + (r.aA - r.aB) * x * x * n0 * n0 / nunit;
+        if (STRICT) {
+            o.N[i] = (s.N[i] + src * dtau) / den;
+#pragma unroll
+            for (int k = 0; k < 3; k++) o.F[i][k] = s.F[i][k] / den;
+        } else {
+            const double rd = 1.0 / den;
+            o.N[i] = (s.N[i] + src * dtau) * rd;
+#pragma unroll
+            for (int k = 0; k < 3; k++) o.F[i][k] = s.F[i][k] * rd;
+        }
+    }
+    double gam = 0.0;
+#pragma unroll
+    for (int i = 0; i < G; i++) gam = gam + ph.csig[i] * (nunit * o.N[i]);
+    o.xHI = (s.xHI + alpha * x * x * n0 * dtau) / (1.0 + dtau * (r.beta * x * n0 + gam));
+    const double e0 = eint(s.xHI, n0, s.T);
+    ep = e0;
+    if (ph.isothermal) {
+        o.T = s.T;
+        e1 = e0;
+        return;
+    }
+    double heat = 0.0;
+#pragma unroll
+    for (int i = 0; i < G; i++) heat = heat + ph.c * o.xHI * n0 * (nunit * o.N[i]) * ph.SigE[i];
+    const double lamc = cooling(r, n0, o.xHI);   // Lambda(n0, x^{p+1}, T^p)
+    const double e = e0 + dtau * heat - dtau * lamc;
+    e1 = e;
+    o.T = e / (1.5 * (1.0 + (1.0 - o.xHI)) * n0 * rtd::KB);
+}
+
+// advance one cell over `span` with sub-cycles: dtau = min(rest,
+// |e/(H - Lambda)|) when use_est (adaptive), halved while the energy changes
+// by more than 10% (Sec. 2.2.4, after Rosdahl et al. 2013)
+template <int G, bool STRICT>
+__device__ unsigned int chem_span(const Phys &ph, double nunit, double n0, const double *S,
+                                  Cell<G> &s, double span, bool use_est, int &ncyc)
+{
+    unsigned int err = 0;
+    double tau = 0.0;
+    for (;;) {
+        const double rem = span - tau;
+        const Rates r = rates_at(ph, s.T);
+        const double alpha = ph.ots ? r.aB : r.aA;
+        double dtau = rem;
+        bool last = true;
+        if (!ph.isothermal && use_est) {
+            double heat = 0.0;
+#pragma unroll
+            for (int i = 0; i < G; i++)
+                heat = heat + ph.c * s.xHI * n0 * (nunit * s.N[i]) * ph.SigE[i];
+            const double rate = heat - cooling(r, n0, s.xHI);
+            const double e = eint(s.xHI, n0, s.T);
+            if (rate != 0.0) {
+                const double est = fabs(e / rate);
+                if (est < rem) { dtau = est; last = false; }
+            }
+        }
+        Cell<G> o;
+        double ep, e1;
+        for (int h = 0;; h++) {
+            chem_trial<G, STRICT>(ph, nunit, n0, S, r, alpha, s, dtau, o, ep, e1);
+            if (ph.isothermal) break;
+            if (!isfinite(e1)) {            // no amount of halving repairs a NaN/Inf
+                s = o;
+                ncyc++;
+                return err | RTD_ERR_NONFINITE;
+            }
+            if (fabs(e1 - ep) <= 0.1 * ep) break;
+            if (h >= ph.max_halvings) { err |= RTD_ERR_SUBCYCLE; break; }
+            dtau = 0.5 * dtau;
+            last = false;
+        }
+        s = o;
+        ncyc++;
+        if (last) break;
+        tau = tau + dtau;
+        if (ncyc >= RTD_MAXCYC) { err |= RTD_ERR_SUBCYCLE; break; }
+    }
+    return err;
+}
+
+template <typename R> __device__ __forceinline__ double flux_tol();
+template <> __device__ __forceinline__ double flux_tol<float>() { return 1e-5; }
+template <> __device__ __forceinline__ double flux_tol<double>() { return 1e-12; }
+
+__device__ __forceinline__ double ldn(const float *p, int64_t i) { return (double)p[i]; }
+__device__ __forceinline__ double ldn(const double *p, int64_t i) { return p[i]; }
+
+// warp + block reduction of RTD_NDIAG values (sum, sum, max, sum, sum), fixed order
+__device__ __forceinline__ void block_reduce_diag(double v[RTD_NDIAG], double *out)
+{
+    __shared__ double red[RTD_CHEM_BLOCK / 32][RTD_NDIAG];
+#pragma unroll
+    for (int k = 0; k < RTD_NDIAG; k++) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, v[k], off);
+            v[k] = (k == 2) ? fmax(v[k], o) : v[k] + o;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < RTD_NDIAG; k++) red[wid][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < RTD_NDIAG; k++) {
+            double a = red[0][k];
+            for (int w = 1; w < RTD_CHEM_BLOCK / 32; w++)
+                a = (k == 2) ? fmax(a, red[w][k]) : a + red[w][k];
+            out[k] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// One work item = RTD_CHEM_BLOCK consecutive cells of one box, one thread per
+// cell.  Reads the post-transport state, runs the sub-cycled chemistry over
+// the box's dt, writes the new radiation state into the caller's U, and the
+// block's diagnostic partials.
+template <int G, typename TU, typename TN, bool STRICT>
+__global__ void __launch_bounds__(RTD_CHEM_BLOCK)
+k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ctl *ctl,
+       double *__restrict__ partials)
+{
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int b = find_box(boxes, nboxes, it, true);
+        const BoxDev &B = boxes[b];
+        const int64_t c = (it - B.citem0) * RTD_CHEM_BLOCK + threadIdx.x;
+        double v[RTD_NDIAG] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        if (c < B.ncell) {
+            const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
+            V4<TU> *U = reinterpret_cast<V4<TU> *>(B.U);
+            Cell<G> s;
+            unsigned long long nclamp = 0;
+#pragma unroll
+            for (int i = 0; i < G; i++) {
+                const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
+                s.N[i] = (double)u.x;
+                s.F[i][0] = (double)u.y; s.F[i][1] = (double)u.z; s.F[i][2] = (double)u.w;
+                if (s.N[i] > 0.0) {
+                    const double ux = s.F[i][0] / s.N[i], uy = s.F[i][1] / s.N[i],
+                                 uz = s.F[i][2] / s.N[i];
+                    const double f2 = ux * ux + uy * uy + uz * uz;
+                    const double tol = 1.0 + flux_tol<TU>();
+                    if (f2 > tol * tol) nclamp++;
+                    if (f2 > 1.01 * 1.01) atomicOr(&ctl->err, RTD_ERR_REALIZ);
+                }
+            }
+            if (nclamp) atomicAdd(&ctl->nclamp, nclamp);
+            s.xHI = B.xHI[c];
+            s.T = B.T[c];
+            const double n0 = ldn(reinterpret_cast<const TN *>(B.n0), c);
+            // source term of this cell: sorted unique cells, binary search
+            double S[G];
+#pragma unroll
+            for (int i = 0; i < G; i++) S[i] = 0.0;
+            if (B.nsrc > 0) {
+                int lo = 0, hi = B.nsrc - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (B.src_cell[mid] < c) lo = mid + 1; else hi = mid;
+                }
+                if (B.src_cell[lo] == c)
+#pragma unroll
+                    for (int i = 0; i < G; i++) S[i] = B.src_S[(int64_t)lo * G + i];
+            }
+            int ncyc = 0;
+            unsigned int err = 0;
+            if (ph.nsub > 0) {
+                const double h = B.dt / ph.nsub;
+                for (int k = 0; k < ph.nsub; k++)
+                    err |= chem_span<G, STRICT>(ph, B.nunit, n0, S, s, h, false, ncyc);
+            } else {
+                err |= chem_span<G, STRICT>(ph, B.nunit, n0, S, s, B.dt, true, ncyc);
+            }
+            if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
+            if (err) atomicOr(&ctl->err, err);
+            double ph_tot = 0.0, fmax = 0.0;
+#pragma unroll
+            for (int i = 0; i < G; i++) {
+                const V4<TU> o = {(TU)s.N[i], (TU)s.F[i][0], (TU)s.F[i][1], (TU)s.F[i][2]};
+                st4(U + (int64_t)i * B.ncell + c, o);
+                const double N = (double)o.x;
+                ph_tot += N;
+                if (N > 0.0) {
+                    const double ux = (double)o.y / N, uy = (double)o.z / N, uz = (double)o.w / N;
+                    const double f = sqrt(ux * ux + uy * uy + uz * uz);
+                    fmax = fmax > f ? fmax : f;
+                }
+            }
+            B.xHI[c] = s.xHI;
+            B.T[c] = s.T;
+            v[0] = 1.0 - s.xHI;
+            v[1] = ph_tot;
+            v[2] = fmax;
+            v[3] = s.xHI < 0.5 ? 1.0 : 0.0;
+            v[4] = (double)ncyc;
+        }
+        block_reduce_diag(v, partials + it * RTD_NDIAG);
+    }
+}
+
+#ifndef RTK_STRICT_TU
+// Per-box sums of the chemistry partials in a fixed order; writes the step's
+// diagnostics (ionised fraction, photons, max f, n(xHI<0.5), mean sub-cycles)
+// into the caller's history and into lastdiag.
+__global__ void __launch_bounds__(RTD_CHEM_BLOCK)
+k_finalize(const BoxDev *__restrict__ boxes, const double *__restrict__ partials, Ctl *ctl,
+           double *lastdiag)
+{
+    const int b = blockIdx.x;
+    const BoxDev &B = boxes[b];
+    double v[RTD_NDIAG] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = threadIdx.x; i < B.ncitems; i += blockDim.x) {
+        const double *p = partials + (B.citem0 + i) * RTD_NDIAG;
+#pragma unroll
+        for (int k = 0; k < RTD_NDIAG; k++) v[k] = (k == 2) ? fmax(v[k], p[k]) : v[k] + p[k];
+    }
+    __shared__ double out[RTD_NDIAG];
+    block_reduce_diag(v, out);
+    if (threadIdx.x == 0) {
+        const double nc = (double)B.ncell;
+        double d[RTD_NDIAG];
+        d[0] = out[0] / nc;
+        d[1] = out[1] * B.nunit * (B.dx * B.dx * B.dx);
+        d[2] = out[2];
+        d[3] = out[3];
+        d[4] = out[4] / nc;
+        for (int k = 0; k < RTD_NDIAG; k++) lastdiag[b * RTD_NDIAG + k] = d[k];
+        if (ctl->hist) {
+            double *h = ctl->hist + ((int64_t)ctl->step * ctl->nboxes + b) * RTD_NDIAG;
+            for (int k = 0; k < RTD_NDIAG; k++) h[k] = d[k];
+        }
+    }
+}
+#endif  // RTK_STRICT_TU
+
+}  // namespace rtk

@@ -116,6 +116,9 @@ typedef struct rt_stats {
     int     nboxes;
     int64_t cells;                       /* cells over all boxes */
     double  last_diag[RT_NDIAG];         /* diagnostics of box 0 after the last step */
+    double  kernel_ms[3];                /* with profiling on: summed CUDA-event time of the
+                                            transport, chemistry and diagnostics kernels */
+    int64_t kernel_launches[3];          /* launches timed into kernel_ms */
 } rt_stats;
 
 typedef struct rt_handle rt_handle;
@@ -147,6 +150,12 @@ RT_API int rt_upload(rt_handle *h, int box, const void *U, const double *xHI, co
 
 /* Copy the device state of `box` into host arrays (NULL skips an array). */
 RT_API int rt_download(rt_handle *h, int box, void *U, double *xHI, double *T);
+
+/* Profiling switch.  on != 0: later rt_step calls launch each kernel directly
+ * (no graph replay) between CUDA events recorded on the library's stream and
+ * add the elapsed times to rt_stats.kernel_ms; the counters restart at zero.
+ * on == 0: back to graph replay. */
+RT_API int rt_set_profiling(rt_handle *h, int on);
 
 /* Counters and the last diagnostics; never launches work. */
 RT_API int rt_query(rt_handle *h, rt_stats *st);

@@ -69,11 +69,14 @@ class rt_stats(C.Structure):
         ("nboxes", C.c_int),
         ("cells", C.c_int64),
         ("last_diag", C.c_double * RT_NDIAG),
+        ("kernel_ms", C.c_double * 3),
+        ("kernel_launches", C.c_int64 * 3),
     ]
 
 
 EXPORTS = ("rt_create", "rt_set_sources", "rt_step", "rt_upload", "rt_download", "rt_query",
-           "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table")
+           "rt_set_profiling", "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table")
+KERNELS = ("transport", "chemistry", "diagnostics")
 
 _lib = None
 
@@ -102,6 +105,7 @@ def lib(build_if_missing: bool = True):
         "rt_upload": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
         "rt_download": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "rt_query": (C.c_int, [vp, C.POINTER(rt_stats)]),
+        "rt_set_profiling": (C.c_int, [vp, C.c_int]),
         "rt_last_error": (C.c_char_p, [vp]),
         "rt_destroy": (None, [vp]),
         "rt_timestep": (C.c_double, [C.POINTER(rt_params), C.c_double]),
@@ -178,6 +182,10 @@ def rt_query(h) -> rt_stats:
     st = rt_stats()
     _check(lib().rt_query(h, C.byref(st)), h)
     return st
+
+
+def rt_set_profiling(h, on: bool) -> None:
+    _check(lib().rt_set_profiling(h, int(bool(on))), h)
 
 
 def rt_last_error(h=None) -> str:

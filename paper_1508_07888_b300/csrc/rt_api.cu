@@ -48,6 +48,10 @@ struct rt_handle {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph = nullptr;
     int64_t steps_done = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;        // 4 per profiled step
+    double kernel_ms[3] = {0, 0, 0};
+    int64_t kernel_launches[3] = {0, 0, 0};
     unsigned long long nclamp = 0;
     int error_bits = 0;
     std::string err;
@@ -86,6 +90,7 @@ static void release(rt_handle *h)
     cudaFree(h->d_ctl);
     cudaFreeHost(h->h_ctl);
     cudaFreeHost(h->h_lastdiag);
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->s) cudaStreamDestroy(h->s);
@@ -319,23 +324,26 @@ extern "C" int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *ce
     }
 }
 
-// one step of the hot path on stream s: transport, chemistry, diagnostics
-static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s)
+// one step of the hot path on stream s: transport, chemistry, diagnostics;
+// ev (profiling) = 4 events recorded before, between and after the kernels
+static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = nullptr)
 {
     rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s};
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
     cudaError_t e;
-    if (h->strict) {
-        e = rtl::transport_strict(Lt, h->zc, h->ph, h->d_ctl);
-        if (e != cudaSuccess) return e;
-        e = rtl::chem_strict(h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials);
-    } else {
-        e = rtl::transport_fast(h->fp64, Lt, h->zc, h->ph, h->d_ctl);
-        if (e != cudaSuccess) return e;
-        e = rtl::chem_fast(h->fp64, h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials);
-    }
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    e = h->strict ? rtl::transport_strict(Lt, h->zc, h->ph, h->d_ctl)
+                  : rtl::transport_fast(h->fp64, Lt, h->zc, h->ph, h->d_ctl);
     if (e != cudaSuccess) return e;
-    return rtl::finalize(h->d_boxes, h->nboxes, h->d_partials, h->d_ctl, h->d_lastdiag, s);
+    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+    e = h->strict ? rtl::chem_strict(h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials)
+                  : rtl::chem_fast(h->fp64, h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+    e = rtl::finalize(h->d_boxes, h->nboxes, h->d_partials, h->d_ctl, h->d_lastdiag, s);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 static int build_graph(rt_handle *h)
@@ -386,16 +394,36 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
         if (rc) return rc;
     }
     int done = 0;
-    if (h->graph)
-        for (; done + RT_GRAPH_STEPS <= nsteps; done += RT_GRAPH_STEPS)
-            CU(h, cudaGraphLaunch(h->graph, h->s));
-    for (; done < nsteps; done++) CU(h, enqueue_step(h, h->s));
+    if (h->profiling) {
+        while (h->prof_ev.size() < (size_t)4 * nsteps) {
+            cudaEvent_t e;
+            CU(h, cudaEventCreate(&e));
+            h->prof_ev.push_back(e);
+        }
+        for (; done < nsteps; done++) CU(h, enqueue_step(h, h->s, &h->prof_ev[4 * (size_t)done]));
+    } else {
+        if (h->graph)
+            for (; done + RT_GRAPH_STEPS <= nsteps; done += RT_GRAPH_STEPS)
+                CU(h, cudaGraphLaunch(h->graph, h->s));
+        for (; done < nsteps; done++) CU(h, enqueue_step(h, h->s));
+    }
     CU(h, cudaMemcpyAsync(c, h->d_ctl, sizeof(rtd::Ctl), cudaMemcpyDeviceToHost, h->s));
     CU(h, cudaMemcpyAsync(h->h_lastdiag, h->d_lastdiag, sizeof(double) * RTD_NDIAG * h->nboxes,
                           cudaMemcpyDeviceToHost, h->s));
     CU(h, cudaEventRecord(h->ev_out, h->s));
     CU(h, cudaStreamWaitEvent(h->user, h->ev_out, 0));
     CU(h, cudaStreamSynchronize(h->s));
+    if (h->profiling) {
+        for (int k = 0; k < nsteps; k++) {
+            for (int j = 0; j < 3; j++) {
+                float ms = 0.f;
+                CU(h, cudaEventElapsedTime(&ms, h->prof_ev[4 * (size_t)k + j],
+                                           h->prof_ev[4 * (size_t)k + j + 1]));
+                h->kernel_ms[j] += ms;
+                h->kernel_launches[j] += 1;
+            }
+        }
+    }
     h->steps_done += nsteps;
     h->nclamp += c->nclamp;
     h->error_bits |= (int)c->err;
@@ -439,6 +467,17 @@ extern "C" int rt_download(rt_handle *h, int box, void *U, double *xHI, double *
     return copy_state(h, box, false, U, xHI, T, nullptr);
 }
 
+extern "C" int rt_set_profiling(rt_handle *h, int on)
+{
+    if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
+    h->profiling = on != 0;
+    for (int j = 0; j < 3; j++) {
+        h->kernel_ms[j] = 0.0;
+        h->kernel_launches[j] = 0;
+    }
+    return RT_OK;
+}
+
 extern "C" int rt_query(rt_handle *h, rt_stats *st)
 {
     if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
@@ -450,6 +489,10 @@ extern "C" int rt_query(rt_handle *h, rt_stats *st)
     st->nboxes = h->nboxes;
     for (const auto &D : h->bdev) st->cells += D.ncell;
     for (int k = 0; k < RT_NDIAG; k++) st->last_diag[k] = h->h_lastdiag[k];
+    for (int j = 0; j < 3; j++) {
+        st->kernel_ms[j] = h->kernel_ms[j];
+        st->kernel_launches[j] = h->kernel_launches[j];
+    }
     return RT_OK;
 }
 

@@ -60,7 +60,8 @@ typedef enum rt_status {
     RT_ERR_SUBCYCLE = -5,       /* 10% rule needed more than max_halvings halvings,
                                    or a cell exceeded 1e6 sub-cycles in one step */
     RT_ERR_TIMEOUT = -6,        /* reserved: a bounded device wait gave up */
-    RT_ERR_STATE = -7           /* call out of order (e.g. on a destroyed handle) */
+    RT_ERR_STATE = -7,          /* call out of order (e.g. on a destroyed handle) */
+    RT_ERR_TOO_LARGE = -8       /* rt_transport_static: the box does not fit its static scratch */
 } rt_status;
 
 typedef enum rt_precision {
@@ -178,6 +179,40 @@ RT_API double rt_timestep(const rt_params *p, double dx);
  * ngroups values each: sigN, sigE (cm^2), Eavg (erg), frac (sums to 1). */
 RT_API int rt_group_table(int ngroups, const double *edges_eV, double T_bb,
                    double *sigN, double *sigE, double *Eavg, double *frac);
+
+/* Bytes of the file-scope device array that rt_transport_static uses as its
+ * only scratch (32 MiB).  Every GPU that loads this library holds it until
+ * the process exits. */
+#define RT_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* Transport without allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc while they run -- a
+ * framework whose caching allocator owns all device memory, or a code that
+ * must not grow its device footprint or let an allocation synchronise the
+ * device in the middle of a run.  rt_create allocates scratch; this call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * It advances the radiation state box->U of one box, in place, by nsteps
+ * homogeneous GLF transport steps -- the first stage of rt_step, without
+ * sources, absorption or chemistry -- using p->ngroups, c_red, cfl, bc and
+ * precision (SPLIT: float U; FP64 / FP64_STRICT: double U); the chemistry
+ * fields of p and box->xHI, box->T, box->n0 are not used and may be NULL.
+ * The post-transport state lives in a static device array of
+ * RT_STATIC_SCRATCH_BYTES bytes, so the box must satisfy
+ *     ngroups * nx * ny * nz * 4 * element size <= RT_STATIC_SCRATCH_BYTES - 768
+ * (e.g. 2,097,088 cells for one FP32 group); a larger box is rejected with
+ * RT_ERR_TOO_LARGE before any work is queued.
+ *
+ * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * and the call returns after that stream has drained.  The first call made
+ * while a given device is current looks up the array's device address on that
+ * device (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  Every call shares the one array and it keeps the last
+ * call's contents (each call rewrites what it reads before reading it), so
+ * calls that overlap on the GPU -- from several threads or streams at once --
+ * race and must be serialised by the caller.
+ * Returns RT_OK, RT_ERR_ARG (bad argument), RT_ERR_TOO_LARGE or RT_ERR_CUDA. */
+RT_API int rt_transport_static(const rt_params *p, const rt_box *box, int nsteps, void *stream);
 
 #ifdef __cplusplus
 }

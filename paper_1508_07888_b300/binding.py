@@ -22,6 +22,8 @@ RT_MAX_GROUPS = 4
 RT_NDIAG = 5
 RT_OK, RT_ERR_ARG, RT_ERR_CUDA, RT_ERR_NONFINITE = 0, -1, -2, -3
 RT_ERR_REALIZABILITY, RT_ERR_SUBCYCLE, RT_ERR_TIMEOUT, RT_ERR_STATE = -4, -5, -6, -7
+RT_ERR_TOO_LARGE = -8
+RT_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 RT_PREC_SPLIT, RT_PREC_FP64, RT_PREC_FP64_STRICT = 0, 1, 2
 RT_BC_PERIODIC, RT_BC_TRANSMISSIVE, RT_BC_REFLECTIVE = 0, 1, 2
 DIAG_NAMES = ("ionised_fraction", "photons", "max_flux_ratio", "n_ionised", "mean_subcycles")
@@ -75,7 +77,8 @@ class rt_stats(C.Structure):
 
 
 EXPORTS = ("rt_create", "rt_set_sources", "rt_step", "rt_upload", "rt_download", "rt_query",
-           "rt_set_profiling", "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table")
+           "rt_set_profiling", "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table",
+           "rt_transport_static")
 KERNELS = ("transport", "chemistry", "diagnostics")
 
 _lib = None
@@ -110,6 +113,7 @@ def lib(build_if_missing: bool = True):
         "rt_destroy": (None, [vp]),
         "rt_timestep": (C.c_double, [C.POINTER(rt_params), C.c_double]),
         "rt_group_table": (C.c_int, [C.c_int, dp, C.c_double, dp, dp, dp, dp]),
+        "rt_transport_static": (C.c_int, [C.POINTER(rt_params), C.POINTER(rt_box), C.c_int, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -194,6 +198,12 @@ def rt_last_error(h=None) -> str:
 
 def rt_destroy(h) -> None:
     lib().rt_destroy(h)
+
+
+def rt_transport_static(p: rt_params, box: rt_box, nsteps: int, stream_ptr: int = 0) -> int:
+    """Transport steps that allocate no device memory (see include/rt_m1.h);
+    returns the status code."""
+    return lib().rt_transport_static(C.byref(p), C.byref(box), int(nsteps), C.c_void_p(stream_ptr or None))
 
 
 # ------------------------------------------------------------------ helpers

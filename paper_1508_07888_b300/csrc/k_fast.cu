@@ -6,25 +6,60 @@
 
 namespace rtl {
 
+// dynamic shared memory of the transport pipeline (above the 48 KB default
+// for FP64); set once per kernel and device before its first launch
+template <typename R, bool STRICT>
+static cudaError_t transport_attr()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport<R, STRICT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rtk::transport_smem_bytes<R>());
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
 cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
     dim3 blk(RTD_TX, RTD_TY);
-    if (fp64)
-        rtk::k_transport<double, false><<<L.grid, blk, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
-    else
-        rtk::k_transport<float, false><<<L.grid, blk, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    if (fp64) {
+        cudaError_t e = transport_attr<double, false>();
+        if (e != cudaSuccess) return e;
+        rtk::k_transport<double, false><<<L.grid, blk, rtk::transport_smem_bytes<double>(), L.stream>>>(
+            L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    } else {
+        cudaError_t e = transport_attr<float, false>();
+        if (e != cudaSuccess) return e;
+        rtk::k_transport<float, false><<<L.grid, blk, rtk::transport_smem_bytes<float>(), L.stream>>>(
+            L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    }
     return cudaGetLastError();
+}
+
+// dynamic shared memory of the chemistry kernel: the rate table
+template <typename K>
+static size_t chem_smem(K kernel, const rtd::Phys &ph)
+{
+    const size_t bytes = (ph.rtab && !ph.rates_const) ? rate_table_doubles() * sizeof(double) : 0;
+    if (bytes) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return bytes;
 }
 
 template <int G>
 static void chem_g(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, double *partials)
 {
-    if (fp64)
-        rtk::k_chem<G, double, double, false><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(
-            L.boxes, L.nboxes, L.nitems, ph, ctl, partials);
-    else
-        rtk::k_chem<G, float, float, false><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(
-            L.boxes, L.nboxes, L.nitems, ph, ctl, partials);
+    if (fp64) {
+        auto k = rtk::k_chem<G, double, double, false>;
+        k<<<L.grid, RTD_CHEM_BLOCK, chem_smem(k, ph), L.stream>>>(L.boxes, L.nboxes, L.nitems, ph,
+                                                                  ctl, partials);
+    } else {
+        auto k = rtk::k_chem<G, float, float, false>;
+        k<<<L.grid, RTD_CHEM_BLOCK, chem_smem(k, ph), L.stream>>>(L.boxes, L.nboxes, L.nitems, ph,
+                                                                  ctl, partials);
+    }
 }
 
 cudaError_t chem_fast(bool fp64, int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
@@ -47,24 +82,35 @@ cudaError_t finalize(const rtd::BoxDev *boxes, int nboxes, const double *partial
     return cudaGetLastError();
 }
 
-static int occ(const void *f, int threads)
+static int occ(const void *f, int threads, size_t smem = 0)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, 0) != cudaSuccess) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }
 
 int transport_occupancy_fast(bool fp64)
 {
-    return fp64 ? occ((const void *)rtk::k_transport<double, false>, RTD_TX * RTD_TY)
-                : occ((const void *)rtk::k_transport<float, false>, RTD_TX * RTD_TY);
+    if (fp64) {
+        transport_attr<double, false>();
+        return occ((const void *)rtk::k_transport<double, false>, RTD_TX * RTD_TY,
+                   rtk::transport_smem_bytes<double>());
+    }
+    transport_attr<float, false>();
+    return occ((const void *)rtk::k_transport<float, false>, RTD_TX * RTD_TY,
+               rtk::transport_smem_bytes<float>());
 }
 
 int chem_occupancy_fast(bool fp64, int G)
 {
-#define OCC_G(g) \
-    (fp64 ? occ((const void *)rtk::k_chem<g, double, double, false>, RTD_CHEM_BLOCK) \
-          : occ((const void *)rtk::k_chem<g, float, float, false>, RTD_CHEM_BLOCK))
+    const size_t tb = rate_table_doubles() * sizeof(double);
+#define OCC_G(g)                                                                                \
+    (fp64 ? (cudaFuncSetAttribute(rtk::k_chem<g, double, double, false>,                         \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb),         \
+             occ((const void *)rtk::k_chem<g, double, double, false>, RTD_CHEM_BLOCK, tb))       \
+          : (cudaFuncSetAttribute(rtk::k_chem<g, float, float, false>,                           \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb),         \
+             occ((const void *)rtk::k_chem<g, float, float, false>, RTD_CHEM_BLOCK, tb)))
     switch (G) {
     case 1: return OCC_G(1);
     case 2: return OCC_G(2);

@@ -7,18 +7,39 @@
 
 namespace rtl {
 
+static cudaError_t transport_attr_strict()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport<double, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rtk::transport_smem_bytes<double>());
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
 cudaError_t transport_strict(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
     dim3 blk(RTD_TX, RTD_TY);
-    rtk::k_transport<double, true><<<L.grid, blk, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    cudaError_t e = transport_attr_strict();
+    if (e != cudaSuccess) return e;
+    rtk::k_transport<double, true><<<L.grid, blk, rtk::transport_smem_bytes<double>(), L.stream>>>(
+        L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
     return cudaGetLastError();
 }
 
 cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, double *partials)
 {
-#define CHEM_G(g)                                                                          \
-    rtk::k_chem<g, double, double, true><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(          \
-        L.boxes, L.nboxes, L.nitems, ph, ctl, partials)
+    const size_t tb = (ph.rtab && !ph.rates_const) ? rate_table_doubles() * sizeof(double) : 0;
+#define CHEM_G(g)                                                                                \
+    do {                                                                                         \
+        if (tb) cudaFuncSetAttribute(rtk::k_chem<g, double, double, true>,                       \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);      \
+        rtk::k_chem<g, double, double, true><<<L.grid, RTD_CHEM_BLOCK, tb, L.stream>>>(          \
+            L.boxes, L.nboxes, L.nitems, ph, ctl, partials);                                     \
+    } while (0)
     switch (G) {
     case 1: CHEM_G(1); break;
     case 2: CHEM_G(2); break;
@@ -30,10 +51,10 @@ cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *c
     return cudaGetLastError();
 }
 
-static int occ(const void *f, int threads)
+static int occ(const void *f, int threads, size_t smem = 0)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, 0) != cudaSuccess) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }
 
@@ -42,19 +63,29 @@ int chem_occupancy_fast(bool fp64, int G);
 
 int transport_occupancy(bool fp64, bool strict)
 {
-    if (strict) return occ((const void *)rtk::k_transport<double, true>, RTD_TX * RTD_TY);
+    if (strict) {
+        transport_attr_strict();
+        return occ((const void *)rtk::k_transport<double, true>, RTD_TX * RTD_TY,
+                   rtk::transport_smem_bytes<double>());
+    }
     return transport_occupancy_fast(fp64);
 }
 
 int chem_occupancy(bool fp64, bool strict, int G)
 {
     if (!strict) return chem_occupancy_fast(fp64, G);
+    const size_t tb = rate_table_doubles() * sizeof(double);
+#define OCC_S(g)                                                                                 \
+    (cudaFuncSetAttribute(rtk::k_chem<g, double, double, true>,                                  \
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb),                 \
+     occ((const void *)rtk::k_chem<g, double, double, true>, RTD_CHEM_BLOCK, tb))
     switch (G) {
-    case 1: return occ((const void *)rtk::k_chem<1, double, double, true>, RTD_CHEM_BLOCK);
-    case 2: return occ((const void *)rtk::k_chem<2, double, double, true>, RTD_CHEM_BLOCK);
-    case 3: return occ((const void *)rtk::k_chem<3, double, double, true>, RTD_CHEM_BLOCK);
-    default: return occ((const void *)rtk::k_chem<4, double, double, true>, RTD_CHEM_BLOCK);
+    case 1: return OCC_S(1);
+    case 2: return OCC_S(2);
+    case 3: return OCC_S(3);
+    default: return OCC_S(4);
     }
+#undef OCC_S
 }
 
 }  // namespace rtl

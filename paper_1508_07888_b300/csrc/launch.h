@@ -30,6 +30,20 @@ cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *c
 cudaError_t finalize(const rtd::BoxDev *boxes, int nboxes, const double *partials, rtd::Ctl *ctl,
                      double *lastdiag, cudaStream_t stream);
 
+// transport tiling of a box: x/y tiles and the number of plane units
+// (ngroups x tiles_x x tiles_y x nz) the transport kernel spreads over its grid
+inline void transport_layout(rtd::BoxDev &B, int ngroups)
+{
+    B.tiles_x = (B.nx + RTD_TX - 1) / RTD_TX;
+    B.tiles_y = (B.ny + RTD_TY - 1) / RTD_TY;
+    B.zchunks = 1;
+    B.ntitems = (int64_t)ngroups * B.tiles_x * B.tiles_y * B.nz;
+}
+
+// rate tables of the chemistry kernel (rate_table.cu); false = unusable
+bool build_rate_table(bool ots, double *out);
+constexpr size_t rate_table_doubles() { return (size_t)RTD_TAB_NF * RTD_TAB_NINT * RTD_TAB_NC; }
+
 // resident blocks per SM of each kernel (for persistent grid sizing)
 int transport_occupancy(bool fp64, bool strict);
 int chem_occupancy(bool fp64, bool strict, int G);

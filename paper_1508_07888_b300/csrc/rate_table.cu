@@ -1,0 +1,114 @@
+// rate_table.cu -- host-side construction of the temperature-rate tables
+// used by the chemistry kernel.
+//
+// The rate fits (Hui & Gnedin 1997 recombination, collisional ionisation and
+// recombination cooling; exp(-118348/T)/(1 + sqrt(T/1e5)) excitation cooling;
+// 1.42e-27 x 1.3 sqrt(T) bremsstrahlung) are evaluated here in long double and
+// interpolated, per interval of ll = ln(2 T_HI / T), by a degree-10 Chebyshev
+// polynomial rewritten in the monomial basis of the local variable
+// t in [-1, 1].  Tabulated functions:
+//   0: alpha_A   1: alpha_B   2: recombination (case A or B) + free-free cooling
+//   3: ln(beta) + lambda/2            (beta = exp(f3 - lambda/2))
+//   4: ln(excitation cooling) + 118348/T
+// The two exp(-c/T) factors stay outside the tables so every tabulated
+// function is smooth in ll.  The table is checked against the long-double
+// fits before use; the kernel evaluates the fits directly when it is absent.
+#include <cmath>
+
+#include "launch.h"
+#include "rt_device.h"
+
+namespace {
+
+typedef long double LD;
+const LD THI = 157807.0L;
+
+LD fit_aA(LD T)
+{
+    const LD l = 2 * THI / T;
+    return 1.269e-13L * powl(l, 1.503L) / powl(1 + powl(l / 0.522L, 0.470L), 1.923L);
+}
+LD fit_aB(LD T)
+{
+    const LD l = 2 * THI / T;
+    return 2.753e-14L * powl(l, 1.500L) / powl(1 + powl(l / 2.740L, 0.407L), 2.242L);
+}
+LD fit_kR(LD T, bool ots)
+{
+    const LD l = 2 * THI / T;
+    const LD rec = ots ? 3.435e-30L * T * powl(l, 1.970L) / powl(1 + powl(l / 2.250L, 0.376L), 3.720L)
+                       : 1.778e-29L * T * powl(l, 1.965L) / powl(1 + powl(l / 0.541L, 0.502L), 2.697L);
+    return rec + 1.42e-27L * 1.3L * sqrtl(T);
+}
+LD fit_lnbeta_plus(LD T)   // ln(beta) + lambda/2
+{
+    const LD l = 2 * THI / T;
+    return logl(21.11L) - 1.5L * logl(T) - 1.089L * logl(l) - 1.101L * log1pl(powl(l / 0.354L, 0.874L));
+}
+LD fit_lncce_plus(LD T)    // ln(excitation cooling) + 118348/T
+{
+    return logl(7.5e-19L) - log1pl(sqrtl(T / 1.0e5L));
+}
+
+LD fit(int f, LD ll, bool ots)
+{
+    const LD T = 2 * THI / expl(ll);
+    switch (f) {
+    case 0: return fit_aA(T);
+    case 1: return fit_aB(T);
+    case 2: return fit_kR(T, ots);
+    case 3: return fit_lnbeta_plus(T);
+    default: return fit_lncce_plus(T);
+    }
+}
+
+}  // namespace
+
+namespace rtl {
+
+// fills out[RTD_TAB_NF][RTD_TAB_NINT][RTD_TAB_NC]; returns true when the
+// table reproduces the long-double fits to 1e-13 (relative for functions
+// 0-2, absolute for the logarithms 3-4) at 17 points per interval
+bool build_rate_table(bool ots, double *out)
+{
+    const int N = RTD_TAB_NC;
+    // monomial coefficients of the Chebyshev polynomials T_0 .. T_{N-1}
+    LD cheb[RTD_TAB_NC][RTD_TAB_NC] = {};
+    cheb[0][0] = 1;
+    cheb[1][1] = 1;
+    for (int n = 2; n < N; n++)
+        for (int i = 0; i < N; i++)
+            cheb[n][i] = (i > 0 ? 2 * cheb[n - 1][i - 1] : 0) - cheb[n - 2][i];
+    for (int f = 0; f < RTD_TAB_NF; f++) {
+        for (int j = 0; j < RTD_TAB_NINT; j++) {
+            const LD a = (LD)RTD_TAB_LL0 + j * (LD)RTD_TAB_H;
+            LD fv[RTD_TAB_NC], c[RTD_TAB_NC];
+            for (int m = 0; m < N; m++) {
+                const LD t = cosl(M_PIl * (m + 0.5L) / N);
+                fv[m] = fit(f, a + (t + 1) * 0.5L * (LD)RTD_TAB_H, ots);
+            }
+            for (int n = 0; n < N; n++) {
+                LD s = 0;
+                for (int m = 0; m < N; m++) s += fv[m] * cosl(M_PIl * n * (m + 0.5L) / N);
+                c[n] = (n == 0 ? 1.0L : 2.0L) * s / N;
+            }
+            double *o = out + ((size_t)f * RTD_TAB_NINT + j) * N;
+            for (int i = 0; i < N; i++) {
+                LD s = 0;
+                for (int n = 0; n < N; n++) s += c[n] * cheb[n][i];
+                o[i] = (double)s;
+            }
+            for (int k = 0; k <= 16; k++) {           // check, in double Horner
+                const double t = -1.0 + 2.0 * k / 16.0;
+                double p = o[N - 1];
+                for (int i = N - 2; i >= 0; i--) p = p * t + o[i];
+                const LD ex = fit(f, a + ((LD)t + 1) * 0.5L * (LD)RTD_TAB_H, ots);
+                const LD err = f <= 2 ? fabsl((p - ex) / ex) : fabsl(p - ex);
+                if (!(err <= 1e-13L)) return false;
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace rtl

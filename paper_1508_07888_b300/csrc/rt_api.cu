@@ -37,6 +37,7 @@ struct rt_handle {
     std::vector<int64_t *> d_src_cell;
     std::vector<double *> d_src_S;
     double *d_partials = nullptr;
+    double *d_rtab = nullptr;                // rate table (null: fits evaluated directly)
     double *d_lastdiag = nullptr;
     rtd::Ctl *d_ctl = nullptr;
     rtd::Ctl *h_ctl = nullptr;               // pinned mirror
@@ -86,6 +87,7 @@ static void release(rt_handle *h)
     for (auto *p : h->d_src_S) cudaFree(p);
     cudaFree(h->d_boxes);
     cudaFree(h->d_partials);
+    cudaFree(h->d_rtab);
     cudaFree(h->d_lastdiag);
     cudaFree(h->d_ctl);
     cudaFreeHost(h->h_ctl);
@@ -218,9 +220,6 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     std::memset(&D, 0, sizeof D);
                     D.nx = B.nx; D.ny = B.ny; D.nz = B.nz;
                     D.ncell = (int64_t)B.nx * B.ny * B.nz;
-                    D.tiles_x = (B.nx + RTD_TX - 1) / RTD_TX;
-                    D.tiles_y = (B.ny + RTD_TY - 1) / RTD_TY;
-                    D.zchunks = (B.nz + h->zc - 1) / h->zc;
                     D.dx = B.dx;
                     D.nunit = B.nunit;
                     D.dt = p->cfl * B.dx / (3.0 * p->c_red);
@@ -231,8 +230,8 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     D.n0 = B.n0;
                     CU(h, cudaMalloc(&h->d_us[b], (size_t)G * D.ncell * 4 * es));
                     D.Us = h->d_us[b];
+                    rtl::transport_layout(D, G);
                     D.titem0 = titem;
-                    D.ntitems = (int64_t)G * D.tiles_x * D.tiles_y * D.zchunks;
                     titem += D.ntitems;
                     D.citem0 = citem;
                     D.ncitems = (D.ncell + RTD_CHEM_BLOCK - 1) / RTD_CHEM_BLOCK;
@@ -244,6 +243,15 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * nboxes,
                                  cudaMemcpyHostToDevice));
                 CU(h, cudaMalloc(&h->d_partials, sizeof(double) * RTD_NDIAG * citem));
+                if (!p->rates_const) {
+                    std::vector<double> tab(rtl::rate_table_doubles());
+                    if (rtl::build_rate_table(p->ots != 0, tab.data())) {
+                        CU(h, cudaMalloc(&h->d_rtab, sizeof(double) * tab.size()));
+                        CU(h, cudaMemcpy(h->d_rtab, tab.data(), sizeof(double) * tab.size(),
+                                         cudaMemcpyHostToDevice));
+                        h->ph.rtab = h->d_rtab;
+                    }
+                }
                 CU(h, cudaMalloc(&h->d_lastdiag, sizeof(double) * RTD_NDIAG * nboxes));
                 CU(h, cudaMemset(h->d_lastdiag, 0, sizeof(double) * RTD_NDIAG * nboxes));
                 CU(h, cudaMalloc(&h->d_ctl, sizeof(rtd::Ctl)));
@@ -255,7 +263,8 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
                 const int to = rtl::transport_occupancy(fp64, h->strict);
                 const int co = rtl::chem_occupancy(fp64, h->strict, G);
-                h->tgrid = (int)std::min<int64_t>(titem, (int64_t)to * nsm);
+                // transport: at least 4 planes per block (each run re-reads 2)
+                h->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((titem + 3) / 4, (int64_t)to * nsm));
                 h->cgrid = (int)std::min<int64_t>(citem, (int64_t)co * nsm);
                 return RT_OK;
             }()))

@@ -22,6 +22,14 @@
 
 #define RTD_MAXCYC 1000000   // sub-cycles per cell and step before giving up
 
+// rate tables: piecewise polynomials in ll = ln(2 T_HI / T) on equal
+// intervals covering 1 K <= T <= 1e9 K (see rate_table.cu)
+#define RTD_TAB_NF 5         // aA, aB, kR, ln(beta) + lambda/2, ln(cce) + 118348/T
+#define RTD_TAB_NINT 128
+#define RTD_TAB_NC 11        // degree 10 in the local variable t in [-1, 1]
+#define RTD_TAB_LL0 (-8.1)
+#define RTD_TAB_H 0.1625
+
 namespace rtd {
 
 // physical constants (cgs)
@@ -39,13 +47,14 @@ struct Phys {
     double alphaA, alphaB, beta;  // rates_const values
     double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250
     double ln2THI;                // ln(2 T_HI)
+    const double *rtab;           // rate table [RTD_TAB_NF][RTD_TAB_NINT][RTD_TAB_NC] or null
     int bc[6];                    // -x,+x,-y,+y,-z,+z
 };
 
 // One box (array in device memory, indexed by work items).
 struct BoxDev {
     int nx, ny, nz;
-    int tiles_x, tiles_y, zchunks;   // transport tiling
+    int tiles_x, tiles_y, zchunks;   // transport tiling (zchunks unused: runs are balanced)
     int64_t ncell;
     double dx, nunit, dt, lam;        // lam = c dt / dx (Courant number)
     void *U;                          // caller's state, [G][nz][ny][nx][4]
@@ -55,7 +64,7 @@ struct BoxDev {
     const int64_t *src_cell;          // sorted unique source cells (nsrc)
     const double *src_S;              // [nsrc][G] source term, stored units per second
     int nsrc;
-    int64_t titem0, ntitems;          // transport work items of this box
+    int64_t titem0, ntitems;          // transport plane units of this box (prefix, count)
     int64_t citem0, ncitems;          // chemistry work items of this box
 };
 

@@ -155,132 +155,203 @@ __device__ __forceinline__ int find_box(const BoxDev *boxes, int nboxes, int64_t
 }
 
 // ------------------------------------------------------------- transport
-// One work item = (box, group, z-chunk, y-tile, x-tile).  A block of
-// TX x TY threads owns TX x TY columns and marches through the z-chunk:
-// the plane z (with its x/y halo) is staged in shared memory, each cell's
-// closure is evaluated once per plane, the z-face flux is carried in
-// registers from one plane to the next (each z-face evaluated once).
+// cp.async (16-byte global -> shared copies, completion tracked per thread in
+// commit groups)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename R>
+__device__ __forceinline__ void cp_cell(V4<R> *dst, const V4<R> *src)
+{
+    if (sizeof(V4<R>) == 16) {
+        cp_async16(dst, src);
+    } else {
+        cp_async16(dst, src);
+        cp_async16(reinterpret_cast<char *>(dst) + 16, reinterpret_cast<const char *>(src) + 16);
+    }
+}
+
+// Shared-memory layout of the transport pipeline: a ring of TP_STAGES planes
+// of U over the (TY+2) x (TX+2) tile-with-halo, and two planes of the closure
+// P (the plane being updated and the next one).
+constexpr int TP_STAGES = 5;
+constexpr int TP_W = RTD_TX + 2, TP_H = RTD_TY + 2;
+
+template <typename R>
+struct TransportSmem {
+    V4<R> U[TP_STAGES][TP_H][TP_W];
+    R P[2][6][TP_H][TP_W];
+};
+
+template <typename R>
+constexpr size_t transport_smem_bytes() { return sizeof(TransportSmem<R>); }
+
+// Work is counted in plane units: (box, group, y-tile, x-tile, z), z
+// fastest.  Block b of a grid of n takes the units [b U/n, (b+1) U/n) and
+// splits them into runs of consecutive planes of one column of tiles, so
+// every block carries the same number of planes whatever the box sizes.
+// For a run z0..z1-1, a block of TX x TY threads owns TX x TY columns:
+// planes q = 0..L-1 (z = z0-1 .. z1) stream into a TP_STAGES-deep ring of
+// shared memory by cp.async, TP_STAGES-2 planes ahead of the plane being
+// updated, with the x/y halo (periodic halos from the wrapped cells, ghost
+// halos copied from the boundary cell and, for reflective faces, the normal
+// flux negated in shared memory).  Each cell's closure is evaluated once per
+// plane; a thread updates plane q-1 as soon as plane q's closures are
+// written (its own cell's closure of plane q stays in registers), so one
+// barrier per plane separates the phases.  The z-face flux is carried in
+// registers (each z-face evaluated once).
 // Update (Eq. e:uprt, unsplit): U* = U - lam ((dPhi_x + dPhi_y) + dPhi_z).
+__device__ __forceinline__ int find_box_unit(const BoxDev *boxes, int nboxes, int64_t unit)
+{
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].titem0 <= unit) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <typename R, bool STRICT>
 __global__ void __launch_bounds__(RTD_TX *RTD_TY)
-k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, int zc, Phys ph,
+k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*unused*/, Phys ph,
             Ctl *ctl)
 {
-    constexpr int TX = RTD_TX, TY = RTD_TY;
-    __shared__ V4<R> sU[TY + 2][TX + 2];
-    __shared__ R sP[6][TY + 2][TX + 2];
+    constexpr int TX = RTD_TX, TY = RTD_TY, S = TP_STAGES;
+    extern __shared__ __align__(16) unsigned char tp_smem_raw[];
+    TransportSmem<R> &sm = *reinterpret_cast<TransportSmem<R> *>(tp_smem_raw);
 
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    if (blockIdx.x == 0 && tx == 0 && ty == 0) ctl->step += 1;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
 
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int b = find_box(boxes, nboxes, it, false);
+    const int64_t ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
+    const int64_t uend = nunits * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    for (int64_t u = ubeg; u < uend;) {
+        const int b = find_box_unit(boxes, nboxes, u);
         const BoxDev &B = boxes[b];
-        int64_t loc = it - B.titem0;
-        const int ix = (int)(loc % B.tiles_x); loc /= B.tiles_x;
-        const int iy = (int)(loc % B.tiles_y); loc /= B.tiles_y;
-        const int iz = (int)(loc % B.zchunks);
-        const int g = (int)(loc / B.zchunks);
         const int nx = B.nx, ny = B.ny, nz = B.nz;
-        const int x = ix * TX + tx, y = iy * TY + ty;
-        const bool act = (x < nx) && (y < ny);
-        const int z0 = iz * zc, z1 = min(z0 + zc, nz);
+        const int64_t loc = u - B.titem0;
+        int64_t colid = loc / nz;
+        const int z0 = (int)(loc - colid * nz);
+        const int64_t zlim = (int64_t)z0 + (uend - u);
+        const int z1 = zlim < (int64_t)nz ? (int)zlim : nz;
+        u += z1 - z0;
+        const int ix = (int)(colid % B.tiles_x); colid /= B.tiles_x;
+        const int iy = (int)(colid % B.tiles_y);
+        const int g = (int)(colid / B.tiles_y);
+        const int x0 = ix * TX, y0 = iy * TY;
+        const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
+        const int x = x0 + tx, y = y0 + ty;
+        const bool act = (tx < ntx) && (ty < nty);
+        const int L = (z1 - z0) + 2;                       // planes z0-1 .. z1
         const V4<R> *Ug = reinterpret_cast<const V4<R> *>(B.U) + (int64_t)g * B.ncell;
         V4<R> *Og = reinterpret_cast<V4<R> *>(B.Us) + (int64_t)g * B.ncell;
         const R lam = (R)B.lam;
         const int64_t sxy = (int64_t)nx * ny;
 
-        V4<R> uc = {}, un = {};
-        R Pc[6], Pn[6], Fzm[4];
-        if (act) {
-            const int64_t col = (int64_t)y * nx + x;
-            uc = ld4(Ug + z0 * sxy + col);
-            V4<R> up;
-            if (z0 > 0) up = ld4(Ug + (z0 - 1) * sxy + col);
-            else if (ph.bc[4] == 0) up = ld4(Ug + (nz - 1) * sxy + col);
-            else up = ghost_of(uc, ph.bc[4], 2);
-            R Pp[6];
-            closure<R, STRICT>(up, Pp);
-            closure<R, STRICT>(uc, Pc);
-            glf<R, 2>(up, Pp, uc, Pc, Fzm);
-        }
-        for (int z = z0; z < z1; z++) {
-            const int64_t pl = (int64_t)z * sxy;
-            if (act) {
-                const int64_t col = (int64_t)y * nx + x;
-                if (z + 1 < nz) un = ld4(Ug + pl + sxy + col);
-                else if (ph.bc[5] == 0) un = ld4(Ug + col);
-                else un = ghost_of(uc, ph.bc[5], 2);
-                closure<R, STRICT>(un, Pn);
-
-                sU[ty + 1][tx + 1] = uc;
-#pragma unroll
-                for (int k = 0; k < 6; k++) sP[k][ty + 1][tx + 1] = Pc[k];
-                // x halo
-                if (tx == 0) {
-                    V4<R> h;
-                    if (x > 0) h = ld4(Ug + pl + (int64_t)y * nx + x - 1);
-                    else if (ph.bc[0] == 0) h = ld4(Ug + pl + (int64_t)y * nx + nx - 1);
-                    else h = ghost_of(uc, ph.bc[0], 0);
-                    R Ph[6];
-                    closure<R, STRICT>(h, Ph);
-                    sU[ty + 1][0] = h;
-#pragma unroll
-                    for (int k = 0; k < 6; k++) sP[k][ty + 1][0] = Ph[k];
-                }
-                if (tx == TX - 1 || x == nx - 1) {
-                    V4<R> h;
-                    if (x + 1 < nx) h = ld4(Ug + pl + (int64_t)y * nx + x + 1);
-                    else if (ph.bc[1] == 0) h = ld4(Ug + pl + (int64_t)y * nx);
-                    else h = ghost_of(uc, ph.bc[1], 0);
-                    R Ph[6];
-                    closure<R, STRICT>(h, Ph);
-                    sU[ty + 1][tx + 2] = h;
-#pragma unroll
-                    for (int k = 0; k < 6; k++) sP[k][ty + 1][tx + 2] = Ph[k];
-                }
-                // y halo
-                if (ty == 0) {
-                    V4<R> h;
-                    if (y > 0) h = ld4(Ug + pl + (int64_t)(y - 1) * nx + x);
-                    else if (ph.bc[2] == 0) h = ld4(Ug + pl + (int64_t)(ny - 1) * nx + x);
-                    else h = ghost_of(uc, ph.bc[2], 1);
-                    R Ph[6];
-                    closure<R, STRICT>(h, Ph);
-                    sU[0][tx + 1] = h;
-#pragma unroll
-                    for (int k = 0; k < 6; k++) sP[k][0][tx + 1] = Ph[k];
-                }
-                if (ty == TY - 1 || y == ny - 1) {
-                    V4<R> h;
-                    if (y + 1 < ny) h = ld4(Ug + pl + (int64_t)(y + 1) * nx + x);
-                    else if (ph.bc[3] == 0) h = ld4(Ug + pl + x);
-                    else h = ghost_of(uc, ph.bc[3], 1);
-                    R Ph[6];
-                    closure<R, STRICT>(h, Ph);
-                    sU[ty + 2][tx + 1] = h;
-#pragma unroll
-                    for (int k = 0; k < 6; k++) sP[k][ty + 2][tx + 1] = Ph[k];
-                }
+        // this thread's halo cell (at most one): smem position (hx, hy),
+        // source (sx, sy) inside the box, negated component (0 = none)
+        int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0;
+        {
+            int t = tid;
+            if (t < nty) {                                   // left column
+                hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1;
+                if (sx < 0) { if (ph.bc[0] == 0) sx = nx - 1; else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; } }
+            } else if ((t -= nty) < nty) {                   // right column
+                hx = ntx + 1; hy = t + 1; sy = y0 + t; sx = x0 + ntx;
+                if (sx >= nx) { if (ph.bc[1] == 0) sx = 0; else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; } }
+            } else if ((t -= nty) < ntx) {                   // bottom row
+                hx = t + 1; hy = 0; sx = x0 + t; sy = y0 - 1;
+                if (sy < 0) { if (ph.bc[2] == 0) sy = ny - 1; else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; } }
+            } else if ((t -= ntx) < ntx) {                   // top row
+                hx = t + 1; hy = nty + 1; sx = x0 + t; sy = y0 + nty;
+                if (sy >= ny) { if (ph.bc[3] == 0) sy = 0; else { sy = ny - 1; hneg = ph.bc[3] == 2 ? 2 : 0; } }
             }
-            __syncthreads();
+        }
+        const int64_t own_col = (int64_t)y * nx + x;
+        const int64_t halo_col = (int64_t)sy * nx + sx;
+
+        // plane q of the run: z = z0 - 1 + q, wrapped or clamped at the faces
+        auto src_plane = [&](int q, int &zneg) -> int {
+            int zz = z0 - 1 + q;
+            zneg = 0;
+            if (zz < 0) { if (ph.bc[4] == 0) zz = nz - 1; else { zz = 0; zneg = ph.bc[4] == 2; } }
+            else if (zz >= nz) { if (ph.bc[5] == 0) zz = 0; else { zz = nz - 1; zneg = ph.bc[5] == 2; } }
+            return zz;
+        };
+        auto issue = [&](int q) {
+            if (q < L) {
+                int zneg;
+                const int64_t pl = (int64_t)src_plane(q, zneg) * sxy;
+                const int slot = q % S;
+                if (act) cp_cell(&sm.U[slot][ty + 1][tx + 1], Ug + pl + own_col);
+                if (hx >= 0) cp_cell(&sm.U[slot][hy][hx], Ug + pl + halo_col);
+            }
+            cp_async_commit();
+        };
+
+#pragma unroll
+        for (int q = 0; q < S - 2; q++) issue(q);
+
+        R Fzm[4] = {R(0), R(0), R(0), R(0)};
+        for (int q = 0; q < L; q++) {
+            cp_async_wait<S - 3>();
+            __syncthreads();        // plane q landed everywhere; plane q-1's closures visible;
+                                    // plane q-2 retired (its U slot and P slot are reused)
+            issue(q + S - 2);
+            const int slot = q % S, pslot = q & 1;
+            int zneg;
+            src_plane(q, zneg);
+            R Pn[6];
+            V4<R> un = {};
             if (act) {
+                V4<R> &uref = sm.U[slot][ty + 1][tx + 1];
+                if (zneg) uref.w = -uref.w;                // reflective z ghost plane
+                un = uref;
+                closure<R, STRICT>(un, Pn);
+#pragma unroll
+                for (int k = 0; k < 6; k++) sm.P[pslot][k][ty + 1][tx + 1] = Pn[k];
+            }
+            if (hx >= 0) {
+                V4<R> &h = sm.U[slot][hy][hx];
+                if (zneg) h.w = -h.w;
+                if (hneg == 1) h.y = -h.y;
+                else if (hneg == 2) h.z = -h.z;
+                R Ph[6];
+                closure<R, STRICT>(h, Ph);
+#pragma unroll
+                for (int k = 0; k < 6; k++) sm.P[pslot][k][hy][hx] = Ph[k];
+            }
+            if (q == 0 || !act) continue;
+            // update plane c = q - 1 (z = z0 + q - 2) unless c is the ghost plane 0
+            const int c = q - 1, cs = c % S, cp = c & 1;
+            const V4<R> uc = sm.U[cs][ty + 1][tx + 1];
+            R Pc[6];
+#pragma unroll
+            for (int k = 0; k < 6; k++) Pc[k] = sm.P[cp][k][ty + 1][tx + 1];
+            R Fzp[4];
+            glf<R, 2>(uc, Pc, un, Pn, Fzp);
+            if (c >= 1) {
                 R Pl[6], Pr[6], Pd[6], Pu[6];
 #pragma unroll
                 for (int k = 0; k < 6; k++) {
-                    Pl[k] = sP[k][ty + 1][tx];
-                    Pr[k] = sP[k][ty + 1][tx + 2];
-                    Pd[k] = sP[k][ty][tx + 1];
-                    Pu[k] = sP[k][ty + 2][tx + 1];
+                    Pl[k] = sm.P[cp][k][ty + 1][tx];
+                    Pr[k] = sm.P[cp][k][ty + 1][tx + 2];
+                    Pd[k] = sm.P[cp][k][ty][tx + 1];
+                    Pu[k] = sm.P[cp][k][ty + 2][tx + 1];
                 }
-                const V4<R> ul = sU[ty + 1][tx], ur = sU[ty + 1][tx + 2];
-                const V4<R> ud = sU[ty][tx + 1], uu = sU[ty + 2][tx + 1];
-                R Fxm[4], Fxp[4], Fym[4], Fyp[4], Fzp[4];
+                const V4<R> ul = sm.U[cs][ty + 1][tx], ur = sm.U[cs][ty + 1][tx + 2];
+                const V4<R> ud = sm.U[cs][ty][tx + 1], uu = sm.U[cs][ty + 2][tx + 1];
+                R Fxm[4], Fxp[4], Fym[4], Fyp[4];
                 glf<R, 0>(ul, Pl, uc, Pc, Fxm);
                 glf<R, 0>(uc, Pc, ur, Pr, Fxp);
                 glf<R, 1>(ud, Pd, uc, Pc, Fym);
                 glf<R, 1>(uc, Pc, uu, Pu, Fyp);
-                glf<R, 2>(uc, Pc, un, Pn, Fzp);
                 R o[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) {
@@ -288,15 +359,15 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, int zc
                     const R dyf = Fyp[m] - Fym[m];
                     const R dzf = Fzp[m] - Fzm[m];
                     o[m] = comp(uc, m) - lam * ((dxf + dyf) + dzf);
-                    Fzm[m] = Fzp[m];
                 }
-                st4(Og + pl + (int64_t)y * nx + x, V4<R>{o[0], o[1], o[2], o[3]});
-                uc = un;
-#pragma unroll
-                for (int k = 0; k < 6; k++) Pc[k] = Pn[k];
+                const int z = z0 + c - 1;
+                st4(Og + (int64_t)z * sxy + own_col, V4<R>{o[0], o[1], o[2], o[3]});
             }
-            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < 4; m++) Fzm[m] = Fzp[m];
         }
+        cp_async_wait<0>();
+        __syncthreads();                                   // ring free for the next run
     }
 }
 
@@ -340,6 +411,39 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
     const double cce = 7.5e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1.0e5));
     r.kR = crec + cff;
     r.kC = cci + cce;
+    return r;
+}
+
+// The same rates from the tables built at set-up (rate_table.cu): Chebyshev
+// interpolants of degree 10 on 128 intervals of ll = ln(2 T_HI/T), accurate
+// to ~1e-15 relative; beta and the excitation cooling keep their
+// exp(-c/T) factor exact.  Outside 1 K .. 1e9 K the fits are evaluated directly.
+__device__ __forceinline__ Rates rates_tab(const Phys &ph, const double *tab, double T)
+{
+    const double invT = 1.0 / T;
+    const double lam = (2.0 * rtd::T_HI) * invT;
+    const double ll = log(lam);
+    const double u = (ll - RTD_TAB_LL0) * (1.0 / RTD_TAB_H);
+    if (!(u >= 0.0 && u < (double)RTD_TAB_NINT)) return rates_at(ph, T);
+    const int j = (int)u;
+    const double t = 2.0 * (u - (double)j) - 1.0;
+    double g[RTD_TAB_NF];
+#pragma unroll
+    for (int f = 0; f < RTD_TAB_NF; f++) {
+        if (f == 0 && ph.ots) { g[0] = 0.0; continue; }
+        const double *a = tab + (f * RTD_TAB_NINT + j) * RTD_TAB_NC;
+        double p = a[RTD_TAB_NC - 1];
+#pragma unroll
+        for (int i = RTD_TAB_NC - 2; i >= 0; i--) p = p * t + a[i];
+        g[f] = p;
+    }
+    Rates r;
+    r.aB = g[1];
+    r.aA = ph.ots ? g[1] : g[0];
+    r.kR = g[2];
+    r.beta = exp(g[3] - 0.5 * lam);
+    const double cce = exp(g[4] - 118348.0 * invT);
+    r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
     return r;
 }
 
@@ -413,14 +517,14 @@ __device__ __forceinline__ void chem_trial(const Phys &ph, double nunit, double 
 // |e/(H - Lambda)|) when use_est (adaptive), halved while the energy changes
 // by more than 10% (Sec. 2.2.4, after Rosdahl et al. 2013)
 template <int G, bool STRICT>
-__device__ unsigned int chem_span(const Phys &ph, double nunit, double n0, const double *S,
-                                  Cell<G> &s, double span, bool use_est, int &ncyc)
+__device__ unsigned int chem_span(const Phys &ph, const double *tab, double nunit, double n0,
+                                  const double *S, Cell<G> &s, double span, bool use_est, int &ncyc)
 {
     unsigned int err = 0;
     double tau = 0.0;
     for (;;) {
         const double rem = span - tau;
-        const Rates r = rates_at(ph, s.T);
+        const Rates r = tab ? rates_tab(ph, tab, s.T) : rates_at(ph, s.T);
         const double alpha = ph.ots ? r.aB : r.aA;
         double dtau = rem;
         bool last = true;
@@ -505,6 +609,14 @@ __global__ void __launch_bounds__(RTD_CHEM_BLOCK)
 k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ctl *ctl,
        double *__restrict__ partials)
 {
+    extern __shared__ double s_tab[];
+    const double *tab = nullptr;
+    if (ph.rtab && !ph.rates_const) {
+        for (int i = threadIdx.x; i < RTD_TAB_NF * RTD_TAB_NINT * RTD_TAB_NC; i += blockDim.x)
+            s_tab[i] = ph.rtab[i];
+        __syncthreads();
+        tab = s_tab;
+    }
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int b = find_box(boxes, nboxes, it, true);
         const BoxDev &B = boxes[b];
@@ -515,20 +627,24 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             V4<TU> *U = reinterpret_cast<V4<TU> *>(B.U);
             Cell<G> s;
             unsigned long long nclamp = 0;
+            bool gross = false;
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
                 s.N[i] = (double)u.x;
                 s.F[i][0] = (double)u.y; s.F[i][1] = (double)u.z; s.F[i][2] = (double)u.w;
-                if (s.N[i] > 0.0) {
-                    const double ux = s.F[i][0] / s.N[i], uy = s.F[i][1] / s.N[i],
-                                 uz = s.F[i][2] / s.N[i];
-                    const double f2 = ux * ux + uy * uy + uz * uz;
-                    const double tol = 1.0 + flux_tol<TU>();
+                // flux limit after transport, in the state's own precision;
+                // F is scaled by 1/N first so no square underflows
+                if (u.x > TU(0)) {
+                    const TU rn = TU(1) / u.x;
+                    const TU ux = u.y * rn, uy = u.z * rn, uz = u.w * rn;
+                    const TU f2 = ux * ux + uy * uy + uz * uz;
+                    const TU tol = (TU)(1.0 + flux_tol<TU>());
                     if (f2 > tol * tol) nclamp++;
-                    if (f2 > 1.01 * 1.01) atomicOr(&ctl->err, RTD_ERR_REALIZ);
+                    if (f2 > TU(1.01 * 1.01)) gross = true;
                 }
             }
+            if (gross) atomicOr(&ctl->err, RTD_ERR_REALIZ);
             if (nclamp) atomicAdd(&ctl->nclamp, nclamp);
             s.xHI = B.xHI[c];
             s.T = B.T[c];
@@ -552,30 +668,31 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (ph.nsub > 0) {
                 const double h = B.dt / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    err |= chem_span<G, STRICT>(ph, B.nunit, n0, S, s, h, false, ncyc);
+                    err |= chem_span<G, STRICT>(ph, tab, B.nunit, n0, S, s, h, false, ncyc);
             } else {
-                err |= chem_span<G, STRICT>(ph, B.nunit, n0, S, s, B.dt, true, ncyc);
+                err |= chem_span<G, STRICT>(ph, tab, B.nunit, n0, S, s, B.dt, true, ncyc);
             }
             if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
             if (err) atomicOr(&ctl->err, err);
-            double ph_tot = 0.0, fmax = 0.0;
+            double ph_tot = 0.0;
+            TU f2max = TU(0);                  // largest |F/N|^2 of the cell's groups
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 const V4<TU> o = {(TU)s.N[i], (TU)s.F[i][0], (TU)s.F[i][1], (TU)s.F[i][2]};
                 st4(U + (int64_t)i * B.ncell + c, o);
-                const double N = (double)o.x;
-                ph_tot += N;
-                if (N > 0.0) {
-                    const double ux = (double)o.y / N, uy = (double)o.z / N, uz = (double)o.w / N;
-                    const double f = sqrt(ux * ux + uy * uy + uz * uz);
-                    fmax = fmax > f ? fmax : f;
+                ph_tot += (double)o.x;
+                if (o.x > TU(0)) {
+                    const TU rn = TU(1) / o.x;
+                    const TU ux = o.y * rn, uy = o.z * rn, uz = o.w * rn;
+                    const TU f2 = ux * ux + uy * uy + uz * uz;
+                    f2max = f2 > f2max ? f2 : f2max;
                 }
             }
             B.xHI[c] = s.xHI;
             B.T[c] = s.T;
             v[0] = 1.0 - s.xHI;
             v[1] = ph_tot;
-            v[2] = fmax;
+            v[2] = (double)sqrt(f2max);
             v[3] = s.xHI < 0.5 ? 1.0 : 0.0;
             v[4] = (double)ncyc;
         }

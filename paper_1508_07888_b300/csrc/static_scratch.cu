@@ -106,15 +106,12 @@ extern "C" int rt_transport_static(const rt_params *p, const rt_box *box, int ns
         rtd::BoxDev &B = D[k];
         B.nx = box->nx; B.ny = box->ny; B.nz = box->nz;
         B.ncell = ncell;
-        B.tiles_x = (box->nx + RTD_TX - 1) / RTD_TX;
-        B.tiles_y = (box->ny + RTD_TY - 1) / RTD_TY;
-        B.zchunks = (box->nz + 31) / 32;
         B.dx = box->dx;
         B.nunit = box->nunit;
         B.dt = p->cfl * box->dx / (3.0 * p->c_red);
         B.lam = p->c_red * B.dt / box->dx;
+        rtl::transport_layout(B, p->ngroups);
         B.titem0 = 0;
-        B.ntitems = (int64_t)p->ngroups * B.tiles_x * B.tiles_y * B.zchunks;
         B.U = k == 0 ? box->U : (void *)(base + kStateOff);
         B.Us = k == 0 ? (void *)(base + kStateOff) : box->U;
     }

@@ -218,7 +218,7 @@ def time_device(w, precision, K, W, nsteps, ws, profile):
     ms = e0.elapsed_time(e1)
     st = B.rt_query(r.solver.h)
     kern = {name: {"ms_total": st.kernel_ms[j], "launches": int(st.kernel_launches[j])}
-            for j, name in enumerate(B.KERNELS)}
+            for j, name in enumerate(B.KERNELS) if st.kernel_launches[j] > 0}
     diag = list(st.last_diag)
     nbytes = r.state_bytes
     r.close()

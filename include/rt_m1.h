@@ -111,14 +111,18 @@ typedef struct rt_box {
 typedef struct rt_stats {
     int64_t steps;                       /* steps run since rt_create */
     int64_t realizability_clamps;        /* post-transport cells with |F| > cN (1 + tol),
-                                            tol 1e-12 (FP64) or 1e-5 (FP32), summed over steps */
+                                            tol 1e-12 (FP64) or 1e-5 (FP32), summed over steps;
+                                            cells with N <= 1e-290 (FP64) / 1e-30 (FP32) stored
+                                            units are not checked (|F|/N has no digits there) */
     int     error_bits;                  /* OR of device error bits seen (1 nonfinite, 2 realizability,
                                             4 sub-cycle cap) */
     int     nboxes;
     int64_t cells;                       /* cells over all boxes */
     double  last_diag[RT_NDIAG];         /* diagnostics of box 0 after the last step */
     double  kernel_ms[3];                /* with profiling on: summed CUDA-event time of the
-                                            transport, chemistry and diagnostics kernels */
+                                            transport and chemistry kernels; the per-box
+                                            diagnostics run inside the chemistry kernel, so
+                                            the third entry stays 0 */
     int64_t kernel_launches[3];          /* launches timed into kernel_ms */
 } rt_stats;
 

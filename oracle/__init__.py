@@ -127,6 +127,10 @@ def lib():
             "orc_run": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                   _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _i64p]),
             "orc_sigma_HI": (C.c_double, [C.c_double]),
+            "orc_transport_cells": (None, [PP, C.c_int, C.c_int, C.c_int, C.c_double, _dp, C.c_int,
+                                           C.c_int, _i64p, _dp]),
+            "orc_step_cells": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                         _dp, _dp, _dp, _dp, _dp, C.c_int, _i64p, _dp, _dp, _dp]),
             "orc_set_threads": (None, [C.c_int]),
             "orc_get_threads": (C.c_int, []),
             "orc_group_table": (None, [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp]),
@@ -257,6 +261,27 @@ def run(p: Params, U, xHI, T, n0, dx: float, nunit: float, nsteps: int,
     err = lib().orc_run(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
                         _ptr(T), _ptr(n0), Sp, nsteps, _ptr(hist), C.byref(ncl))
     return RunResult(U, xHI, T, hist, err, ncl.value)
+
+
+def step_cells(p: Params, U, xHI, T, n0, dx: float, nunit: float, cells, S=None):
+    """One full step (transport + chemistry) of the listed cells only, from
+    the full state.  Returns (U[ncells, G, 4], xHI[ncells], T[ncells], err)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    xHI = np.ascontiguousarray(xHI, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    n0 = np.ascontiguousarray(n0, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    G, nz, ny, nx, _ = U.shape
+    k = len(cells)
+    Uo = np.zeros((k, G, 4))
+    xo, To = np.zeros(k), np.zeros(k)
+    Sp = None
+    if S is not None:
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        Sp = _ptr(S)
+    err = lib().orc_step_cells(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
+                               _ptr(T), _ptr(n0), Sp, k, _ptr(cells), _ptr(Uo), _ptr(xo), _ptr(To))
+    return Uo, xo, To, err
 
 
 def sigma_HI(E_eV: float) -> float:

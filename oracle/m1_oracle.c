@@ -277,6 +277,40 @@ void orc_transport(const orc_params *p, int nx, int ny, int nz, double lam,
     free(P);
 }
 
+/* Transport of single cells (the same per-cell expression as
+ * orc_transport, with every closure evaluated from its state): post-transport
+ * state of cells cell[0..ncells) of group g, written to out[ncells][4].
+ * Used to check a large grid one sampled cell at a time. */
+void orc_transport_cells(const orc_params *p, int nx, int ny, int nz, double lam, const double *U,
+                         int g, int ncells, const int64_t *cell, double *out)
+{
+    size_t ncell = (size_t)nx * ny * nz;
+    const double *Ug = U + 4 * ncell * g;
+    for (int k = 0; k < ncells; k++) {
+        int64_t id = cell[k];
+        int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((int64_t)nx * ny));
+        const double *Uc = Ug + 4 * id;
+        double Pc[6], diff[3][4];
+        orc_closure(Uc, Pc, NULL, NULL);
+        for (int d = 0; d < 3; d++) {
+            double Gc[4], Us[2][4], Ps[6], Gs[2][4];
+            flux_from(d, Uc, Pc, Gc);
+            for (int side = 0; side < 2; side++) {
+                neighbour(p, Ug, nx, ny, nz, x, y, z, d, side ? +1 : -1, Us[side]);
+                orc_closure(Us[side], Ps, NULL, NULL);
+                flux_from(d, Us[side], Ps, Gs[side]);
+            }
+            for (int m = 0; m < 4; m++) {
+                double Fm = 0.5 * ((Gs[0][m] + Gc[m]) - (Uc[m] - Us[0][m]));
+                double Fp = 0.5 * ((Gc[m] + Gs[1][m]) - (Us[1][m] - Uc[m]));
+                diff[d][m] = Fp - Fm;
+            }
+        }
+        for (int m = 0; m < 4; m++)
+            out[4 * k + m] = Uc[m] - lam * ((diff[0][m] + diff[1][m]) + diff[2][m]);
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* 3a. atomic rates (R8); T in K, results in cgs                        */
 /* ------------------------------------------------------------------ */
@@ -488,6 +522,38 @@ void orc_source_field(const orc_params *p, int64_t ncell, int nsrc, const int64_
     for (int i = 0; i < p->G; i++)
         for (int64_t c = 0; c < ncell; c++)
             S[(size_t)i * ncell + c] = S[(size_t)i * ncell + c] / (vol * nunit);
+}
+
+/* One full step (transport, then chemistry) of the sampled cells only,
+ * from the full state U/xHI/T: Uout[ncells][G][4], xout, Tout[ncells].
+ * S: dense source field [G][ncell] or NULL.  Returns the error bits. */
+int orc_step_cells(const orc_params *p, int nx, int ny, int nz, double dx, double nunit,
+                   const double *U, const double *xHI, const double *T, const double *n0,
+                   const double *S, int ncells, const int64_t *cell,
+                   double *Uout, double *xout, double *Tout)
+{
+    size_t ncell = (size_t)nx * ny * nz;
+    int G = p->G;
+    double dt = orc_timestep(p, dx);
+    double lam = p->c * dt / dx;
+    double *tmp = (double *)malloc(sizeof(double) * 4 * (size_t)ncells);
+    if (!tmp) return -1;
+    for (int i = 0; i < G; i++) {
+        orc_transport_cells(p, nx, ny, nz, lam, U, i, ncells, cell, tmp);
+        for (int k = 0; k < ncells; k++)
+            for (int m = 0; m < 4; m++) Uout[((size_t)k * G + i) * 4 + m] = tmp[4 * k + m];
+    }
+    free(tmp);
+    int err = 0;
+    for (int k = 0; k < ncells; k++) {
+        double Sc[ORC_MAXG];
+        for (int i = 0; i < G; i++) Sc[i] = S ? S[ncell * i + cell[k]] : 0.0;
+        xout[k] = xHI[cell[k]];
+        Tout[k] = T[cell[k]];
+        err |= orc_chem_cell(p, dt, nunit, n0[cell[k]], Sc, Uout + (size_t)k * G * 4, &xout[k],
+                             &Tout[k], NULL);
+    }
+    return err;
 }
 
 /* ------------------------------------------------------------------ */

@@ -79,7 +79,7 @@ class rt_stats(C.Structure):
 EXPORTS = ("rt_create", "rt_set_sources", "rt_step", "rt_upload", "rt_download", "rt_query",
            "rt_set_profiling", "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table",
            "rt_transport_static")
-KERNELS = ("transport", "chemistry", "diagnostics")
+KERNELS = ("transport", "chemistry", "diagnostics")   # diagnostics: fused into chemistry
 
 _lib = None
 

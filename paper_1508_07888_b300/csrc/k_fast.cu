@@ -31,9 +31,16 @@ cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &
         rtk::k_transport<double, false><<<L.grid, blk, rtk::transport_smem_bytes<double>(), L.stream>>>(
             L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
     } else {
-        cudaError_t e = transport_attr<float, false>();
-        if (e != cudaSuccess) return e;
-        rtk::k_transport<float, false><<<L.grid, blk, rtk::transport_smem_bytes<float>(), L.stream>>>(
+        static int done_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (done_dev != dev) {
+            cudaError_t e = cudaFuncSetAttribute(rtk::k_transport_pm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)rtk::transport_pm_smem_bytes());
+            if (e != cudaSuccess) return e;
+            done_dev = dev;
+        }
+        rtk::k_transport_pm<<<L.grid, blk, rtk::transport_pm_smem_bytes(), L.stream>>>(
             L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
     }
     return cudaGetLastError();
@@ -49,38 +56,33 @@ static size_t chem_smem(K kernel, const rtd::Phys &ph)
 }
 
 template <int G>
-static void chem_g(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, double *partials)
+static void chem_g(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, const rtd::DiagBuf &db)
 {
     if (fp64) {
         auto k = rtk::k_chem<G, double, double, false>;
         k<<<L.grid, RTD_CHEM_BLOCK, chem_smem(k, ph), L.stream>>>(L.boxes, L.nboxes, L.nitems, ph,
-                                                                  ctl, partials);
+                                                                  ctl, db);
     } else {
         auto k = rtk::k_chem<G, float, float, false>;
         k<<<L.grid, RTD_CHEM_BLOCK, chem_smem(k, ph), L.stream>>>(L.boxes, L.nboxes, L.nitems, ph,
-                                                                  ctl, partials);
+                                                                  ctl, db);
     }
 }
 
 cudaError_t chem_fast(bool fp64, int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
-                      double *partials)
+                      const rtd::DiagBuf &db)
 {
     switch (G) {
-    case 1: chem_g<1>(fp64, L, ph, ctl, partials); break;
-    case 2: chem_g<2>(fp64, L, ph, ctl, partials); break;
-    case 3: chem_g<3>(fp64, L, ph, ctl, partials); break;
-    case 4: chem_g<4>(fp64, L, ph, ctl, partials); break;
+    case 1: chem_g<1>(fp64, L, ph, ctl, db); break;
+    case 2: chem_g<2>(fp64, L, ph, ctl, db); break;
+    case 3: chem_g<3>(fp64, L, ph, ctl, db); break;
+    case 4: chem_g<4>(fp64, L, ph, ctl, db); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t finalize(const rtd::BoxDev *boxes, int nboxes, const double *partials, rtd::Ctl *ctl,
-                     double *lastdiag, cudaStream_t stream)
-{
-    rtk::k_finalize<<<nboxes, RTD_CHEM_BLOCK, 0, stream>>>(boxes, partials, ctl, lastdiag);
-    return cudaGetLastError();
-}
+
 
 static int occ(const void *f, int threads, size_t smem = 0)
 {
@@ -96,9 +98,9 @@ int transport_occupancy_fast(bool fp64)
         return occ((const void *)rtk::k_transport<double, false>, RTD_TX * RTD_TY,
                    rtk::transport_smem_bytes<double>());
     }
-    transport_attr<float, false>();
-    return occ((const void *)rtk::k_transport<float, false>, RTD_TX * RTD_TY,
-               rtk::transport_smem_bytes<float>());
+    cudaFuncSetAttribute(rtk::k_transport_pm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rtk::transport_pm_smem_bytes());
+    return occ((const void *)rtk::k_transport_pm, RTD_TX * RTD_TY, rtk::transport_pm_smem_bytes());
 }
 
 int chem_occupancy_fast(bool fp64, int G)

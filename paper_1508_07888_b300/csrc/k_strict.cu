@@ -1,7 +1,7 @@
 // k_strict.cu -- instantiations of the FP64 hot-path kernels compiled with
 // --fmad=false: no contraction, IEEE division and square root, operations in
 // the order the source writes them (RT_PREC_FP64_STRICT).
-#define RTK_STRICT_TU 1   // the diagnostics kernel is defined once, in k_fast.cu
+#define RTK_STRICT_TU 1   // the FP32-only kernels are defined once, in k_fast.cu
 #include "launch.h"
 #include "rt_kernels.cuh"
 
@@ -30,7 +30,7 @@ cudaError_t transport_strict(const Launch &L, int zc, const rtd::Phys &ph, rtd::
     return cudaGetLastError();
 }
 
-cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, double *partials)
+cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, const rtd::DiagBuf &db)
 {
     const size_t tb = (ph.rtab && !ph.rates_const) ? rate_table_doubles() * sizeof(double) : 0;
 #define CHEM_G(g)                                                                                \
@@ -38,7 +38,7 @@ cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *c
         if (tb) cudaFuncSetAttribute(rtk::k_chem<g, double, double, true>,                       \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);      \
         rtk::k_chem<g, double, double, true><<<L.grid, RTD_CHEM_BLOCK, tb, L.stream>>>(          \
-            L.boxes, L.nboxes, L.nitems, ph, ctl, partials);                                     \
+            L.boxes, L.nboxes, L.nitems, ph, ctl, db);                                           \
     } while (0)
     switch (G) {
     case 1: CHEM_G(1); break;

@@ -24,11 +24,9 @@ struct Launch {
 cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl);
 cudaError_t transport_strict(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl);
 cudaError_t chem_fast(bool fp64, int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
-                      double *partials);
+                      const rtd::DiagBuf &db);
 cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
-                        double *partials);
-cudaError_t finalize(const rtd::BoxDev *boxes, int nboxes, const double *partials, rtd::Ctl *ctl,
-                     double *lastdiag, cudaStream_t stream);
+                        const rtd::DiagBuf &db);
 
 // transport tiling of a box: x/y tiles and the number of plane units
 // (ngroups x tiles_x x tiles_y x nz) the transport kernel spreads over its grid

@@ -4,8 +4,9 @@
 // C++ exception out.  All device work is ordered on a private non-blocking
 // stream that is joined to the caller's stream with events at the start and
 // end of each call, so the caller may pass the legacy default stream.  The
-// per-step kernel sequence (transport, chemistry, diagnostics) is captured
-// once into a CUDA graph of RT_GRAPH_STEPS steps and replayed.
+// per-step kernel sequence (transport, then chemistry with the diagnostics
+// fused into it) is captured once into a CUDA graph of RT_GRAPH_STEPS steps
+// and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -36,7 +37,8 @@ struct rt_handle {
     std::vector<void *> d_us;                // post-transport scratch per box
     std::vector<int64_t *> d_src_cell;
     std::vector<double *> d_src_S;
-    double *d_partials = nullptr;
+    rtd::DiagPart *d_partials = nullptr;
+    unsigned *d_done = nullptr;              // per-box item counters of the fused reduction
     double *d_rtab = nullptr;                // rate table (null: fits evaluated directly)
     double *d_lastdiag = nullptr;
     rtd::Ctl *d_ctl = nullptr;
@@ -87,6 +89,7 @@ static void release(rt_handle *h)
     for (auto *p : h->d_src_S) cudaFree(p);
     cudaFree(h->d_boxes);
     cudaFree(h->d_partials);
+    cudaFree(h->d_done);
     cudaFree(h->d_rtab);
     cudaFree(h->d_lastdiag);
     cudaFree(h->d_ctl);
@@ -242,7 +245,9 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMalloc(&h->d_boxes, sizeof(rtd::BoxDev) * nboxes));
                 CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * nboxes,
                                  cudaMemcpyHostToDevice));
-                CU(h, cudaMalloc(&h->d_partials, sizeof(double) * RTD_NDIAG * citem));
+                CU(h, cudaMalloc(&h->d_partials, sizeof(rtd::DiagPart) * citem));
+                CU(h, cudaMalloc(&h->d_done, sizeof(unsigned) * nboxes));
+                CU(h, cudaMemset(h->d_done, 0, sizeof(unsigned) * nboxes));
                 if (!p->rates_const) {
                     std::vector<double> tab(rtl::rate_table_doubles());
                     if (rtl::build_rate_table(p->ots != 0, tab.data())) {
@@ -333,24 +338,24 @@ extern "C" int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *ce
     }
 }
 
-// one step of the hot path on stream s: transport, chemistry, diagnostics;
-// ev (profiling) = 4 events recorded before, between and after the kernels
+// one step of the hot path on stream s: transport, then chemistry with the
+// per-box diagnostics fused into it; ev (profiling) = 4 events recorded
+// before, between and after the kernels (the third interval stays empty)
 static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = nullptr)
 {
     rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s};
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
+    const rtd::DiagBuf db{h->d_partials, h->d_done, h->d_lastdiag};
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     e = h->strict ? rtl::transport_strict(Lt, h->zc, h->ph, h->d_ctl)
                   : rtl::transport_fast(h->fp64, Lt, h->zc, h->ph, h->d_ctl);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
-    e = h->strict ? rtl::chem_strict(h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials)
-                  : rtl::chem_fast(h->fp64, h->p.ngroups, Lc, h->ph, h->d_ctl, h->d_partials);
+    e = h->strict ? rtl::chem_strict(h->p.ngroups, Lc, h->ph, h->d_ctl, db)
+                  : rtl::chem_fast(h->fp64, h->p.ngroups, Lc, h->ph, h->d_ctl, db);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
-    e = rtl::finalize(h->d_boxes, h->nboxes, h->d_partials, h->d_ctl, h->d_lastdiag, s);
-    if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -424,7 +429,7 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
     CU(h, cudaStreamSynchronize(h->s));
     if (h->profiling) {
         for (int k = 0; k < nsteps; k++) {
-            for (int j = 0; j < 3; j++) {
+            for (int j = 0; j < 2; j++) {          // transport, chemistry (+ fused diagnostics)
                 float ms = 0.f;
                 CU(h, cudaEventElapsedTime(&ms, h->prof_ev[4 * (size_t)k + j],
                                            h->prof_ev[4 * (size_t)k + j + 1]));

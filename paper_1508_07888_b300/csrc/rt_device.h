@@ -68,6 +68,19 @@ struct BoxDev {
     int64_t citem0, ncitems;          // chemistry work items of this box
 };
 
+// Per-item diagnostic partials of the chemistry kernel and the per-box
+// reduction state (the last item of a box to finish reduces the box).
+struct DiagPart {
+    double X, ph;                     // sum of (1 - xHI), sum of N over groups
+    unsigned long long fbits;         // max |F|/N (bits of a non-negative double)
+    unsigned count, ncyc;             // cells with xHI < 0.5, chemistry sub-cycles
+};
+struct DiagBuf {
+    DiagPart *part;                   // one per chemistry work item
+    unsigned *done;                   // per box: items finished in this step
+    double *last;                     // per box: RTD_NDIAG values of the last step
+};
+
 // Per-call control block in device memory.
 struct Ctl {
     double *hist;                     // caller's [step][box][RTD_NDIAG] or nullptr

@@ -21,6 +21,8 @@ namespace rtk {
 
 using rtd::BoxDev;
 using rtd::Ctl;
+using rtd::DiagBuf;
+using rtd::DiagPart;
 using rtd::Phys;
 
 // ------------------------------------------------------------- vector I/O
@@ -371,6 +373,201 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
     }
 }
 
+#ifndef RTK_STRICT_TU
+// FP32 closure with the MUFU reciprocal / reciprocal square root (~1-2 ulp):
+// P = N D as in closure(); N below 1e-37 (FP32 denormals) gives P = 0, an
+// absolute change below 1e-37 of a state whose scale is O(1).
+__device__ __forceinline__ void closure_fast(const V4<float> &u, float P[6])
+{
+    const float N = u.x;
+    if (N > 1e-37f) {
+        const float rN = __fdividef(1.0f, N);
+        float ux = u.y * rN, uy = u.z * rN, uz = u.w * rN;
+        float f2 = ux * ux + uy * uy + uz * uz;
+        if (f2 > 1.0f) {
+            const float rf = rsqrtf(f2);
+            ux *= rf; uy *= rf; uz *= rf;
+            f2 = 1.0f;
+        }
+        const float q = 4.0f - 3.0f * f2;
+        const float s = q * rsqrtf(q);
+        const float r5 = __fdividef(1.0f, 5.0f + 2.0f * s);
+        const float a = ((1.0f + s) - 2.0f * f2) * r5;
+        const float g = (6.0f + __fdividef(3.0f, 2.0f + s)) * r5;
+        P[0] = N * (a + g * (ux * ux));
+        P[1] = N * (g * (ux * uy));
+        P[2] = N * (g * (ux * uz));
+        P[3] = N * (a + g * (uy * uy));
+        P[4] = N * (g * (uy * uz));
+        P[5] = N * (a + g * (uz * uz));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; k++) P[k] = 0.0f;
+    }
+}
+
+// right- and left-going halves of the GLF flux along d: Rg = U + G_d(U),
+// Lf = U - G_d(U); the face flux between L and R is (Rg(L) - Lf(R)) / 2
+template <int d>
+__device__ __forceinline__ void halves(const V4<float> &u, const float P[6], float4 &Rg, float4 &Lf)
+{
+    const float g0 = comp(u, 1 + d), g1 = P[pidx(d, 0)], g2 = P[pidx(d, 1)], g3 = P[pidx(d, 2)];
+    Rg = make_float4(u.x + g0, u.y + g1, u.z + g2, u.w + g3);
+    Lf = make_float4(u.x - g0, u.y - g1, u.z - g2, u.w - g3);
+}
+
+struct TransportSmemPM {
+    V4<float> U[TP_STAGES][TP_H][TP_W];
+    float4 H[2][4][TP_H][TP_W];        // per cell: Rx, Lx, Ry, Ly of two planes
+};
+
+constexpr size_t transport_pm_smem_bytes() { return sizeof(TransportSmemPM); }
+
+// FP32 transport of the split form.  Same pipeline and work split as
+// k_transport; the unsplit GLF update is evaluated in its convex form
+//   U* = (1 - 3 lam) U + (lam/2) sum_d [ (U + G_d)(left_d) + (U - G_d)(right_d) ],
+// which equals U - lam sum_d (Phi_{d,+} - Phi_{d,-}) with Phi of Eq. e:glf.
+// Each cell computes its halves once per plane; x/y neighbours read them from
+// shared memory, the z halves stay in registers.
+__global__ void __launch_bounds__(RTD_TX *RTD_TY)
+k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
+{
+    constexpr int TX = RTD_TX, TY = RTD_TY, S = TP_STAGES;
+    extern __shared__ __align__(16) unsigned char tp_smem_raw[];
+    TransportSmemPM &sm = *reinterpret_cast<TransportSmemPM *>(tp_smem_raw);
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
+
+    const int64_t ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
+    const int64_t uend = nunits * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    for (int64_t u = ubeg; u < uend;) {
+        const int b = find_box_unit(boxes, nboxes, u);
+        const BoxDev &B = boxes[b];
+        const int nx = B.nx, ny = B.ny, nz = B.nz;
+        const int64_t loc = u - B.titem0;
+        int64_t colid = loc / nz;
+        const int z0 = (int)(loc - colid * nz);
+        const int64_t zlim = (int64_t)z0 + (uend - u);
+        const int z1 = zlim < (int64_t)nz ? (int)zlim : nz;
+        u += z1 - z0;
+        const int ix = (int)(colid % B.tiles_x); colid /= B.tiles_x;
+        const int iy = (int)(colid % B.tiles_y);
+        const int g = (int)(colid / B.tiles_y);
+        const int x0 = ix * TX, y0 = iy * TY;
+        const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
+        const int x = x0 + tx, y = y0 + ty;
+        const bool act = (tx < ntx) && (ty < nty);
+        const int L = (z1 - z0) + 2;
+        const V4<float> *Ug = reinterpret_cast<const V4<float> *>(B.U) + (int64_t)g * B.ncell;
+        V4<float> *Og = reinterpret_cast<V4<float> *>(B.Us) + (int64_t)g * B.ncell;
+        const float lam = (float)B.lam;
+        const float c0 = 1.0f - 3.0f * lam, c1 = 0.5f * lam;
+        const int64_t sxy = (int64_t)nx * ny;
+
+        // halo cell of this thread and which half of it the tile needs:
+        // 0 = Rx (left column), 1 = Lx (right), 2 = Ry (bottom), 3 = Ly (top)
+        int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0, hk = 0;
+        {
+            int t = tid;
+            if (t < nty) {
+                hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1; hk = 0;
+                if (sx < 0) { if (ph.bc[0] == 0) sx = nx - 1; else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; } }
+            } else if ((t -= nty) < nty) {
+                hx = ntx + 1; hy = t + 1; sy = y0 + t; sx = x0 + ntx; hk = 1;
+                if (sx >= nx) { if (ph.bc[1] == 0) sx = 0; else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; } }
+            } else if ((t -= nty) < ntx) {
+                hx = t + 1; hy = 0; sx = x0 + t; sy = y0 - 1; hk = 2;
+                if (sy < 0) { if (ph.bc[2] == 0) sy = ny - 1; else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; } }
+            } else if ((t -= ntx) < ntx) {
+                hx = t + 1; hy = nty + 1; sx = x0 + t; sy = y0 + nty; hk = 3;
+                if (sy >= ny) { if (ph.bc[3] == 0) sy = 0; else { sy = ny - 1; hneg = ph.bc[3] == 2 ? 2 : 0; } }
+            }
+        }
+        const int64_t own_col = (int64_t)y * nx + x;
+        const int64_t halo_col = (int64_t)sy * nx + sx;
+        auto src_plane = [&](int q, int &zneg) -> int {
+            int zz = z0 - 1 + q;
+            zneg = 0;
+            if (zz < 0) { if (ph.bc[4] == 0) zz = nz - 1; else { zz = 0; zneg = ph.bc[4] == 2; } }
+            else if (zz >= nz) { if (ph.bc[5] == 0) zz = 0; else { zz = nz - 1; zneg = ph.bc[5] == 2; } }
+            return zz;
+        };
+        auto issue = [&](int q) {
+            if (q < L) {
+                int zneg;
+                const int64_t pl = (int64_t)src_plane(q, zneg) * sxy;
+                const int slot = q % S;
+                if (act) cp_async16(&sm.U[slot][ty + 1][tx + 1], Ug + pl + own_col);
+                if (hx >= 0) cp_async16(&sm.U[slot][hy][hx], Ug + pl + halo_col);
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int q = 0; q < S - 2; q++) issue(q);
+
+        V4<float> uc = {};                  // own cell of plane q-1
+        float4 Rz_prev = {}, Rz_c = {};     // right-going z halves of planes q-2 and q-1
+        for (int q = 0; q < L; q++) {
+            cp_async_wait<S - 3>();
+            __syncthreads();
+            issue(q + S - 2);
+            const int slot = q % S, hs = q & 1;
+            int zneg;
+            src_plane(q, zneg);
+            V4<float> un = {};
+            float4 Rz_n = {}, Lz_n = {};
+            if (act) {
+                un = sm.U[slot][ty + 1][tx + 1];
+                if (zneg) un.w = -un.w;
+                float P[6];
+                closure_fast(un, P);
+                float4 Rx, Lx, Ry, Ly;
+                halves<0>(un, P, Rx, Lx);
+                halves<1>(un, P, Ry, Ly);
+                halves<2>(un, P, Rz_n, Lz_n);
+                sm.H[hs][0][ty + 1][tx + 1] = Rx;
+                sm.H[hs][1][ty + 1][tx + 1] = Lx;
+                sm.H[hs][2][ty + 1][tx + 1] = Ry;
+                sm.H[hs][3][ty + 1][tx + 1] = Ly;
+            }
+            if (hx >= 0) {
+                V4<float> h = sm.U[slot][hy][hx];
+                if (zneg) h.w = -h.w;
+                if (hneg == 1) h.y = -h.y;
+                else if (hneg == 2) h.z = -h.z;
+                float P[6];
+                closure_fast(h, P);
+                float4 Rg, Lf;
+                if (hk < 2) halves<0>(h, P, Rg, Lf);
+                else halves<1>(h, P, Rg, Lf);
+                sm.H[hs][hk][hy][hx] = (hk & 1) ? Lf : Rg;
+            }
+            if (act && q >= 2) {
+                // update plane c = q - 1 (z = z0 + q - 2)
+                const int cs = (q - 1) & 1;
+                const float4 l = sm.H[cs][0][ty + 1][tx];        // Rx of the left cell
+                const float4 r = sm.H[cs][1][ty + 1][tx + 2];    // Lx of the right cell
+                const float4 d = sm.H[cs][2][ty][tx + 1];        // Ry of the cell below
+                const float4 p = sm.H[cs][3][ty + 2][tx + 1];    // Ly of the cell above
+                const float sx_ = ((l.x + r.x) + (d.x + p.x)) + (Rz_prev.x + Lz_n.x);
+                const float sy_ = ((l.y + r.y) + (d.y + p.y)) + (Rz_prev.y + Lz_n.y);
+                const float sz_ = ((l.z + r.z) + (d.z + p.z)) + (Rz_prev.z + Lz_n.z);
+                const float sw_ = ((l.w + r.w) + (d.w + p.w)) + (Rz_prev.w + Lz_n.w);
+                const V4<float> o = {c0 * uc.x + c1 * sx_, c0 * uc.y + c1 * sy_,
+                                     c0 * uc.z + c1 * sz_, c0 * uc.w + c1 * sw_};
+                st4(Og + (int64_t)(z0 + q - 2) * sxy + own_col, o);
+            }
+            Rz_prev = Rz_c;
+            Rz_c = Rz_n;
+            uc = un;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+}
+#endif  // RTK_STRICT_TU
+
 // ------------------------------------------------------------- rates
 // Temperature fits (cgs).  Recombination, collisional ionisation and
 // recombination cooling: Hui & Gnedin (1997) fits in lambda = 2 T_HI / T;
@@ -567,48 +764,95 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, double nuni
 template <typename R> __device__ __forceinline__ double flux_tol();
 template <> __device__ __forceinline__ double flux_tol<float>() { return 1e-5; }
 template <> __device__ __forceinline__ double flux_tol<double>() { return 1e-12; }
+// smallest N at which |F|/N is meaningful in the stored precision: below it
+// N is denormal or near it (FP32 keeps < 24 bits there and 1/N overflows)
+template <typename R> __device__ __forceinline__ R flux_nmin();
+template <> __device__ __forceinline__ float flux_nmin<float>() { return 1e-30f; }
+template <> __device__ __forceinline__ double flux_nmin<double>() { return 1e-290; }
 
 __device__ __forceinline__ double ldn(const float *p, int64_t i) { return (double)p[i]; }
 __device__ __forceinline__ double ldn(const double *p, int64_t i) { return p[i]; }
 
-// warp + block reduction of RTD_NDIAG values (sum, sum, max, sum, sum), fixed order
-__device__ __forceinline__ void block_reduce_diag(double v[RTD_NDIAG], double *out)
+// Block reduction of one thread's diagnostics, fixed order: two FP64 sums
+// by warp shuffles then warp order; the max and the counts on the integer
+// path.  Result valid in thread 0.
+struct DiagAcc {
+    double X, ph;
+    unsigned long long fbits, count, ncyc;
+};
+
+__device__ __forceinline__ DiagAcc block_reduce_diag(DiagAcc a)
 {
-    __shared__ double red[RTD_CHEM_BLOCK / 32][RTD_NDIAG];
+    __shared__ DiagAcc red[32];
 #pragma unroll
-    for (int k = 0; k < RTD_NDIAG; k++) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double o = __shfl_down_sync(0xffffffffu, v[k], off);
-            v[k] = (k == 2) ? fmax(v[k], o) : v[k] + o;
-        }
+    for (int off = 16; off > 0; off >>= 1) {
+        a.X += __shfl_down_sync(0xffffffffu, a.X, off);
+        a.ph += __shfl_down_sync(0xffffffffu, a.ph, off);
+        const unsigned long long f = __shfl_down_sync(0xffffffffu, a.fbits, off);
+        a.fbits = f > a.fbits ? f : a.fbits;
+        a.count += __shfl_down_sync(0xffffffffu, a.count, off);
+        a.ncyc += __shfl_down_sync(0xffffffffu, a.ncyc, off);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < RTD_NDIAG; k++) red[wid][k] = v[k];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) red[wid] = a;
     __syncthreads();
     if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < RTD_NDIAG; k++) {
-            double a = red[0][k];
-            for (int w = 1; w < RTD_CHEM_BLOCK / 32; w++)
-                a = (k == 2) ? fmax(a, red[w][k]) : a + red[w][k];
-            out[k] = a;
+        for (int w = 1; w < nw; w++) {
+            a.X += red[w].X;
+            a.ph += red[w].ph;
+            a.fbits = red[w].fbits > a.fbits ? red[w].fbits : a.fbits;
+            a.count += red[w].count;
+            a.ncyc += red[w].ncyc;
         }
     }
     __syncthreads();
+    return a;
+}
+
+// Items of box b are all reduced: sum its partials in a fixed order and
+// write the step's diagnostics (ionised fraction, photons, max f,
+// n(xHI < 0.5), mean sub-cycles) into lastdiag and the caller's history.
+__device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf &db, Ctl *ctl)
+{
+    DiagAcc a = {0.0, 0.0, 0ull, 0ull, 0ull};
+    const DiagPart *p = db.part + B.citem0;
+    for (int64_t i = threadIdx.x; i < B.ncitems; i += blockDim.x) {
+        a.X += __ldcg(&p[i].X);
+        a.ph += __ldcg(&p[i].ph);
+        const unsigned long long f = __ldcg(&p[i].fbits);
+        a.fbits = f > a.fbits ? f : a.fbits;
+        a.count += __ldcg(&p[i].count);
+        a.ncyc += __ldcg(&p[i].ncyc);
+    }
+    a = block_reduce_diag(a);
+    if (threadIdx.x == 0) {
+        const double nc = (double)B.ncell;
+        double d[RTD_NDIAG];
+        d[0] = a.X / nc;
+        d[1] = a.ph * B.nunit * (B.dx * B.dx * B.dx);
+        d[2] = __longlong_as_double((long long)a.fbits);
+        d[3] = (double)a.count;
+        d[4] = (double)a.ncyc / nc;
+        for (int k = 0; k < RTD_NDIAG; k++) db.last[b * RTD_NDIAG + k] = d[k];
+        if (ctl->hist) {
+            double *h = ctl->hist + ((int64_t)ctl->step * ctl->nboxes + b) * RTD_NDIAG;
+            for (int k = 0; k < RTD_NDIAG; k++) h[k] = d[k];
+        }
+        db.done[b] = 0;                      // ready for the next step
+    }
 }
 
 // One work item = RTD_CHEM_BLOCK consecutive cells of one box, one thread per
 // cell.  Reads the post-transport state, runs the sub-cycled chemistry over
-// the box's dt, writes the new radiation state into the caller's U, and the
-// block's diagnostic partials.
+// the box's dt, writes the new radiation state into the caller's U and the
+// item's diagnostic partial; the block that finishes a box's last item
+// reduces that box (no separate diagnostics launch).
 template <int G, typename TU, typename TN, bool STRICT>
 __global__ void __launch_bounds__(RTD_CHEM_BLOCK)
 k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ctl *ctl,
-       double *__restrict__ partials)
+       DiagBuf db)
 {
+    __shared__ int s_last;
     extern __shared__ double s_tab[];
     const double *tab = nullptr;
     if (ph.rtab && !ph.rates_const) {
@@ -621,7 +865,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
         const int b = find_box(boxes, nboxes, it, true);
         const BoxDev &B = boxes[b];
         const int64_t c = (it - B.citem0) * RTD_CHEM_BLOCK + threadIdx.x;
-        double v[RTD_NDIAG] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        DiagAcc v = {0.0, 0.0, 0ull, 0ull, 0ull};
         if (c < B.ncell) {
             const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
             V4<TU> *U = reinterpret_cast<V4<TU> *>(B.U);
@@ -635,7 +879,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 s.F[i][0] = (double)u.y; s.F[i][1] = (double)u.z; s.F[i][2] = (double)u.w;
                 // flux limit after transport, in the state's own precision;
                 // F is scaled by 1/N first so no square underflows
-                if (u.x > TU(0)) {
+                if (u.x > flux_nmin<TU>()) {
                     const TU rn = TU(1) / u.x;
                     const TU ux = u.y * rn, uy = u.z * rn, uz = u.w * rn;
                     const TU f2 = ux * ux + uy * uy + uz * uz;
@@ -681,7 +925,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 const V4<TU> o = {(TU)s.N[i], (TU)s.F[i][0], (TU)s.F[i][1], (TU)s.F[i][2]};
                 st4(U + (int64_t)i * B.ncell + c, o);
                 ph_tot += (double)o.x;
-                if (o.x > TU(0)) {
+                if (o.x > flux_nmin<TU>()) {
                     const TU rn = TU(1) / o.x;
                     const TU ux = o.y * rn, uy = o.z * rn, uz = o.w * rn;
                     const TU f2 = ux * ux + uy * uy + uz * uz;
@@ -690,49 +934,31 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             }
             B.xHI[c] = s.xHI;
             B.T[c] = s.T;
-            v[0] = 1.0 - s.xHI;
-            v[1] = ph_tot;
-            v[2] = (double)sqrt(f2max);
-            v[3] = s.xHI < 0.5 ? 1.0 : 0.0;
-            v[4] = (double)ncyc;
+            v.X = 1.0 - s.xHI;
+            v.ph = ph_tot;
+            v.fbits = (unsigned long long)__double_as_longlong((double)sqrt(f2max));
+            v.count = s.xHI < 0.5 ? 1ull : 0ull;
+            v.ncyc = (unsigned long long)ncyc;
         }
-        block_reduce_diag(v, partials + it * RTD_NDIAG);
+        v = block_reduce_diag(v);
+        if (threadIdx.x == 0) {
+            DiagPart &p = db.part[it];
+            p.X = v.X;
+            p.ph = v.ph;
+            p.fbits = v.fbits;
+            p.count = (unsigned)v.count;
+            p.ncyc = (unsigned)v.ncyc;
+            __threadfence();
+            s_last = atomicAdd(&db.done[b], 1u) == (unsigned)(B.ncitems - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            reduce_box(B, b, db, ctl);
+        }
     }
 }
 
-#ifndef RTK_STRICT_TU
-// Per-box sums of the chemistry partials in a fixed order; writes the step's
-// diagnostics (ionised fraction, photons, max f, n(xHI<0.5), mean sub-cycles)
-// into the caller's history and into lastdiag.
-__global__ void __launch_bounds__(RTD_CHEM_BLOCK)
-k_finalize(const BoxDev *__restrict__ boxes, const double *__restrict__ partials, Ctl *ctl,
-           double *lastdiag)
-{
-    const int b = blockIdx.x;
-    const BoxDev &B = boxes[b];
-    double v[RTD_NDIAG] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int64_t i = threadIdx.x; i < B.ncitems; i += blockDim.x) {
-        const double *p = partials + (B.citem0 + i) * RTD_NDIAG;
-#pragma unroll
-        for (int k = 0; k < RTD_NDIAG; k++) v[k] = (k == 2) ? fmax(v[k], p[k]) : v[k] + p[k];
-    }
-    __shared__ double out[RTD_NDIAG];
-    block_reduce_diag(v, out);
-    if (threadIdx.x == 0) {
-        const double nc = (double)B.ncell;
-        double d[RTD_NDIAG];
-        d[0] = out[0] / nc;
-        d[1] = out[1] * B.nunit * (B.dx * B.dx * B.dx);
-        d[2] = out[2];
-        d[3] = out[3];
-        d[4] = out[4] / nc;
-        for (int k = 0; k < RTD_NDIAG; k++) lastdiag[b * RTD_NDIAG + k] = d[k];
-        if (ctl->hist) {
-            double *h = ctl->hist + ((int64_t)ctl->step * ctl->nboxes + b) * RTD_NDIAG;
-            for (int k = 0; k < RTD_NDIAG; k++) h[k] = d[k];
-        }
-    }
-}
-#endif  // RTK_STRICT_TU
+
 
 }  // namespace rtk

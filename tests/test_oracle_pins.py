@@ -532,3 +532,25 @@ def test_group_table_structure():
             assert lo < t["Eavg"][i] < hi
             assert O.sigma_HI(edges[i + 1]) < t["sigN"][i] < O.sigma_HI(edges[i])
             assert t["sigE"][i] < t["sigN"][i]       # sigma falls with energy
+
+
+def test_step_cells_is_the_full_step_on_those_cells():
+    """The sampled-cell step used by the large-grid GPU checks reproduces the
+    oracle's full step bit for bit on the cells it evaluates."""
+    w = I.reion(n=20, steps=5, nsrc=6)
+    t = O.group_table(w.edges_eV, w.T_bb)
+    t = {k: I.f32(v) for k, v in t.items()}
+    p = O.Params(sigN=t["sigN"], sigE=t["sigE"], Eavg=t["Eavg"], frac=t["frac"], c=w.c_red,
+                 bc=[2, 1, 0, 0, 1, 1])
+    box = w.boxes[0]
+    nunit = w.nunit(box)
+    S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)
+    U, x, T = box.initial_state(3)
+    r = O.run(p, U, x, T, box.n0, box.dx, nunit, 4, S)
+    full = O.run(p, r.U, r.xHI, r.T, box.n0, box.dx, nunit, 1, S)
+    cells = np.array([0, 19, 380, 399, 7999, 4210, int(box.src_cells[0])], dtype=np.int64)
+    Uo, xo, To, err = O.step_cells(p, r.U, r.xHI, r.T, box.n0, box.dx, nunit, cells, S)
+    assert err == 0
+    np.testing.assert_array_equal(Uo, full.U.reshape(3, -1, 4)[:, cells, :].transpose(1, 0, 2))
+    np.testing.assert_array_equal(xo, full.xHI.reshape(-1)[cells])
+    np.testing.assert_array_equal(To, full.T.reshape(-1)[cells])

@@ -132,6 +132,13 @@ def lib():
             "orc_step_cells": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                          _dp, _dp, _dp, _dp, _dp, C.c_int, _i64p, _dp, _dp, _dp]),
             "orc_set_threads": (None, [C.c_int]),
+            "orc_chem_cell_adj": (C.c_int, [PP, C.c_double, C.c_double, C.c_double, _dp, _dp,
+                                            C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp]),
+            "orc_flux_jacobian": (None, [C.c_int, _dp, _dp]),
+            "orc_transport_adj": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp,
+                                            _dp]),
+            "orc_adjoint": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                      _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp]),
             "orc_get_threads": (C.c_int, []),
             "orc_group_table": (None, [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp]),
             "orc_group_table_w": (None, [C.c_int, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp]),
@@ -282,6 +289,57 @@ def step_cells(p: Params, U, xHI, T, n0, dx: float, nunit: float, cells, S=None)
     err = lib().orc_step_cells(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
                                _ptr(T), _ptr(n0), Sp, k, _ptr(cells), _ptr(Uo), _ptr(xo), _ptr(To))
     return Uo, xo, To, err
+
+
+def chem_cell_adj(p: Params, dt, nunit, n0, S, U, xHI, T, bU, bxHI, bT):
+    """Reverse of chem_cell at (U, xHI, T): adjoints of the outputs in, of the
+    inputs out.  Returns (bU[G,4], bxHI, bT, dn0, dS[G], n_trials)."""
+    Uc = np.ascontiguousarray(np.asarray(U, dtype=np.float64).reshape(p.G * 4))
+    Sc = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(p.G))
+    b = np.ascontiguousarray(np.asarray(bU, dtype=np.float64).reshape(p.G * 4)).copy()
+    bx, bt, dn = C.c_double(bxHI), C.c_double(bT), C.c_double(0.0)
+    dS = np.zeros(p.G)
+    n = lib().orc_chem_cell_adj(C.byref(p.to_c()), dt, nunit, n0, _ptr(Sc), _ptr(Uc), xHI, T,
+                                _ptr(b), C.byref(bx), C.byref(bt), C.byref(dn), _ptr(dS))
+    return b.reshape(p.G, 4), bx.value, bt.value, dn.value, dS, n
+
+
+def flux_jacobian(d: int, U4) -> np.ndarray:
+    U = np.ascontiguousarray(U4, dtype=np.float64)
+    J = np.zeros((4, 4))
+    lib().orc_flux_jacobian(d, _ptr(U), _ptr(J))
+    return J
+
+
+def transport_adj(p: Params, U, lamS, lam: float) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    lamS = np.ascontiguousarray(lamS, dtype=np.float64)
+    G, nz, ny, nx, _ = U.shape
+    out = np.empty_like(U)
+    rc = lib().orc_transport_adj(C.byref(p.to_c()), nx, ny, nz, lam, _ptr(U), _ptr(lamS), _ptr(out))
+    assert rc == 0, "adjoint needs periodic boundaries"
+    return out
+
+
+def adjoint(p: Params, U0, xHI0, T0, n0, dx, nunit, nsteps, dLdX, S=None):
+    """dL/dS [G, ncell] and dL/dn0 [ncell] of L(X(1..nsteps))."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    G, nz, ny, nx, _ = U0.shape
+    ncell = nx * ny * nz
+    dS = np.zeros((G, ncell))
+    dn0 = np.zeros(ncell)
+    dLdX = np.ascontiguousarray(dLdX, dtype=np.float64)
+    Sp = None
+    if S is not None:
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        Sp = _ptr(S)
+    rc = lib().orc_adjoint(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U0),
+                           _ptr(np.ascontiguousarray(xHI0, dtype=np.float64)),
+                           _ptr(np.ascontiguousarray(T0, dtype=np.float64)),
+                           _ptr(np.ascontiguousarray(n0, dtype=np.float64)), Sp, nsteps,
+                           _ptr(dLdX), _ptr(dS), _ptr(dn0))
+    assert rc == 0, "adjoint needs periodic boundaries"
+    return dS, dn0
 
 
 def sigma_HI(E_eV: float) -> float:

@@ -429,9 +429,38 @@ static void chem_trial(const orc_params *p, double nunit, double n0, const doubl
     o->T = e / (1.5 * (1.0 + (1.0 - o->xHI)) * n0 * ORC_KB);
 }
 
+/* accepted trials of one cell's step, recorded for the adjoint */
+typedef struct {
+    int n, cap;
+    cellstate *s;     /* state before each accepted trial */
+    double *dtau;     /* its length */
+} chem_trace;
+
+static void trace_push(chem_trace *tr, const cellstate *s, double dtau)
+{
+    if (!tr) return;
+    if (tr->n == tr->cap) {
+        tr->cap = tr->cap ? 2 * tr->cap : 16;
+        tr->s = (cellstate *)realloc(tr->s, sizeof(cellstate) * tr->cap);
+        tr->dtau = (double *)realloc(tr->dtau, sizeof(double) * tr->cap);
+    }
+    tr->s[tr->n] = *s;
+    tr->dtau[tr->n] = dtau;
+    tr->n++;
+}
+
 /* advance one cell over a span of time with sub-cycles (R4) */
+static int chem_span_tr(const orc_params *p, double nunit, double n0, const double *S,
+                        cellstate *s, double span, int use_estimate, int *ncyc, chem_trace *tr);
+
 static int chem_span(const orc_params *p, double nunit, double n0, const double *S,
                      cellstate *s, double span, int use_estimate, int *ncyc)
+{
+    return chem_span_tr(p, nunit, n0, S, s, span, use_estimate, ncyc, NULL);
+}
+
+static int chem_span_tr(const orc_params *p, double nunit, double n0, const double *S,
+                        cellstate *s, double span, int use_estimate, int *ncyc, chem_trace *tr)
 {
     int err = 0;
     double tau = 0.0;
@@ -469,6 +498,7 @@ static int chem_span(const orc_params *p, double nunit, double n0, const double 
             dtau = 0.5 * dtau;
             last = 0;
         }
+        trace_push(tr, s, dtau);
         *s = o;
         (*ncyc)++;
         if (last) break;
@@ -682,4 +712,374 @@ void orc_group_table(int G, const double *edges, double Tbb,
                      double *sigN, double *sigE, double *Eavg, double *frac)
 {
     orc_group_table_w(G, edges, Tbb, 1, sigN, sigE, Eavg, frac);
+}
+
+
+/* ------------------------------------------------------------------ */
+/* 6. adjoint (reverse mode) of the step, branch decisions frozen       */
+/*    READING: the halving decisions, the dtau sequence and the flux-   */
+/*    limit clamp of the forward pass are held fixed (stop-gradient     */
+/*    through the dtau selection); everything else is differentiated.   */
+/* ------------------------------------------------------------------ */
+
+/* rates at T and their T-derivatives (cgs, per K) */
+typedef struct {
+    double aA, aB, beta, kR, kC;
+    double daA, daB, dbeta, dkR, dkC;
+} rates_d;
+
+static void rates_with_derivs(const orc_params *p, double T, rates_d *r)
+{
+    memset(r, 0, sizeof *r);
+    if (p->rates_const) {
+        r->aA = p->alphaA; r->aB = p->alphaB; r->beta = p->beta;
+        return;
+    }
+    double l = 2.0 * ORC_T_HI / T;
+    double y;
+    r->aA = orc_alphaA(T);
+    y = pow(l / 0.522, 0.470);
+    r->daA = r->aA * (1.503 - 1.923 * 0.470 * y / (1.0 + y)) * (-1.0 / T);
+    r->aB = orc_alphaB(T);
+    y = pow(l / 2.740, 0.407);
+    r->daB = r->aB * (1.500 - 2.242 * 0.407 * y / (1.0 + y)) * (-1.0 / T);
+    r->beta = orc_beta(T);
+    y = pow(l / 0.354, 0.874);
+    r->dbeta = r->beta * (-1.5 + 0.5 * l + 1.089 + 1.101 * 0.874 * y / (1.0 + y)) / T;
+    double crec, dcrec;
+    if (p->ots) {
+        crec = orc_cool_recB(T);
+        y = pow(l / 2.250, 0.376);
+        dcrec = crec * (1.0 - 1.970 + 3.720 * 0.376 * y / (1.0 + y)) / T;
+    } else {
+        crec = orc_cool_recA(T);
+        y = pow(l / 0.541, 0.502);
+        dcrec = crec * (1.0 - 1.965 + 2.697 * 0.502 * y / (1.0 + y)) / T;
+    }
+    double cff = orc_cool_brems(T), dcff = 0.5 * cff / T;
+    double cci = orc_cool_colion(T), dcci = ORC_KB * ORC_T_HI * r->dbeta;
+    double cce = orc_cool_colexc(T);
+    double dcce = cce * (118348.0 / (T * T) - (0.5 / sqrt(1.0e5 * T)) / (1.0 + sqrt(T / 1.0e5)));
+    r->kR = crec + cff;
+    r->dkR = dcrec + dcff;
+    r->kC = cci + cce;
+    r->dkC = dcci + dcce;
+}
+
+/* Reverse of one accepted trial (chem_trial) of length dtau from state s.
+ * In: adjoints ob of the trial's output.  Out: adjoints sb of its input
+ * (overwritten), and dn0 / dS accumulated. */
+static void chem_trial_adj(const orc_params *p, double nunit, double n0, const double *S,
+                           const cellstate *s, double dtau, const cellstate *ob, cellstate *sb,
+                           double *dn0, double *dS)
+{
+    int G = p->G;
+    double c = p->c;
+    rates_d r;
+    rates_with_derivs(p, s->T, &r);
+    double alpha = p->ots ? r.aB : r.aA;
+    double x = 1.0 - s->xHI;
+    /* forward again, keeping the intermediates */
+    double den[ORC_MAXG], N1[ORC_MAXG], F1[ORC_MAXG][3], csig[ORC_MAXG], SigE[ORC_MAXG];
+    double rec = (p->ots ? 0.0 : (r.aA - r.aB) * x * x * n0 * n0 / nunit);
+    for (int i = 0; i < G; i++) {
+        csig[i] = c * p->sigN[i];
+        SigE[i] = p->sigE[i] * p->Eavg[i] - p->sigN[i] * ORC_E_HI;
+        den[i] = 1.0 + csig[i] * s->xHI * n0 * dtau;
+        double src = S[i] + (i == 0 ? rec : 0.0);
+        N1[i] = (s->N[i] + src * dtau) / den[i];
+        for (int k = 0; k < 3; k++) F1[i][k] = s->F[i][k] / den[i];
+    }
+    double gam = 0.0;
+    for (int i = 0; i < G; i++) gam += csig[i] * nunit * N1[i];
+    double A = s->xHI + alpha * x * x * n0 * dtau;
+    double Bd = 1.0 + dtau * (r.beta * x * n0 + gam);
+    double xHI1 = A / Bd;
+
+    double bN1[ORC_MAXG], bxHI1 = ob->xHI, bT = 0.0, bxHI = 0.0, bx = 0.0, bn0 = 0.0;
+    double baA = 0.0, baB = 0.0, bbeta = 0.0, bkR = 0.0, bkC = 0.0, balpha = 0.0;
+    for (int i = 0; i < G; i++) bN1[i] = ob->N[i];
+    if (p->isothermal) {
+        bT += ob->T;
+    } else {
+        double x1 = 1.0 - xHI1;
+        double heat = 0.0;
+        for (int i = 0; i < G; i++) heat += c * xHI1 * n0 * (nunit * N1[i]) * SigE[i];
+        double Lam = (x1 * n0) * (x1 * n0) * r.kR + (x1 * n0) * (xHI1 * n0) * r.kC;
+        double e0 = 1.5 * (1.0 + (1.0 - s->xHI)) * n0 * ORC_KB * s->T;
+        double e1 = e0 + dtau * heat - dtau * Lam;
+        double W = 1.5 * (1.0 + x1) * n0 * ORC_KB;
+        double T1 = e1 / W;
+        double be1 = ob->T / W;
+        double bW = -ob->T * T1 / W;
+        bxHI1 += bW * (-1.5 * n0 * ORC_KB);
+        bn0 += bW * 1.5 * (1.0 + x1) * ORC_KB;
+        double be0 = be1, bheat = be1 * dtau, bLam = -be1 * dtau;
+        /* Lam = n0^2 (x1^2 kR + x1 xHI1 kC), x1 = 1 - xHI1 */
+        bxHI1 += bLam * n0 * n0 * (x1 * r.kC - (2.0 * x1 * r.kR + xHI1 * r.kC));
+        bn0 += bLam * 2.0 * n0 * (x1 * x1 * r.kR + x1 * xHI1 * r.kC);
+        bkR += bLam * n0 * n0 * x1 * x1;
+        bkC += bLam * n0 * n0 * x1 * xHI1;
+        /* heat = sum_i c xHI1 n0 nunit N1_i SigE_i */
+        double hs = 0.0;
+        for (int i = 0; i < G; i++) hs += c * nunit * N1[i] * SigE[i];
+        bxHI1 += bheat * n0 * hs;
+        bn0 += bheat * xHI1 * hs;
+        for (int i = 0; i < G; i++) bN1[i] += bheat * c * xHI1 * n0 * nunit * SigE[i];
+        /* e0 = 1.5 (2 - xHI) n0 kB T */
+        bxHI += be0 * (-1.5 * n0 * ORC_KB * s->T);
+        bn0 += be0 * 1.5 * (1.0 + x) * ORC_KB * s->T;
+        bT += be0 * 1.5 * (1.0 + x) * n0 * ORC_KB;
+    }
+    /* xHI1 = A / Bd */
+    double bA = bxHI1 / Bd, bBd = -bxHI1 * xHI1 / Bd;
+    bxHI += bA;
+    balpha += bA * x * x * n0 * dtau;
+    bx += bA * 2.0 * alpha * x * n0 * dtau;
+    bn0 += bA * alpha * x * x * dtau;
+    bbeta += bBd * dtau * x * n0;
+    bx += bBd * dtau * r.beta * n0;
+    bn0 += bBd * dtau * r.beta * x;
+    double bgam = bBd * dtau;
+    for (int i = 0; i < G; i++) bN1[i] += bgam * csig[i] * nunit;
+    double brec = 0.0;
+    for (int i = 0; i < G; i++) {
+        double bnum = bN1[i] / den[i];
+        double bden = -bN1[i] * N1[i] / den[i];
+        for (int k = 0; k < 3; k++) {
+            sb->F[i][k] = ob->F[i][k] / den[i];
+            bden += -ob->F[i][k] * F1[i][k] / den[i];
+        }
+        sb->N[i] = bnum;
+        double bsrc = bnum * dtau;
+        dS[i] += bsrc;
+        if (i == 0 && !p->ots) brec += bsrc;
+        bxHI += bden * csig[i] * n0 * dtau;
+        bn0 += bden * csig[i] * s->xHI * dtau;
+    }
+    if (!p->ots) {
+        double k2 = x * x * n0 * n0 / nunit;
+        baA += brec * k2;
+        baB -= brec * k2;
+        bx += brec * 2.0 * (r.aA - r.aB) * x * n0 * n0 / nunit;
+        bn0 += brec * 2.0 * (r.aA - r.aB) * x * x * n0 / nunit;
+    }
+    if (p->ots) baB += balpha; else baA += balpha;
+    bxHI -= bx;
+    bT += baA * r.daA + baB * r.daB + bbeta * r.dbeta + bkR * r.dkR + bkC * r.dkC;
+    sb->xHI = bxHI;
+    sb->T = bT;
+    *dn0 += bn0;
+}
+
+/* Adjoint of orc_chem_cell: U, xHI, T are the inputs of the forward call;
+ * bU (G x 4), bxHI, bT hold the adjoints of its outputs on entry and of its
+ * inputs on return; dn0 and dS (G) are accumulated.  Returns the number of
+ * accepted trials. */
+int orc_chem_cell_adj(const orc_params *p, double dt, double nunit, double n0, const double *S,
+                      const double *U, double xHI, double T, double *bU, double *bxHI, double *bT,
+                      double *dn0, double *dS)
+{
+    cellstate s;
+    s.G = p->G;
+    for (int i = 0; i < p->G; i++) {
+        s.N[i] = U[4 * i];
+        for (int k = 0; k < 3; k++) s.F[i][k] = U[4 * i + 1 + k];
+    }
+    s.xHI = xHI;
+    s.T = T;
+    chem_trace tr = {0, 0, NULL, NULL};
+    int ncyc = 0;
+    if (p->nsub > 0) {
+        double h = dt / p->nsub;
+        for (int k = 0; k < p->nsub; k++) chem_span_tr(p, nunit, n0, S, &s, h, 0, &ncyc, &tr);
+    } else {
+        chem_span_tr(p, nunit, n0, S, &s, dt, 1, &ncyc, &tr);
+    }
+    cellstate ob;
+    ob.G = p->G;
+    for (int i = 0; i < p->G; i++) {
+        ob.N[i] = bU[4 * i];
+        for (int k = 0; k < 3; k++) ob.F[i][k] = bU[4 * i + 1 + k];
+    }
+    ob.xHI = *bxHI;
+    ob.T = *bT;
+    for (int t = tr.n - 1; t >= 0; t--) {
+        cellstate sb;
+        chem_trial_adj(p, nunit, n0, S, &tr.s[t], tr.dtau[t], &ob, &sb, dn0, dS);
+        ob = sb;
+    }
+    for (int i = 0; i < p->G; i++) {
+        bU[4 * i] = ob.N[i];
+        for (int k = 0; k < 3; k++) bU[4 * i + 1 + k] = ob.F[i][k];
+    }
+    *bxHI = ob.xHI;
+    *bT = ob.T;
+    int n = tr.n;
+    free(tr.s);
+    free(tr.dtau);
+    return n;
+}
+
+/* Jacobian J[r][m] = d G_d[r] / d U[m] of the physical flux along d (the
+ * closure P = N D of orc_closure, with its clamp branch frozen). */
+void orc_flux_jacobian(int d, const double *U, double J[4][4])
+{
+    memset(J, 0, sizeof(double) * 16);
+    J[0][1 + d] = 1.0;                      /* G_0 = F_d */
+    double N = U[0];
+    if (!(N > 0.0)) return;
+    double u[3] = {U[1] / N, U[2] / N, U[3] / N};
+    double f2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    if (f2 > 1.0) {
+        /* P = N uh uh^T, uh = F/|F|: dP/dN = uh uh^T,
+           dP_dj/dF_k = (N/|F|)(d_dk uh_j + uh_d d_jk - 2 uh_d uh_j uh_k) */
+        double Fn = sqrt(U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
+        double uh[3] = {U[1] / Fn, U[2] / Fn, U[3] / Fn};
+        for (int j = 0; j < 3; j++) {
+            J[1 + j][0] = uh[d] * uh[j];
+            for (int k = 0; k < 3; k++)
+                J[1 + j][1 + k] = (N / Fn) * ((d == k ? uh[j] : 0.0) + (j == k ? uh[d] : 0.0)
+                                              - 2.0 * uh[d] * uh[j] * uh[k]);
+        }
+        return;
+    }
+    double s = sqrt(4.0 - 3.0 * f2);
+    double a = ((1.0 + s) - 2.0 * f2) / (5.0 + 2.0 * s);
+    double g = (6.0 + 3.0 / (2.0 + s)) / (5.0 + 2.0 * s);
+    /* derivatives with respect to f2, ds/df2 = -3/(2s) */
+    double ds = -1.5 / s;
+    double da = ((ds - 2.0) * (5.0 + 2.0 * s) - ((1.0 + s) - 2.0 * f2) * 2.0 * ds)
+                / ((5.0 + 2.0 * s) * (5.0 + 2.0 * s));
+    double dg = ((-3.0 * ds / ((2.0 + s) * (2.0 + s))) * (5.0 + 2.0 * s)
+                 - (6.0 + 3.0 / (2.0 + s)) * 2.0 * ds) / ((5.0 + 2.0 * s) * (5.0 + 2.0 * s));
+    for (int j = 0; j < 3; j++) {
+        double djd = (j == d) ? 1.0 : 0.0;
+        /* dP_dj/dN = (a - 2 f2 a') d_dj - (g + 2 f2 g') u_d u_j */
+        J[1 + j][0] = (a - 2.0 * f2 * da) * djd - (g + 2.0 * f2 * dg) * u[d] * u[j];
+        /* dP_dj/dF_k = 2 u_k (a' d_dj + g' u_d u_j) + g (d_dk u_j + d_jk u_d) */
+        for (int k = 0; k < 3; k++)
+            J[1 + j][1 + k] = 2.0 * u[k] * (da * djd + dg * u[d] * u[j])
+                              + g * ((d == k ? u[j] : 0.0) + (j == k ? u[d] : 0.0));
+    }
+}
+
+/* Adjoint of orc_transport on a periodic box: lamU = (dUs/dU)^T lamS for
+ * every group, with
+ *   (Us = U* the post-transport state)
+ *   lamU_c = lamS_c + (lam/2) sum_d [ J_d(U_c)^T (lamS_{c+d} - lamS_{c-d})
+ *                                     + (lamS_{c+d} - 2 lamS_c + lamS_{c-d}) ]
+ * (from U*_c = U_c - lam sum_d (Phi_{d,+} - Phi_{d,-}) and Eq. e:glf). */
+int orc_transport_adj(const orc_params *p, int nx, int ny, int nz, double lam, const double *U,
+                      const double *lamS, double *lamU)
+{
+    for (int f = 0; f < 6; f++)
+        if (p->bc[f] != 0) return -1;
+    size_t ncell = (size_t)nx * ny * nz;
+    int n[3] = {nx, ny, nz};
+    size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
+    for (int g = 0; g < p->G; g++) {
+        const double *Ug = U + 4 * ncell * g;
+        const double *Lg = lamS + 4 * ncell * g;
+        double *Og = lamU + 4 * ncell * g;
+        for (int z = 0; z < nz; z++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    int c[3] = {x, y, z};
+                    size_t id = ((size_t)z * ny + y) * nx + x;
+                    double acc[4];
+                    for (int m = 0; m < 4; m++) acc[m] = 0.0;
+                    for (int d = 0; d < 3; d++) {
+                        size_t ip = c[d] + 1 < n[d] ? id + stride[d] : id - stride[d] * (n[d] - 1);
+                        size_t im = c[d] > 0 ? id - stride[d] : id + stride[d] * (n[d] - 1);
+                        double J[4][4], dl[4];
+                        orc_flux_jacobian(d, Ug + 4 * id, J);
+                        for (int r = 0; r < 4; r++) dl[r] = Lg[4 * ip + r] - Lg[4 * im + r];
+                        for (int m = 0; m < 4; m++) {
+                            double jt = 0.0;
+                            for (int r = 0; r < 4; r++) jt += J[r][m] * dl[r];
+                            acc[m] += jt + ((Lg[4 * ip + m] - 2.0 * Lg[4 * id + m]) + Lg[4 * im + m]);
+                        }
+                    }
+                    for (int m = 0; m < 4; m++) Og[4 * id + m] = Lg[4 * id + m] + 0.5 * lam * acc[m];
+                }
+    }
+    return 0;
+}
+
+/* Gradient of a loss L(X(1..nsteps)) of the volume-weighted ionised
+ * fraction history X(t) = mean(1 - xHI) after step t, for a run of nsteps
+ * steps from (U0, xHI0, T0): in dLdX[t-1] = dL/dX(t); out dS[G][ncell]
+ * (dL/dS, S in stored units per second) and dn0[ncell].  Plain: the whole
+ * trajectory is stored.  Periodic boxes only.  Returns 0 or -1. */
+int orc_adjoint(const orc_params *p, int nx, int ny, int nz, double dx, double nunit,
+                const double *U0, const double *xHI0, const double *T0, const double *n0,
+                const double *S, int nsteps, const double *dLdX, double *dS, double *dn0)
+{
+    for (int f = 0; f < 6; f++)
+        if (p->bc[f] != 0) return -1;
+    size_t ncell = (size_t)nx * ny * nz;
+    int G = p->G;
+    size_t nu = 4 * ncell * G;
+    double dt = orc_timestep(p, dx);
+    double lam = p->c * dt / dx;
+    double *Uk = (double *)malloc(sizeof(double) * nu * (nsteps + 1));
+    double *Us = (double *)malloc(sizeof(double) * nu * nsteps);
+    double *xk = (double *)malloc(sizeof(double) * ncell * (nsteps + 1));
+    double *Tk = (double *)malloc(sizeof(double) * ncell * (nsteps + 1));
+    double *lU = (double *)calloc(nu, sizeof(double));
+    double *lS = (double *)calloc(nu, sizeof(double));
+    double *lx = (double *)calloc(ncell, sizeof(double));
+    double *lT = (double *)calloc(ncell, sizeof(double));
+    if (!Uk || !Us || !xk || !Tk || !lU || !lS || !lx || !lT) return -1;
+    memcpy(Uk, U0, sizeof(double) * nu);
+    memcpy(xk, xHI0, sizeof(double) * ncell);
+    memcpy(Tk, T0, sizeof(double) * ncell);
+    for (int k = 0; k < nsteps; k++) {           /* forward, keeping every state */
+        double *Un = Uk + nu * (k + 1), *xn = xk + ncell * (k + 1), *Tn = Tk + ncell * (k + 1);
+        orc_transport(p, nx, ny, nz, lam, Uk + nu * k, Us + nu * k);
+        memcpy(xn, xk + ncell * k, sizeof(double) * ncell);
+        memcpy(Tn, Tk + ncell * k, sizeof(double) * ncell);
+#pragma omp parallel for num_threads(orc_threads) schedule(dynamic, 256)
+        for (size_t id = 0; id < ncell; id++) {
+            double Uc[4 * ORC_MAXG], Sc[ORC_MAXG];
+            for (int i = 0; i < G; i++) {
+                for (int m = 0; m < 4; m++) Uc[4 * i + m] = Us[nu * k + 4 * (ncell * i + id) + m];
+                Sc[i] = S ? S[ncell * i + id] : 0.0;
+            }
+            orc_chem_cell(p, dt, nunit, n0[id], Sc, Uc, &xn[id], &Tn[id], NULL);
+            for (int i = 0; i < G; i++)
+                for (int m = 0; m < 4; m++) Un[4 * (ncell * i + id) + m] = Uc[4 * i + m];
+        }
+    }
+    memset(dS, 0, sizeof(double) * G * ncell);
+    memset(dn0, 0, sizeof(double) * ncell);
+    for (int k = nsteps - 1; k >= 0; k--) {      /* reverse */
+        double gx = -dLdX[k] / (double)ncell;    /* X(k+1) = mean(1 - xHI) */
+#pragma omp parallel for num_threads(orc_threads) schedule(dynamic, 256)
+        for (size_t id = 0; id < ncell; id++) {
+            double Uc[4 * ORC_MAXG], Sc[ORC_MAXG], bU[4 * ORC_MAXG], dSc[ORC_MAXG];
+            for (int i = 0; i < G; i++) {
+                for (int m = 0; m < 4; m++) {
+                    Uc[4 * i + m] = Us[nu * k + 4 * (ncell * i + id) + m];
+                    bU[4 * i + m] = lU[4 * (ncell * i + id) + m];
+                }
+                Sc[i] = S ? S[ncell * i + id] : 0.0;
+                dSc[i] = 0.0;
+            }
+            double bx = lx[id] + gx, bT = lT[id], bn = 0.0;
+            orc_chem_cell_adj(p, dt, nunit, n0[id], Sc, Uc, xk[ncell * k + id], Tk[ncell * k + id],
+                              bU, &bx, &bT, &bn, dSc);
+            for (int i = 0; i < G; i++) {
+                for (int m = 0; m < 4; m++) lS[4 * (ncell * i + id) + m] = bU[4 * i + m];
+                dS[ncell * i + id] += dSc[i];
+            }
+            lx[id] = bx;
+            lT[id] = bT;
+            dn0[id] += bn;
+        }
+        orc_transport_adj(p, nx, ny, nz, lam, Uk + nu * k, lS, lU);
+    }
+    free(Uk); free(Us); free(xk); free(Tk); free(lU); free(lS); free(lx); free(lT);
+    return 0;
 }

@@ -147,6 +147,26 @@ RT_API int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *cell, 
  * RT_ERR_REALIZABILITY) after completing all steps. */
 RT_API int rt_step(rt_handle *h, int nsteps, double *hist);
 
+/* Gradient of a loss of the ionised-fraction history (the paper has no
+ * adjoint: this is the reverse mode of its step).
+ * Runs the handle's step nsteps times from the device state (U0, xHI0, T0)
+ * with the handle's current sources and density, X(t) = volume-weighted
+ * ionised fraction mean(1 - xHI) after step t (the first diagnostic of
+ * rt_step), then the hand-written reverse pass of every step with the
+ * forward's branch decisions frozen (10% halvings, dtau sequence, flux
+ * clamp), recomputing each segment of ckpt_every steps from a checkpoint.
+ *   dL_dX   device, nsteps doubles: dL/dX(t), t = 1..nsteps
+ *   dL_dQ   host, one double per source of the last rt_set_sources call, in
+ *           its order: dL/dQ (per photons/s of the whole spectrum)
+ *   dL_dn0  device, ncell doubles: dL/dn0 per cell (per cm^-3)
+ * Needs one box, an FP64 form and periodic faces (RT_ERR_ARG otherwise).
+ * Allocates its checkpoints and segment states for the call.  On return the
+ * box holds the state after the nsteps forward steps.  RT_ERR_SUBCYCLE if a
+ * cell-step of the recomputation needs more than 2048 accepted sub-cycles. */
+RT_API int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, const double *T0,
+                      int nsteps, int ckpt_every, const double *dL_dX, double *dL_dQ,
+                      double *dL_dn0);
+
 /* Copy host arrays into the device state of `box` (any argument may be NULL
  * to skip it; U in the precision's element type; n0 overwrites the caller's
  * density buffer).  Ordered on the handle's stream; returns after the copy. */

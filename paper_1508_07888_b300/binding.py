@@ -78,7 +78,7 @@ class rt_stats(C.Structure):
 
 EXPORTS = ("rt_create", "rt_set_sources", "rt_step", "rt_upload", "rt_download", "rt_query",
            "rt_set_profiling", "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table",
-           "rt_transport_static")
+           "rt_transport_static", "rt_adjoint")
 KERNELS = ("transport", "chemistry", "diagnostics")   # diagnostics: fused into chemistry
 
 _lib = None
@@ -114,6 +114,7 @@ def lib(build_if_missing: bool = True):
         "rt_timestep": (C.c_double, [C.POINTER(rt_params), C.c_double]),
         "rt_group_table": (C.c_int, [C.c_int, dp, C.c_double, dp, dp, dp, dp]),
         "rt_transport_static": (C.c_int, [C.POINTER(rt_params), C.POINTER(rt_box), C.c_int, vp]),
+        "rt_adjoint": (C.c_int, [vp, vp, vp, vp, C.c_int, C.c_int, vp, dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -198,6 +199,19 @@ def rt_last_error(h=None) -> str:
 
 def rt_destroy(h) -> None:
     lib().rt_destroy(h)
+
+
+def rt_adjoint(h, U0_ptr: int, xHI0_ptr: int, T0_ptr: int, nsteps: int, ckpt_every: int,
+               dLdX_ptr: int, nsrc: int, dLdn0_ptr: int):
+    """Gradient of a loss of the ionised-fraction history (see include/rt_m1.h).
+    Returns (status, dL/dQ as a numpy array of nsrc doubles)."""
+    dQ = np.zeros(max(nsrc, 1))
+    code = lib().rt_adjoint(h, C.c_void_p(U0_ptr), C.c_void_p(xHI0_ptr), C.c_void_p(T0_ptr),
+                            int(nsteps), int(ckpt_every), C.c_void_p(dLdX_ptr),
+                            dQ.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(dLdn0_ptr))
+    if code in (RT_ERR_ARG, RT_ERR_CUDA, RT_ERR_STATE):
+        _check(code, h)
+    return code, dQ[:nsrc]
 
 
 def rt_transport_static(p: rt_params, box: rt_box, nsteps: int, stream_ptr: int = 0) -> int:

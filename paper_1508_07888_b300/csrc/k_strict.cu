@@ -1,7 +1,7 @@
 // k_strict.cu -- instantiations of the FP64 hot-path kernels compiled with
 // --fmad=false: no contraction, IEEE division and square root, operations in
 // the order the source writes them (RT_PREC_FP64_STRICT).
-#define RTK_STRICT_TU 1   // the FP32-only kernels are defined once, in k_fast.cu
+#define RTK_SKIP_SINGLE_KERNELS 1   // the FP32-only kernels are defined once, in k_fast.cu
 #include "launch.h"
 #include "rt_kernels.cuh"
 

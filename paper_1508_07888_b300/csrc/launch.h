@@ -42,6 +42,14 @@ inline void transport_layout(rtd::BoxDev &B, int ngroups)
 bool build_rate_table(bool ots, double *out);
 constexpr size_t rate_table_doubles() { return (size_t)RTD_TAB_NF * RTD_TAB_NINT * RTD_TAB_NC; }
 
+// reverse-mode kernels of one FP64 step on a periodic single box (adjoint.cu)
+cudaError_t chem_adj(int G, const rtd::BoxDev *boxes, const rtd::Phys &ph, const double *Us,
+                     const double *xk, const double *Tk, double *lamU, double *lamx, double *lamT,
+                     double gx, double *dn0, double *dS, unsigned *err, int64_t ncell,
+                     cudaStream_t s);
+cudaError_t transport_adj(int G, const rtd::BoxDev *boxes, const double *U, const double *lamS,
+                          double *lamU, int64_t ncell, cudaStream_t s);
+
 // resident blocks per SM of each kernel (for persistent grid sizing)
 int transport_occupancy(bool fp64, bool strict);
 int chem_occupancy(bool fp64, bool strict, int G);

@@ -36,6 +36,7 @@ struct rt_handle {
     rtd::BoxDev *d_boxes = nullptr;
     std::vector<void *> d_us;                // post-transport scratch per box
     std::vector<int64_t *> d_src_cell;
+    std::vector<std::vector<int>> src_uidx;  // per box: unique-table index of each given source
     std::vector<double *> d_src_S;
     rtd::DiagPart *d_partials = nullptr;
     unsigned *d_done = nullptr;              // per-box item counters of the fused reduction
@@ -217,6 +218,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 h->d_us.assign(nboxes, nullptr);
                 h->d_src_cell.assign(nboxes, nullptr);
                 h->d_src_S.assign(nboxes, nullptr);
+                h->src_uidx.assign(nboxes, std::vector<int>());
                 for (int b = 0; b < nboxes; b++) {
                     const rt_box &B = boxes[b];
                     rtd::BoxDev &D = h->bdev[b];
@@ -303,12 +305,14 @@ extern "C" int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *ce
                          [&](int a, int b) { return cell[a] < cell[b]; });
         std::vector<int64_t> ucell;
         std::vector<double> sums;
+        std::vector<int> uidx(nsrc);
         for (int j = 0; j < nsrc; j++) {
             const int k = order[j];
             if (ucell.empty() || ucell.back() != cell[k]) {
                 ucell.push_back(cell[k]);
                 sums.insert(sums.end(), G, 0.0);
             }
+            uidx[k] = (int)ucell.size() - 1;
             double *s = &sums[(ucell.size() - 1) * G];
             for (int i = 0; i < G; i++) s[i] += Q[k] * h->p.frac[i];
         }
@@ -331,6 +335,7 @@ extern "C" int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *ce
         D.src_cell = h->d_src_cell[box];
         D.src_S = h->d_src_S[box];
         D.nsrc = nu;
+        h->src_uidx[box] = uidx;
         CU(h, cudaMemcpy(h->d_boxes + box, &D, sizeof D, cudaMemcpyHostToDevice));
         return RT_OK;
     } catch (...) {
@@ -446,6 +451,167 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
     if (c->err & RTD_ERR_NONFINITE) return fail(h, RT_ERR_NONFINITE, "non-finite xHI or T");
     if (c->err & RTD_ERR_REALIZ) return fail(h, RT_ERR_REALIZABILITY, "|F| > 1.01 cN after transport");
     return RT_OK;
+}
+
+// device buffers of rt_adjoint, freed on every exit path
+struct AdjBufs {
+    std::vector<void *> p;
+    ~AdjBufs()
+    {
+        for (void *q : p) cudaFree(q);
+    }
+    template <typename T>
+    cudaError_t get(T **out, size_t n)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        if (e == cudaSuccess) p.push_back(q);
+        *out = static_cast<T *>(q);
+        return e;
+    }
+};
+
+static bool is_device(const void *q)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, const double *T0,
+                          int nsteps, int ckpt_every, const double *dL_dX, double *dL_dQ,
+                          double *dL_dn0)
+{
+    if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
+    try {
+        if (h->nboxes != 1) return fail(h, RT_ERR_ARG, "rt_adjoint needs a single-box handle");
+        if (!h->fp64) return fail(h, RT_ERR_ARG, "rt_adjoint needs an FP64 precision form");
+        for (int f = 0; f < 6; f++)
+            if (h->p.bc[f] != RT_BC_PERIODIC)
+                return fail(h, RT_ERR_ARG, "rt_adjoint needs periodic boundaries");
+        if (nsteps < 1 || ckpt_every < 1) return fail(h, RT_ERR_ARG, "nsteps and ckpt_every must be >= 1");
+        if (!U0 || !xHI0 || !T0 || !dL_dX || !dL_dn0 || !is_device(U0) || !is_device(xHI0) ||
+            !is_device(T0) || !is_device(dL_dX) || !is_device(dL_dn0))
+            return fail(h, RT_ERR_ARG, "U0, xHI0, T0, dL_dX and dL_dn0 must be device pointers");
+        const rtd::BoxDev &D = h->bdev[0];
+        const int G = h->p.ngroups;
+        const int64_t ncell = D.ncell;
+        const size_t nU = (size_t)G * ncell * 4;
+        const int nsrc_given = (int)h->src_uidx[0].size();
+        if (nsrc_given > 0 && !dL_dQ) return fail(h, RT_ERR_ARG, "dL_dQ is NULL but the box has sources");
+        const int ck = std::min(ckpt_every, nsteps);
+        const int nck = (nsteps + ck - 1) / ck;
+        cudaStream_t s = h->s;
+        AdjBufs B;
+        double *ckU, *ckx, *ckT, *segU, *segUs, *segx, *segT, *lamU, *lamS, *lamx, *lamT, *dS = nullptr;
+        double *endU, *endx, *endT;
+        unsigned *derr;
+        CU(h, B.get(&ckU, nU * nck));
+        CU(h, B.get(&ckx, (size_t)ncell * nck));
+        CU(h, B.get(&ckT, (size_t)ncell * nck));
+        CU(h, B.get(&segU, nU * ck));
+        CU(h, B.get(&segUs, nU * ck));
+        CU(h, B.get(&segx, (size_t)ncell * ck));
+        CU(h, B.get(&segT, (size_t)ncell * ck));
+        CU(h, B.get(&lamU, nU));
+        CU(h, B.get(&lamS, nU));
+        CU(h, B.get(&lamx, (size_t)ncell));
+        CU(h, B.get(&lamT, (size_t)ncell));
+        CU(h, B.get(&endU, nU));
+        CU(h, B.get(&endx, (size_t)ncell));
+        CU(h, B.get(&endT, (size_t)ncell));
+        CU(h, B.get(&derr, 1));
+        if (D.nsrc > 0) CU(h, B.get(&dS, (size_t)D.nsrc * G));
+        std::vector<double> dLdX(nsteps);
+        const size_t bU = nU * sizeof(double), bS = (size_t)ncell * sizeof(double);
+
+        CU(h, cudaEventRecord(h->ev_in, h->user));
+        CU(h, cudaStreamWaitEvent(s, h->ev_in, 0));
+        CU(h, cudaMemcpyAsync(dLdX.data(), dL_dX, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, s));
+        rtd::Ctl *c = h->h_ctl;
+        c->hist = nullptr;
+        c->step = -1;
+        c->nboxes = 1;
+        c->err = 0;
+        c->nclamp = 0;
+        CU(h, cudaMemcpyAsync(h->d_ctl, c, sizeof(rtd::Ctl), cudaMemcpyHostToDevice, s));
+        // forward from (U0, xHI0, T0) with a checkpoint every ck steps
+        CU(h, cudaMemcpyAsync(D.U, U0, bU, cudaMemcpyDeviceToDevice, s));
+        CU(h, cudaMemcpyAsync(D.xHI, xHI0, bS, cudaMemcpyDeviceToDevice, s));
+        CU(h, cudaMemcpyAsync(D.T, T0, bS, cudaMemcpyDeviceToDevice, s));
+        for (int k = 0; k < nsteps; k++) {
+            if (k % ck == 0) {
+                const int q = k / ck;
+                CU(h, cudaMemcpyAsync(ckU + nU * q, D.U, bU, cudaMemcpyDeviceToDevice, s));
+                CU(h, cudaMemcpyAsync(ckx + ncell * q, D.xHI, bS, cudaMemcpyDeviceToDevice, s));
+                CU(h, cudaMemcpyAsync(ckT + ncell * q, D.T, bS, cudaMemcpyDeviceToDevice, s));
+            }
+            CU(h, enqueue_step(h, s));
+        }
+        CU(h, cudaMemcpyAsync(endU, D.U, bU, cudaMemcpyDeviceToDevice, s));
+        CU(h, cudaMemcpyAsync(endx, D.xHI, bS, cudaMemcpyDeviceToDevice, s));
+        CU(h, cudaMemcpyAsync(endT, D.T, bS, cudaMemcpyDeviceToDevice, s));
+        CU(h, cudaStreamSynchronize(s));          // dLdX is on the host from here
+        // reverse, one checkpoint segment at a time
+        CU(h, cudaMemsetAsync(lamU, 0, bU, s));
+        CU(h, cudaMemsetAsync(lamx, 0, bS, s));
+        CU(h, cudaMemsetAsync(lamT, 0, bS, s));
+        CU(h, cudaMemsetAsync(dL_dn0, 0, bS, s));
+        CU(h, cudaMemsetAsync(derr, 0, sizeof(unsigned), s));
+        if (dS) CU(h, cudaMemsetAsync(dS, 0, sizeof(double) * D.nsrc * G, s));
+        for (int q = nck - 1; q >= 0; q--) {
+            const int k0 = q * ck, k1 = std::min(nsteps, k0 + ck);
+            CU(h, cudaMemcpyAsync(D.U, ckU + nU * q, bU, cudaMemcpyDeviceToDevice, s));
+            CU(h, cudaMemcpyAsync(D.xHI, ckx + ncell * q, bS, cudaMemcpyDeviceToDevice, s));
+            CU(h, cudaMemcpyAsync(D.T, ckT + ncell * q, bS, cudaMemcpyDeviceToDevice, s));
+            for (int k = k0; k < k1; k++) {       // recompute the segment, keeping every state
+                const int j = k - k0;
+                CU(h, cudaMemcpyAsync(segU + nU * j, D.U, bU, cudaMemcpyDeviceToDevice, s));
+                CU(h, cudaMemcpyAsync(segx + ncell * j, D.xHI, bS, cudaMemcpyDeviceToDevice, s));
+                CU(h, cudaMemcpyAsync(segT + ncell * j, D.T, bS, cudaMemcpyDeviceToDevice, s));
+                CU(h, enqueue_step(h, s));
+                CU(h, cudaMemcpyAsync(segUs + nU * j, D.Us, bU, cudaMemcpyDeviceToDevice, s));
+            }
+            for (int k = k1 - 1; k >= k0; k--) {
+                const int j = k - k0;
+                const double gx = -dLdX[k] / (double)ncell;   // X(k+1) = mean(1 - xHI)
+                CU(h, rtl::chem_adj(G, h->d_boxes, h->ph, segUs + nU * j, segx + ncell * j,
+                                    segT + ncell * j, lamU, lamx, lamT, gx, dL_dn0, dS, derr, ncell, s));
+                CU(h, rtl::transport_adj(G, h->d_boxes, segU + nU * j, lamU, lamS, ncell, s));
+                std::swap(lamU, lamS);
+            }
+        }
+        // leave the box at the end of the forward run
+        CU(h, cudaMemcpyAsync(D.U, endU, bU, cudaMemcpyDeviceToDevice, s));
+        CU(h, cudaMemcpyAsync(D.xHI, endx, bS, cudaMemcpyDeviceToDevice, s));
+        CU(h, cudaMemcpyAsync(D.T, endT, bS, cudaMemcpyDeviceToDevice, s));
+        std::vector<double> hS((size_t)D.nsrc * G);
+        if (dS) CU(h, cudaMemcpyAsync(hS.data(), dS, sizeof(double) * hS.size(), cudaMemcpyDeviceToHost, s));
+        unsigned herr = 0;
+        CU(h, cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CU(h, cudaMemcpyAsync(c, h->d_ctl, sizeof(rtd::Ctl), cudaMemcpyDeviceToHost, s));
+        CU(h, cudaEventRecord(h->ev_out, s));
+        CU(h, cudaStreamWaitEvent(h->user, h->ev_out, 0));
+        CU(h, cudaStreamSynchronize(s));
+        // S_i = (sum_k Q_k frac_i) / (dx^3 nunit)  =>  dL/dQ_k = sum_i frac_i dL/dS_i / (dx^3 nunit)
+        const double vol = D.dx * D.dx * D.dx;
+        for (int k = 0; k < nsrc_given; k++) {
+            const int u = h->src_uidx[0][k];
+            double g = 0.0;
+            for (int i = 0; i < G; i++) g += h->p.frac[i] * hS[(size_t)u * G + i];
+            dL_dQ[k] = g / (vol * D.nunit);
+        }
+        if ((herr | c->err) & RTD_ERR_SUBCYCLE)
+            return fail(h, RT_ERR_SUBCYCLE, "adjoint: a cell-step needed more than 2048 sub-cycles "
+                                            "or hit the halving cap");
+        if (c->err & RTD_ERR_NONFINITE) return fail(h, RT_ERR_NONFINITE, "non-finite xHI or T");
+        return RT_OK;
+    } catch (...) {
+        return fail(h, RT_ERR_ARG, "unexpected host exception in rt_adjoint");
+    }
 }
 
 static int copy_state(rt_handle *h, int box, bool up, void *U, double *xHI, double *T, void *n0)

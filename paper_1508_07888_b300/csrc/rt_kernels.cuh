@@ -373,7 +373,7 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
     }
 }
 
-#ifndef RTK_STRICT_TU
+#ifndef RTK_SKIP_SINGLE_KERNELS
 // FP32 closure with the MUFU reciprocal / reciprocal square root (~1-2 ulp):
 // P = N D as in closure(); N below 1e-37 (FP32 denormals) gives P = 0, an
 // absolute change below 1e-37 of a state whose scale is O(1).
@@ -566,7 +566,7 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         __syncthreads();
     }
 }
-#endif  // RTK_STRICT_TU
+#endif  // RTK_SKIP_SINGLE_KERNELS
 
 // ------------------------------------------------------------- rates
 // Temperature fits (cgs).  Recombination, collisional ionisation and
@@ -713,9 +713,16 @@ __device__ __forceinline__ void chem_trial(const Phys &ph, double nunit, double 
 // advance one cell over `span` with sub-cycles: dtau = min(rest,
 // |e/(H - Lambda)|) when use_est (adaptive), halved while the energy changes
 // by more than 10% (Sec. 2.2.4, after Rosdahl et al. 2013)
-template <int G, bool STRICT>
+// no-op recorder of accepted trials (the adjoint passes one that stores them)
+struct NoTrace {
+    template <int G>
+    __device__ __forceinline__ void push(const Cell<G> &, double) {}
+};
+
+template <int G, bool STRICT, class Trace = NoTrace>
 __device__ unsigned int chem_span(const Phys &ph, const double *tab, double nunit, double n0,
-                                  const double *S, Cell<G> &s, double span, bool use_est, int &ncyc)
+                                  const double *S, Cell<G> &s, double span, bool use_est, int &ncyc,
+                                  Trace *tr = nullptr)
 {
     unsigned int err = 0;
     double tau = 0.0;
@@ -752,6 +759,7 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, double nuni
             dtau = 0.5 * dtau;
             last = false;
         }
+        if (tr) tr->push(s, dtau);
         s = o;
         ncyc++;
         if (last) break;

@@ -374,47 +374,68 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
 }
 
 #ifndef RTK_SKIP_SINGLE_KERNELS
-// FP32 closure with the MUFU reciprocal / reciprocal square root (~1-2 ulp):
-// P = N D as in closure(); N below 1e-37 (FP32 denormals) gives P = 0, an
-// absolute change below 1e-37 of a state whose scale is O(1).
-__device__ __forceinline__ void closure_fast(const V4<float> &u, float P[6])
+// single-instruction MUFU reciprocal and reciprocal square root (~1 ulp)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Packed form of a cell for the FP32 transport: U = (lo, hi) = ((N, Fx),
+// (Fy, Fz)) and the right-/left-going GLF halves U +- G_d(U) per axis, with
+// G_x = (Fx, Pxx, Pxy, Pxz), G_y = (Fy, Pxy, Pyy, Pyz), G_z = (Fz, Pxz, Pyz,
+// Pzz) and P = N D from the Levermore closure (the formulas of closure(),
+// with MUFU reciprocals, N below 1e-37 -- FP32 denormals -- giving P = 0, and
+// N a + N g u_d u_j formed as (N g u_d) u_j + N a).
+struct Halves {
+    float4 R[3], L[3];
+};
+
+__device__ __forceinline__ float4 f4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+__device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
 {
     const float N = u.x;
+    float P0 = 0.f, P1 = 0.f, P2 = 0.f, P3 = 0.f, P4 = 0.f, P5 = 0.f;
     if (N > 1e-37f) {
-        const float rN = __fdividef(1.0f, N);
+        const float rN = rcp_approx(N);
         float ux = u.y * rN, uy = u.z * rN, uz = u.w * rN;
         float f2 = ux * ux + uy * uy + uz * uz;
         if (f2 > 1.0f) {
-            const float rf = rsqrtf(f2);
+            const float rf = rsqrt_approx(f2);
             ux *= rf; uy *= rf; uz *= rf;
             f2 = 1.0f;
         }
         const float q = 4.0f - 3.0f * f2;
-        const float s = q * rsqrtf(q);
-        const float r5 = __fdividef(1.0f, 5.0f + 2.0f * s);
-        const float a = ((1.0f + s) - 2.0f * f2) * r5;
-        const float g = (6.0f + __fdividef(3.0f, 2.0f + s)) * r5;
-        P[0] = N * (a + g * (ux * ux));
-        P[1] = N * (g * (ux * uy));
-        P[2] = N * (g * (ux * uz));
-        P[3] = N * (a + g * (uy * uy));
-        P[4] = N * (g * (uy * uz));
-        P[5] = N * (a + g * (uz * uz));
-    } else {
+        const float s = q * rsqrt_approx(q);
+        const float r5 = rcp_approx(5.0f + 2.0f * s);
+        const float Na = N * (((1.0f + s) - 2.0f * f2) * r5);
+        const float Ng = N * ((6.0f + 3.0f * rcp_approx(2.0f + s)) * r5);
+        const float gx = Ng * ux, gy = Ng * uy, gz = Ng * uz;
+        P0 = gx * ux + Na; P3 = gy * uy + Na; P5 = gz * uz + Na;
+        P1 = gx * uy; P2 = gx * uz; P4 = gy * uz;
+    }
+    const float2 ulo = make_float2(u.x, u.y), uhi = make_float2(u.z, u.w);
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 G[3][2] = {{make_float2(u.y, P0), make_float2(P1, P2)},
+                            {make_float2(u.z, P1), make_float2(P3, P4)},
+                            {make_float2(u.w, P2), make_float2(P4, P5)}};
 #pragma unroll
-        for (int k = 0; k < 6; k++) P[k] = 0.0f;
+    for (int d = 0; d < 3; d++) {
+        h.R[d] = f4(__fadd2_rn(ulo, G[d][0]), __fadd2_rn(uhi, G[d][1]));
+        h.L[d] = f4(__ffma2_rn(G[d][0], m1, ulo), __ffma2_rn(G[d][1], m1, uhi));
     }
 }
 
-// right- and left-going halves of the GLF flux along d: Rg = U + G_d(U),
-// Lf = U - G_d(U); the face flux between L and R is (Rg(L) - Lf(R)) / 2
-template <int d>
-__device__ __forceinline__ void halves(const V4<float> &u, const float P[6], float4 &Rg, float4 &Lf)
-{
-    const float g0 = comp(u, 1 + d), g1 = P[pidx(d, 0)], g2 = P[pidx(d, 1)], g3 = P[pidx(d, 2)];
-    Rg = make_float4(u.x + g0, u.y + g1, u.z + g2, u.w + g3);
-    Lf = make_float4(u.x - g0, u.y - g1, u.z - g2, u.w - g3);
-}
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
 struct TransportSmemPM {
     V4<float> U[TP_STAGES][TP_H][TP_W];
@@ -484,83 +505,84 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
                 if (sy >= ny) { if (ph.bc[3] == 0) sy = 0; else { sy = ny - 1; hneg = ph.bc[3] == 2 ? 2 : 0; } }
             }
         }
-        const int64_t own_col = (int64_t)y * nx + x;
-        const int64_t halo_col = (int64_t)sy * nx + sx;
-        auto src_plane = [&](int q, int &zneg) -> int {
-            int zz = z0 - 1 + q;
-            zneg = 0;
-            if (zz < 0) { if (ph.bc[4] == 0) zz = nz - 1; else { zz = 0; zneg = ph.bc[4] == 2; } }
-            else if (zz >= nz) { if (ph.bc[5] == 0) zz = 0; else { zz = nz - 1; zneg = ph.bc[5] == 2; } }
-            return zz;
-        };
-        auto issue = [&](int q) {
-            if (q < L) {
-                int zneg;
-                const int64_t pl = (int64_t)src_plane(q, zneg) * sxy;
-                const int slot = q % S;
-                if (act) cp_async16(&sm.U[slot][ty + 1][tx + 1], Ug + pl + own_col);
-                if (hx >= 0) cp_async16(&sm.U[slot][hy][hx], Ug + pl + halo_col);
+        // source pointers of this thread's own and halo cells, advanced one
+        // plane per issue; plane q is z0 - 1 + q, wrapped (periodic) or
+        // clamped (ghost planes copy the face plane, negated when reflective)
+        const V4<float> *gown = Ug + (int64_t)y * nx + x;
+        const V4<float> *ghalo = Ug + (int64_t)sy * nx + sx;
+        const bool zneg_first = z0 == 0 && ph.bc[4] == 2, zneg_last = z1 == nz && ph.bc[5] == 2;
+        int zi = z0 - 1;                          // plane of the next issue
+        int slot_i = 0;                           // its ring slot
+        auto issue = [&]() {
+            if (zi < z1 + 1) {
+                int zz = zi;
+                if (zz < 0) zz = ph.bc[4] == 0 ? nz - 1 : 0;
+                else if (zz >= nz) zz = ph.bc[5] == 0 ? 0 : nz - 1;
+                const int64_t pl = (int64_t)zz * sxy;
+                if (act) cp_async16(&sm.U[slot_i][ty + 1][tx + 1], gown + pl);
+                if (hx >= 0) cp_async16(&sm.U[slot_i][hy][hx], ghalo + pl);
             }
             cp_async_commit();
+            zi++;
+            slot_i = slot_i + 1 == S ? 0 : slot_i + 1;
         };
 #pragma unroll
-        for (int q = 0; q < S - 2; q++) issue(q);
+        for (int q = 0; q < S - 2; q++) issue();
 
         V4<float> uc = {};                  // own cell of plane q-1
         float4 Rz_prev = {}, Rz_c = {};     // right-going z halves of planes q-2 and q-1
+        V4<float> *out = Og + (int64_t)z0 * sxy + (int64_t)y * nx + x;
+        int slot = 0;                       // ring slot of plane q
         for (int q = 0; q < L; q++) {
             cp_async_wait<S - 3>();
             __syncthreads();
-            issue(q + S - 2);
-            const int slot = q % S, hs = q & 1;
-            int zneg;
-            src_plane(q, zneg);
+            issue();
+            const int hs = q & 1;
+            const bool zneg = (q == 0 && zneg_first) || (q == L - 1 && zneg_last);
             V4<float> un = {};
             float4 Rz_n = {}, Lz_n = {};
             if (act) {
                 un = sm.U[slot][ty + 1][tx + 1];
                 if (zneg) un.w = -un.w;
-                float P[6];
-                closure_fast(un, P);
-                float4 Rx, Lx, Ry, Ly;
-                halves<0>(un, P, Rx, Lx);
-                halves<1>(un, P, Ry, Ly);
-                halves<2>(un, P, Rz_n, Lz_n);
-                sm.H[hs][0][ty + 1][tx + 1] = Rx;
-                sm.H[hs][1][ty + 1][tx + 1] = Lx;
-                sm.H[hs][2][ty + 1][tx + 1] = Ry;
-                sm.H[hs][3][ty + 1][tx + 1] = Ly;
+                Halves hv;
+                cell_halves(un, hv);
+                Rz_n = hv.R[2];
+                Lz_n = hv.L[2];
+                sm.H[hs][0][ty + 1][tx + 1] = hv.R[0];
+                sm.H[hs][1][ty + 1][tx + 1] = hv.L[0];
+                sm.H[hs][2][ty + 1][tx + 1] = hv.R[1];
+                sm.H[hs][3][ty + 1][tx + 1] = hv.L[1];
             }
             if (hx >= 0) {
                 V4<float> h = sm.U[slot][hy][hx];
                 if (zneg) h.w = -h.w;
                 if (hneg == 1) h.y = -h.y;
                 else if (hneg == 2) h.z = -h.z;
-                float P[6];
-                closure_fast(h, P);
-                float4 Rg, Lf;
-                if (hk < 2) halves<0>(h, P, Rg, Lf);
-                else halves<1>(h, P, Rg, Lf);
-                sm.H[hs][hk][hy][hx] = (hk & 1) ? Lf : Rg;
+                Halves hv;
+                cell_halves(h, hv);
+                sm.H[hs][hk][hy][hx] = hk == 0 ? hv.R[0] : hk == 1 ? hv.L[0] : hk == 2 ? hv.R[1] : hv.L[1];
             }
             if (act && q >= 2) {
                 // update plane c = q - 1 (z = z0 + q - 2)
-                const int cs = (q - 1) & 1;
+                const int cs = hs ^ 1;
                 const float4 l = sm.H[cs][0][ty + 1][tx];        // Rx of the left cell
                 const float4 r = sm.H[cs][1][ty + 1][tx + 2];    // Lx of the right cell
                 const float4 d = sm.H[cs][2][ty][tx + 1];        // Ry of the cell below
                 const float4 p = sm.H[cs][3][ty + 2][tx + 1];    // Ly of the cell above
-                const float sx_ = ((l.x + r.x) + (d.x + p.x)) + (Rz_prev.x + Lz_n.x);
-                const float sy_ = ((l.y + r.y) + (d.y + p.y)) + (Rz_prev.y + Lz_n.y);
-                const float sz_ = ((l.z + r.z) + (d.z + p.z)) + (Rz_prev.z + Lz_n.z);
-                const float sw_ = ((l.w + r.w) + (d.w + p.w)) + (Rz_prev.w + Lz_n.w);
-                const V4<float> o = {c0 * uc.x + c1 * sx_, c0 * uc.y + c1 * sy_,
-                                     c0 * uc.z + c1 * sz_, c0 * uc.w + c1 * sw_};
-                st4(Og + (int64_t)(z0 + q - 2) * sxy + own_col, o);
+                const float2 slo = __fadd2_rn(__fadd2_rn(__fadd2_rn(lo2(l), lo2(r)), __fadd2_rn(lo2(d), lo2(p))),
+                                              __fadd2_rn(lo2(Rz_prev), lo2(Lz_n)));
+                const float2 shi = __fadd2_rn(__fadd2_rn(__fadd2_rn(hi2(l), hi2(r)), __fadd2_rn(hi2(d), hi2(p))),
+                                              __fadd2_rn(hi2(Rz_prev), hi2(Lz_n)));
+                const float2 cc0 = make_float2(c0, c0), cc1 = make_float2(c1, c1);
+                const float2 olo = __ffma2_rn(cc0, make_float2(uc.x, uc.y), __fmul2_rn(cc1, slo));
+                const float2 ohi = __ffma2_rn(cc0, make_float2(uc.z, uc.w), __fmul2_rn(cc1, shi));
+                st4(out, V4<float>{olo.x, olo.y, ohi.x, ohi.y});
+                out += sxy;
             }
             Rz_prev = Rz_c;
             Rz_c = Rz_n;
             uc = un;
+            slot = slot + 1 == S ? 0 : slot + 1;
         }
         cp_async_wait<0>();
         __syncthreads();

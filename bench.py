@@ -19,6 +19,7 @@ no cross-box exchange), value = total cell-updates of all ranks / max time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -26,6 +27,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -47,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=5)
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -159,35 +164,41 @@ def make_params(w, precision):
 
 
 class DeviceRun:
-    """The workload resident in HBM; reset() restores the initial state."""
+    """The workload resident in HBM (all its boxes in one handle); reset()
+    restores the initial state."""
 
     def __init__(self, w, precision):
         import torch
         from paper_1508_07888_b300 import binding as B
         self.torch, self.B, self.w = torch, B, w
-        box = w.boxes[0]
         self.p = make_params(w, precision)
         fp = torch.float64 if precision != B.RT_PREC_SPLIT else torch.float32
-        U, xHI, T = box.initial_state(w.ngroups)
-        dev = "cuda"
-        self.U0 = torch.as_tensor(U, dtype=fp, device=dev)
-        self.x0 = torch.as_tensor(xHI, dtype=torch.float64, device=dev)
-        self.T0 = torch.as_tensor(T, dtype=torch.float64, device=dev)
-        st = B.BoxState(U=self.U0.clone(), xHI=self.x0.clone(), T=self.T0.clone(),
-                        n0=torch.as_tensor(box.n0, dtype=fp, device=dev), dx=box.dx,
-                        nunit=w.nunit(box))
-        self.state = st
-        self.solver = B.Solver(self.p, [st])
-        self.solver.set_sources(0, box.src_cells, box.src_Q)
-        self.state_bytes = sum(t.numel() * t.element_size() for t in (st.U, st.xHI, st.T, st.n0))
+        self.init, states = [], []
+        for box in w.boxes:
+            U, xHI, T = box.initial_state(w.ngroups)
+            U0 = torch.as_tensor(U, dtype=fp, device="cuda")
+            x0 = torch.as_tensor(xHI, dtype=torch.float64, device="cuda")
+            T0 = torch.as_tensor(T, dtype=torch.float64, device="cuda")
+            self.init.append((U0, x0, T0))
+            states.append(B.BoxState(U=U0.clone(), xHI=x0.clone(), T=T0.clone(),
+                                     n0=torch.as_tensor(box.n0, dtype=fp, device="cuda"),
+                                     dx=box.dx, nunit=w.nunit(box)))
+        self.states = states
+        self.state = states[0]
+        self.solver = B.Solver(self.p, states)
+        for i, box in enumerate(w.boxes):
+            self.solver.set_sources(i, box.src_cells, box.src_Q)
+        self.state_bytes = sum(t.numel() * t.element_size()
+                               for st in states for t in (st.U, st.xHI, st.T, st.n0))
 
     def reset(self):
-        self.state.U.copy_(self.U0)
-        self.state.xHI.copy_(self.x0)
-        self.state.T.copy_(self.T0)
+        for st, (U0, x0, T0) in zip(self.states, self.init):
+            st.U.copy_(U0)
+            st.xHI.copy_(x0)
+            st.T.copy_(T0)
 
-    def run(self, nsteps):
-        code = self.solver.step(nsteps)
+    def run(self, nsteps, hist=None):
+        code = self.solver.step(nsteps, hist)
         if code != self.B.RT_OK:
             raise RuntimeError(f"rt_step status {code}: {self.B.rt_last_error(self.solver.h)}")
 
@@ -196,13 +207,15 @@ class DeviceRun:
 
 
 def time_device(w, precision, K, W, nsteps, ws, profile):
-    """K timed bench steps (reset + nsteps radiative steps) after W warm-ups."""
+    """K timed bench steps (reset + nsteps radiative steps) after W warm-ups.
+    The diagnostics history of every step is written to a device buffer."""
     import torch
     from paper_1508_07888_b300 import binding as B
     r = DeviceRun(w, precision)
+    hist = torch.zeros((nsteps, len(w.boxes), B.RT_NDIAG), dtype=torch.float64, device="cuda")
     for _ in range(W):
         r.reset()
-        r.run(nsteps)
+        r.run(nsteps, hist)
     B.rt_set_profiling(r.solver.h, profile)
     torch.cuda.synchronize()
     barrier(ws)
@@ -211,7 +224,7 @@ def time_device(w, precision, K, W, nsteps, ws, profile):
     e0.record()
     for _ in range(K):
         r.reset()
-        r.run(nsteps)
+        r.run(nsteps, hist)
     e1.record()
     torch.cuda.synchronize()
     barrier(ws)
@@ -220,9 +233,12 @@ def time_device(w, precision, K, W, nsteps, ws, profile):
     kern = {name: {"ms_total": st.kernel_ms[j], "launches": int(st.kernel_launches[j])}
             for j, name in enumerate(B.KERNELS) if st.kernel_launches[j] > 0}
     diag = list(st.last_diag)
+    h = hist.cpu().numpy()
+    cells = np.array([b.ncell for b in w.boxes], dtype=np.float64)
+    mean_sub = float(np.sum(h[:, :, 4] * cells) / (nsteps * cells.sum()))
     nbytes = r.state_bytes
     r.close()
-    return ms, kern, diag, nbytes
+    return ms, kern, diag, nbytes, mean_sub
 
 
 def e2e_host(w, precision, K, W, nsteps):
@@ -291,6 +307,89 @@ def cpu_baseline(w, steps):
                       f"({sec:.1f} s, FP64 C oracle, 1 thread; early steps carry fewer "
                       f"chemistry sub-cycles than the 500-step average)",
             "cpu": cpu_model(), "host_cpu_count": os.cpu_count()}
+
+
+def ensemble_run(B, ws, K=3):
+    """The batched workload: 64 periodic boxes of side 32-96 (2 groups, 1-16
+    sources each) in one handle, 100 radiative steps per run, each step one
+    launch per kernel over all boxes, replayed from the captured graph."""
+    import torch
+    from paper_1508_07888_b300 import inputs as I
+    w = I.ensemble()
+    r = DeviceRun(w, B.RT_PREC_SPLIT)
+    r.reset()
+    r.run(w.steps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        r.reset()
+        r.run(w.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    r.close()
+    return {"value": w.cells * w.steps * K * ws / (ms / 1e3), "unit": UNIT,
+            "ms_per_run": ms / K, "boxes": len(w.boxes), "cells": w.cells,
+            "rt_steps_per_run": w.steps, "launches_per_step": 2, "graph": True}
+
+
+def adjoint_run():
+    """The adjoint workload (64^3, 16 sources, 1 group, 4 fixed chemistry
+    intervals, 200 steps, checkpoints every 20): forward and reverse time of
+    one gradient of an ionised-fraction-history loss."""
+    import torch
+    from paper_1508_07888_b300 import binding as B
+    from paper_1508_07888_b300 import inputs as I
+    from paper_1508_07888_b300.autograd import HistoryRun, ionisation_history
+    w = I.adjoint_box()
+    box = w.boxes[0]
+    t = B.rt_group_table(w.edges_eV, w.T_bb)
+    t = {k: I.f32(v) for k, v in t.items()}
+    p = B.make_params(1, t, w.c_red, nsub=w.nsub, precision=B.RT_PREC_FP64)
+    U, xHI, T = box.initial_state(1)
+    st = B.BoxState(U=torch.as_tensor(U, device="cuda"), xHI=torch.as_tensor(xHI, device="cuda"),
+                    T=torch.as_tensor(T, device="cuda"),
+                    n0=torch.as_tensor(box.n0, dtype=torch.float64, device="cuda"),
+                    dx=box.dx, nunit=w.nunit(box))
+    run = HistoryRun(p, st, box.src_cells, w.steps, ckpt_every=20)
+    Q = torch.tensor(box.src_Q, dtype=torch.float64, requires_grad=True)
+    n0 = torch.as_tensor(box.n0, dtype=torch.float64, device="cuda").requires_grad_(True)
+    with torch.no_grad():
+        Xt = ionisation_history(Q * torch.as_tensor(I.target_perturbation(len(box.src_Q))), n0, run)
+    X = ionisation_history(Q, n0, run)                    # warm-up
+    ((X - Xt) ** 2).mean().backward()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = ionisation_history(Q, n0, run)
+    L = ((X - Xt) ** 2).mean()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    run.close()
+    fwd = box.ncell * w.steps / (t1 - t0)
+    return {"workload": w.name, "forward_ms": 1e3 * (t1 - t0), "backward_ms": 1e3 * (t2 - t1),
+            "forward_cell_updates_per_s": fwd, "backward_over_forward": (t2 - t1) / (t1 - t0),
+            "form": "FP64", "checkpoint_every": 20}
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of each kernel from the committed ncu summary,
+    kept only while the kernel source still has the hash it was captured at."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1508_07888_b300", "csrc", "rt_kernels.cuh")
+    out = {}
+    try:
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        for line in open(path):
+            f = line.split()
+            if len(f) == 4 and not line.startswith("#") and f[3] == digest:
+                out[f[0]] = float(f[2])
+    except OSError:
+        pass
+    return out
 
 
 def cpu_model():
@@ -363,8 +462,8 @@ def main():
 
     clocks = Clocks(local)
     clocks.start()
-    ms, kern, diag, state_bytes = time_device(w, B.RT_PREC_SPLIT, args.steps, args.warmup,
-                                              nsteps, ws, profile=True)
+    ms, kern, diag, state_bytes, mean_sub = time_device(w, B.RT_PREC_SPLIT, args.steps,
+                                                        args.warmup, nsteps, ws, profile=True)
     clk = clocks.stop()
     ms = max_over_ranks(ws, ms)
     value = units_per_step * args.steps * ws / (ms / 1e3)
@@ -372,8 +471,8 @@ def main():
 
     fp64 = None
     if not args.no_fp64_form:
-        ms64, kern64, _, _ = time_device(w, B.RT_PREC_FP64, args.steps, args.warmup, nsteps, ws,
-                                         profile=True)
+        ms64, kern64, _, _, _ = time_device(w, B.RT_PREC_FP64, args.steps, args.warmup, nsteps,
+                                            ws, profile=True)
         ms64 = max_over_ranks(ws, ms64)
         v64 = units_per_step * args.steps * ws / (ms64 / 1e3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.steps,
@@ -388,27 +487,40 @@ def main():
         e2e = {"value": units_per_step * args.steps * ws / sec, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # per-kernel shares and the roofline of the dominant kernel
+    # per-kernel shares and the rooflines (algorithmic units per launch over
+    # the CUDA-event launch time measured above)
     tot = sum(v["ms_total"] for v in kern.values())
     per_launch = {k: v["ms_total"] / max(v["launches"], 1) for k, v in kern.items()}
     shares = {k: v["ms_total"] / tot for k, v in kern.items()} if tot > 0 else {}
     pk = peaks()
     hbm_peak = pk["hbm_gbs"] if pk else 6400.0
     peak_note = "of measured" if pk else "of fallback"
+    traffic = profiled_traffic()
     G = w.ngroups
     t_bytes = 32.0 * G * box.ncell                  # read + write of (N, F) in FP32, per launch
     t_ach = t_bytes / (per_launch["transport"] * 1e-3) / 1e9
     roof_t = {"kernel": "transport", "bound": "hbm", "achieved": t_ach, "peak": hbm_peak,
-              "unit": "GB/s", "frac": t_ach / hbm_peak, "traffic": None,
+              "unit": "GB/s", "frac": t_ach / hbm_peak,
+              "traffic": traffic.get("transport"),
               "algorithmic_bytes_per_launch": t_bytes, "peak_note": peak_note}
+    # chemistry: FP64 flops of the accepted sub-cycles (update formulas, rate
+    # fits and the dtau estimate; elementary functions and divisions count 1),
+    # 25 G + 108 per cell and accepted sub-cycle, against the FP64 pipe peak:
+    # 148 SMs x 2 DFMA/clock x 2 flop x 2032 MHz
+    fp64_peak = 148 * 2 * 2 * 2032e6 / 1e12
+    c_flops = (25.0 * G + 108.0) * box.ncell * mean_sub
+    c_ach = c_flops / (per_launch["chemistry"] * 1e-3) / 1e12
+    roof_c = {"kernel": "chemistry", "bound": "alu", "achieved": c_ach, "peak": fp64_peak,
+              "unit": "TFLOP/s", "frac": c_ach / fp64_peak,
+              "traffic": traffic.get("chemistry"),
+              "algorithmic_flops_per_launch": c_flops, "mean_subcycles": mean_sub,
+              "peak_note": "FP64 pipe, derived from ncu's 2 DFMA/clock/SM and the 2032 MHz "
+                           "maximum clock"}
     dominant = max(shares, key=shares.get) if shares else "transport"
-    c_bytes = (32.0 * G + 36.0) * box.ncell        # chemistry: read U*, xHI, T, n0; write U, xHI, T
-    c_ach = c_bytes / (per_launch["chemistry"] * 1e-3) / 1e9
-    roof_c = {"kernel": "chemistry", "bound": "alu", "achieved": c_ach, "peak": hbm_peak,
-              "unit": "GB/s", "frac": c_ach / hbm_peak, "traffic": None,
-              "algorithmic_bytes_per_launch": c_bytes,
-              "note": "FP64-pipe bound; bytes/launch over time shown against HBM peak"}
     roofline = roof_c if dominant == "chemistry" else roof_t
+
+    ens = None if args.no_ensemble else ensemble_run(B, ws)
+    adj = None if args.no_adjoint else adjoint_run()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -429,6 +541,7 @@ def main():
             "kernels": {k: {"ms_per_launch": per_launch[k], "share": shares.get(k),
                             "launches": kern[k]["launches"]} for k in kern},
             "fp64_form": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "ensemble": ens, "adjoint": adj,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "final_diag": dict(zip(B.DIAG_NAMES, diag)),
         }

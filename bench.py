@@ -87,6 +87,14 @@ def max_over_ranks(ws, v: float) -> float:
     return float(t.item())
 
 
+def replica_value(ws, units_local: float, sec_local: float):
+    """Whole-job throughput of ws replicas that each processed units_local in
+    sec_local: all ranks' units over the slowest rank's time.  Returns
+    (value, max seconds); every rank gets the same numbers."""
+    sec = max_over_ranks(ws, sec_local)
+    return units_local * ws / sec, sec
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     """nvidia-smi sampling during the timed region (every 200 ms)."""
@@ -327,9 +335,10 @@ def ensemble_run(B, ws, K=3):
         r.run(w.steps)
     e1.record()
     torch.cuda.synchronize()
-    ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    val, sec = replica_value(ws, w.cells * w.steps * K, e0.elapsed_time(e1) / 1e3)
+    ms = sec * 1e3
     r.close()
-    return {"value": w.cells * w.steps * K * ws / (ms / 1e3), "unit": UNIT,
+    return {"value": val, "unit": UNIT,
             "ms_per_run": ms / K, "boxes": len(w.boxes), "cells": w.cells,
             "rt_steps_per_run": w.steps, "launches_per_step": 2, "graph": True}
 
@@ -409,6 +418,12 @@ def peaks():
         return None
 
 
+def chem_flops_per_subcycle(G: int, ots: bool) -> float:
+    """Algorithmic FP64 flops of one accepted chemistry sub-cycle (a5-a8 and
+    the rate fits), counted from the formulas as written."""
+    return 22.0 * G + 182.0 - (27.0 if ots else 0.0)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -465,16 +480,16 @@ def main():
     ms, kern, diag, state_bytes, mean_sub = time_device(w, B.RT_PREC_SPLIT, args.steps,
                                                         args.warmup, nsteps, ws, profile=True)
     clk = clocks.stop()
-    ms = max_over_ranks(ws, ms)
-    value = units_per_step * args.steps * ws / (ms / 1e3)
+    value, sec = replica_value(ws, units_per_step * args.steps, ms / 1e3)
+    ms = sec * 1e3
     ms_step = ms / args.steps
 
     fp64 = None
     if not args.no_fp64_form:
         ms64, kern64, _, _, _ = time_device(w, B.RT_PREC_FP64, args.steps, args.warmup, nsteps,
                                             ws, profile=True)
-        ms64 = max_over_ranks(ws, ms64)
-        v64 = units_per_step * args.steps * ws / (ms64 / 1e3)
+        v64, sec64 = replica_value(ws, units_per_step * args.steps, ms64 / 1e3)
+        ms64 = sec64 * 1e3
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.steps,
                 "split_over_fp64": value / v64,
                 "kernels_ms_per_launch": {k: v["ms_total"] / max(v["launches"], 1)
@@ -483,8 +498,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         sec, h2d, d2h = e2e_host(w, B.RT_PREC_SPLIT, args.steps, min(args.warmup, 1), nsteps)
-        sec = max_over_ranks(ws, sec)
-        e2e = {"value": units_per_step * args.steps * ws / sec, "unit": UNIT,
+        v_e2e, sec = replica_value(ws, units_per_step * args.steps, sec)
+        e2e = {"value": v_e2e, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # per-kernel shares and the rooflines (algorithmic units per launch over
@@ -503,12 +518,15 @@ def main():
               "unit": "GB/s", "frac": t_ach / hbm_peak,
               "traffic": traffic.get("transport"),
               "algorithmic_bytes_per_launch": t_bytes, "peak_note": peak_note}
-    # chemistry: FP64 flops of the accepted sub-cycles (update formulas, rate
-    # fits and the dtau estimate; elementary functions and divisions count 1),
-    # 25 G + 108 per cell and accepted sub-cycle, against the FP64 pipe peak:
-    # 148 SMs x 2 DFMA/clock x 2 flop x 2032 MHz
+    # chemistry: FP64 flops of one accepted sub-cycle, counted from the update
+    # formulas as written (+ - x / each 1, a Horner step 2, exp and log 1):
+    # rates from the table 116 (5 degree-10 polynomials 100, the variable and
+    # the two exp(-c/T) factors 16; 96 with OTS, which skips alpha_A), the
+    # dtau estimate 4 G + 19, the trial 18 G + 47 (+7 for the recombination
+    # photons of group 1 without OTS, in the 47) -> 22 G + 182, against the
+    # FP64 pipe peak: 148 SMs x 2 DFMA/clock x 2 flop x 2032 MHz
     fp64_peak = 148 * 2 * 2 * 2032e6 / 1e12
-    c_flops = (25.0 * G + 108.0) * box.ncell * mean_sub
+    c_flops = chem_flops_per_subcycle(G, w.ots) * box.ncell * mean_sub
     c_ach = c_flops / (per_launch["chemistry"] * 1e-3) / 1e12
     roof_c = {"kernel": "chemistry", "bound": "alu", "achieved": c_ach, "peak": fp64_peak,
               "unit": "TFLOP/s", "frac": c_ach / fp64_peak,

@@ -70,28 +70,28 @@ __device__ RatesD rates_d_exact(const Phys &ph, double T)
     return r;
 }
 
-// the tabulated rates of the forward pass, differentiated through the
-// interpolating polynomials (d/dll = (2/h) d/dt, dll/dT = -1/T)
+// the tabulated rates of the forward pass (rates_tab), differentiated
+// through the interpolating polynomials: d/dT = (dt/dT) d/dt, with
+// dt/dT = 2 / (interval width) = 2^(SUB + 1 - e)
 __device__ RatesD rates_d(const Phys &ph, const double *tab, double T)
 {
     if (!tab || ph.rates_const) return rates_d_exact(ph, T);
-    const double invT = 1.0 / T;
-    const double lam = (2.0 * rtd::T_HI) * invT;
-    const double ll = log(lam);
-    const double u = (ll - RTD_TAB_LL0) * (1.0 / RTD_TAB_H);
-    if (!(u >= 0.0 && u < (double)RTD_TAB_NINT)) return rates_d_exact(ph, T);
-    const int j = (int)u;
-    const double t = 2.0 * (u - (double)j) - 1.0;
+    int j;
+    double t;
+    if (!tab_pos(T, j, t)) return rates_d_exact(ph, T);
+    const int e = (int)(__double_as_longlong(T) >> 52) - 1023;
+    const double dtdT = ldexp(1.0, RTD_TAB_SUB + 1 - e);
+    const double *a = tab + (size_t)j * (RTD_TAB_NF * RTD_TAB_NC);
     double g[RTD_TAB_NF], dg[RTD_TAB_NF];
     for (int f = 0; f < RTD_TAB_NF; f++) {
-        const double *a = tab + (f * RTD_TAB_NINT + j) * RTD_TAB_NC;
-        double p = a[RTD_TAB_NC - 1], dp = 0.0;
+        const double *c = a + f * RTD_TAB_NC;
+        double p = c[RTD_TAB_NC - 1], dp = 0.0;
         for (int i = RTD_TAB_NC - 2; i >= 0; i--) {
             dp = dp * t + p;
-            p = p * t + a[i];
+            p = p * t + c[i];
         }
         g[f] = p;
-        dg[f] = dp * (2.0 / RTD_TAB_H) * (-invT);          // d/dT
+        dg[f] = dp * dtdT;
     }
     RatesD r;
     r.aB = g[1];
@@ -100,12 +100,18 @@ __device__ RatesD rates_d(const Phys &ph, const double *tab, double T)
     r.daA = ph.ots ? dg[1] : dg[0];
     r.kR = g[2];
     r.dkR = dg[2];
-    r.beta = exp(g[3] - 0.5 * lam);
-    r.dbeta = r.beta * (dg[3] + 0.5 * lam * invT);
-    const double cce = exp(g[4] - 118348.0 * invT);
-    const double dcce = cce * (dg[4] + 118348.0 * invT * invT);
-    r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
-    r.dkC = rtd::KB * rtd::T_HI * r.dbeta + dcce;
+    if (T >= RTD_TAB_TCUT) {
+        const double invT = 1.0 / T;
+        r.beta = exp(g[3] - rtd::T_HI * invT);
+        r.dbeta = r.beta * (dg[3] + rtd::T_HI * invT * invT);
+        const double cce = exp(g[4] - 118348.0 * invT);
+        const double dcce = cce * (dg[4] + 118348.0 * invT * invT);
+        r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
+        r.dkC = rtd::KB * rtd::T_HI * r.dbeta + dcce;
+    } else {                       // both factors are exactly zero here
+        r.beta = r.dbeta = 0.0;
+        r.kC = r.dkC = 0.0;
+    }
     return r;
 }
 

@@ -46,26 +46,15 @@ cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &
     return cudaGetLastError();
 }
 
-// dynamic shared memory of the chemistry kernel: the rate table
-template <typename K>
-static size_t chem_smem(K kernel, const rtd::Phys &ph)
-{
-    const size_t bytes = (ph.rtab && !ph.rates_const) ? rate_table_doubles() * sizeof(double) : 0;
-    if (bytes) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return bytes;
-}
-
 template <int G>
 static void chem_g(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, const rtd::DiagBuf &db)
 {
     if (fp64) {
         auto k = rtk::k_chem<G, double, double, false>;
-        k<<<L.grid, RTD_CHEM_BLOCK, chem_smem(k, ph), L.stream>>>(L.boxes, L.nboxes, L.nitems, ph,
-                                                                  ctl, db);
+        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db);
     } else {
         auto k = rtk::k_chem<G, float, float, false>;
-        k<<<L.grid, RTD_CHEM_BLOCK, chem_smem(k, ph), L.stream>>>(L.boxes, L.nboxes, L.nitems, ph,
-                                                                  ctl, db);
+        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db);
     }
 }
 
@@ -105,14 +94,9 @@ int transport_occupancy_fast(bool fp64)
 
 int chem_occupancy_fast(bool fp64, int G)
 {
-    const size_t tb = rate_table_doubles() * sizeof(double);
 #define OCC_G(g)                                                                                \
-    (fp64 ? (cudaFuncSetAttribute(rtk::k_chem<g, double, double, false>,                         \
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb),         \
-             occ((const void *)rtk::k_chem<g, double, double, false>, RTD_CHEM_BLOCK, tb))       \
-          : (cudaFuncSetAttribute(rtk::k_chem<g, float, float, false>,                           \
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb),         \
-             occ((const void *)rtk::k_chem<g, float, float, false>, RTD_CHEM_BLOCK, tb)))
+    (fp64 ? occ((const void *)rtk::k_chem<g, double, double, false>, RTD_CHEM_BLOCK, 0)          \
+          : occ((const void *)rtk::k_chem<g, float, float, false>, RTD_CHEM_BLOCK, 0))
     switch (G) {
     case 1: return OCC_G(1);
     case 2: return OCC_G(2);

@@ -32,14 +32,9 @@ cudaError_t transport_strict(const Launch &L, int zc, const rtd::Phys &ph, rtd::
 
 cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, const rtd::DiagBuf &db)
 {
-    const size_t tb = (ph.rtab && !ph.rates_const) ? rate_table_doubles() * sizeof(double) : 0;
 #define CHEM_G(g)                                                                                \
-    do {                                                                                         \
-        if (tb) cudaFuncSetAttribute(rtk::k_chem<g, double, double, true>,                       \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);      \
-        rtk::k_chem<g, double, double, true><<<L.grid, RTD_CHEM_BLOCK, tb, L.stream>>>(          \
-            L.boxes, L.nboxes, L.nitems, ph, ctl, db);                                           \
-    } while (0)
+    rtk::k_chem<g, double, double, true><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(               \
+        L.boxes, L.nboxes, L.nitems, ph, ctl, db)
     switch (G) {
     case 1: CHEM_G(1); break;
     case 2: CHEM_G(2); break;
@@ -74,11 +69,7 @@ int transport_occupancy(bool fp64, bool strict)
 int chem_occupancy(bool fp64, bool strict, int G)
 {
     if (!strict) return chem_occupancy_fast(fp64, G);
-    const size_t tb = rate_table_doubles() * sizeof(double);
-#define OCC_S(g)                                                                                 \
-    (cudaFuncSetAttribute(rtk::k_chem<g, double, double, true>,                                  \
-                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb),                 \
-     occ((const void *)rtk::k_chem<g, double, double, true>, RTD_CHEM_BLOCK, tb))
+#define OCC_S(g) occ((const void *)rtk::k_chem<g, double, double, true>, RTD_CHEM_BLOCK, 0)
     switch (G) {
     case 1: return OCC_S(1);
     case 2: return OCC_S(2);

@@ -4,14 +4,15 @@
 // The rate fits (Hui & Gnedin 1997 recombination, collisional ionisation and
 // recombination cooling; exp(-118348/T)/(1 + sqrt(T/1e5)) excitation cooling;
 // 1.42e-27 x 1.3 sqrt(T) bremsstrahlung) are evaluated here in long double and
-// interpolated, per interval of ll = ln(2 T_HI / T), by a degree-10 Chebyshev
-// polynomial rewritten in the monomial basis of the local variable
-// t in [-1, 1].  Tabulated functions:
+// interpolated on 2^RTD_TAB_SUB equal intervals of T per binade, 1 K <= T <
+// 2^30 K, each by a degree-6 Chebyshev polynomial rewritten in the monomial
+// basis of the local variable t = 2 (T - T_a)/(T_b - T_a) - 1 in [-1, 1).
+// Tabulated functions (layout [interval][function][coefficient]):
 //   0: alpha_A   1: alpha_B   2: recombination (case A or B) + free-free cooling
-//   3: ln(beta) + lambda/2            (beta = exp(f3 - lambda/2))
+//   3: ln(beta) + T_HI/T               (beta = exp(f3 - T_HI/T))
 //   4: ln(excitation cooling) + 118348/T
 // The two exp(-c/T) factors stay outside the tables so every tabulated
-// function is smooth in ll.  The table is checked against the long-double
+// function is smooth in T.  The table is checked against the long-double
 // fits before use; the kernel evaluates the fits directly when it is absent.
 #include <cmath>
 
@@ -40,7 +41,7 @@ LD fit_kR(LD T, bool ots)
                        : 1.778e-29L * T * powl(l, 1.965L) / powl(1 + powl(l / 0.541L, 0.502L), 2.697L);
     return rec + 1.42e-27L * 1.3L * sqrtl(T);
 }
-LD fit_lnbeta_plus(LD T)   // ln(beta) + lambda/2
+LD fit_lnbeta_plus(LD T)   // ln(beta) + T_HI/T  (T_HI/T = lambda/2)
 {
     const LD l = 2 * THI / T;
     return logl(21.11L) - 1.5L * logl(T) - 1.089L * logl(l) - 1.101L * log1pl(powl(l / 0.354L, 0.874L));
@@ -50,9 +51,8 @@ LD fit_lncce_plus(LD T)    // ln(excitation cooling) + 118348/T
     return logl(7.5e-19L) - log1pl(sqrtl(T / 1.0e5L));
 }
 
-LD fit(int f, LD ll, bool ots)
+LD fit(int f, LD T, bool ots)
 {
-    const LD T = 2 * THI / expl(ll);
     switch (f) {
     case 0: return fit_aA(T);
     case 1: return fit_aB(T);
@@ -66,9 +66,10 @@ LD fit(int f, LD ll, bool ots)
 
 namespace rtl {
 
-// fills out[RTD_TAB_NF][RTD_TAB_NINT][RTD_TAB_NC]; returns true when the
+// fills out[RTD_TAB_NINT][RTD_TAB_NF][RTD_TAB_NC]; returns true when the
 // table reproduces the long-double fits to 1e-13 (relative for functions
-// 0-2, absolute for the logarithms 3-4) at 17 points per interval
+// 0-2, absolute for the logarithms 3-4) at 17 points per interval, and when
+// both exp(-c/T) factors are exactly zero in double below RTD_TAB_TCUT
 bool build_rate_table(bool ots, double *out)
 {
     const int N = RTD_TAB_NC;
@@ -79,20 +80,22 @@ bool build_rate_table(bool ots, double *out)
     for (int n = 2; n < N; n++)
         for (int i = 0; i < N; i++)
             cheb[n][i] = (i > 0 ? 2 * cheb[n - 1][i - 1] : 0) - cheb[n - 2][i];
-    for (int f = 0; f < RTD_TAB_NF; f++) {
-        for (int j = 0; j < RTD_TAB_NINT; j++) {
-            const LD a = (LD)RTD_TAB_LL0 + j * (LD)RTD_TAB_H;
+    const int per = 1 << RTD_TAB_SUB;
+    for (int j = 0; j < RTD_TAB_NINT; j++) {
+        const LD lo = ldexpl(1.0L + (LD)(j % per) / per, RTD_TAB_E0 + j / per);
+        const LD hi = ldexpl(1.0L + (LD)(j % per + 1) / per, RTD_TAB_E0 + j / per);
+        for (int f = 0; f < RTD_TAB_NF; f++) {
             LD fv[RTD_TAB_NC], c[RTD_TAB_NC];
             for (int m = 0; m < N; m++) {
                 const LD t = cosl(M_PIl * (m + 0.5L) / N);
-                fv[m] = fit(f, a + (t + 1) * 0.5L * (LD)RTD_TAB_H, ots);
+                fv[m] = fit(f, lo + (t + 1) * 0.5L * (hi - lo), ots);
             }
             for (int n = 0; n < N; n++) {
                 LD s = 0;
                 for (int m = 0; m < N; m++) s += fv[m] * cosl(M_PIl * n * (m + 0.5L) / N);
                 c[n] = (n == 0 ? 1.0L : 2.0L) * s / N;
             }
-            double *o = out + ((size_t)f * RTD_TAB_NINT + j) * N;
+            double *o = out + ((size_t)j * RTD_TAB_NF + f) * N;
             for (int i = 0; i < N; i++) {
                 LD s = 0;
                 for (int n = 0; n < N; n++) s += c[n] * cheb[n][i];
@@ -102,12 +105,16 @@ bool build_rate_table(bool ots, double *out)
                 const double t = -1.0 + 2.0 * k / 16.0;
                 double p = o[N - 1];
                 for (int i = N - 2; i >= 0; i--) p = p * t + o[i];
-                const LD ex = fit(f, a + ((LD)t + 1) * 0.5L * (LD)RTD_TAB_H, ots);
+                const LD ex = fit(f, lo + ((LD)t + 1) * 0.5L * (hi - lo), ots);
                 const LD err = f <= 2 ? fabsl((p - ex) / ex) : fabsl(p - ex);
                 if (!(err <= 1e-13L)) return false;
             }
         }
     }
+    // the factors the kernel skips below RTD_TAB_TCUT (both grow with T)
+    const double tc = RTD_TAB_TCUT;
+    if (std::exp((double)fit_lnbeta_plus(tc) - (double)THI / tc) != 0.0) return false;
+    if (std::exp((double)fit_lncce_plus(tc) - 118348.0 / tc) != 0.0) return false;
     return true;
 }
 

@@ -263,6 +263,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMemset(h->d_lastdiag, 0, sizeof(double) * RTD_NDIAG * nboxes));
                 CU(h, cudaMalloc(&h->d_ctl, sizeof(rtd::Ctl)));
                 CU(h, cudaMallocHost(&h->h_ctl, sizeof(rtd::Ctl)));
+                std::memset(h->h_ctl, 0, sizeof(rtd::Ctl));
                 CU(h, cudaMallocHost(&h->h_lastdiag, sizeof(double) * RTD_NDIAG * nboxes));
                 std::memset(h->h_lastdiag, 0, sizeof(double) * RTD_NDIAG * nboxes);
                 int dev = 0, nsm = 1;
@@ -405,6 +406,8 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
     c->nboxes = h->nboxes;
     c->err = 0;
     c->nclamp = 0;
+    c->chem_next = 0;
+    c->chem_fin = 0;
     CU(h, cudaEventRecord(h->ev_in, h->user));
     CU(h, cudaStreamWaitEvent(h->s, h->ev_in, 0));
     CU(h, cudaMemcpyAsync(h->d_ctl, c, sizeof(rtd::Ctl), cudaMemcpyHostToDevice, h->s));
@@ -537,6 +540,8 @@ extern "C" int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, cons
         c->nboxes = 1;
         c->err = 0;
         c->nclamp = 0;
+        c->chem_next = 0;
+        c->chem_fin = 0;
         CU(h, cudaMemcpyAsync(h->d_ctl, c, sizeof(rtd::Ctl), cudaMemcpyHostToDevice, s));
         // forward from (U0, xHI0, T0) with a checkpoint every ck steps
         CU(h, cudaMemcpyAsync(D.U, U0, bU, cudaMemcpyDeviceToDevice, s));

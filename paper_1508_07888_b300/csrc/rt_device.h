@@ -22,13 +22,19 @@
 
 #define RTD_MAXCYC 1000000   // sub-cycles per cell and step before giving up
 
-// rate tables: piecewise polynomials in ll = ln(2 T_HI / T) on equal
-// intervals covering 1 K <= T <= 1e9 K (see rate_table.cu)
-#define RTD_TAB_NF 5         // aA, aB, kR, ln(beta) + lambda/2, ln(cce) + 118348/T
-#define RTD_TAB_NINT 128
-#define RTD_TAB_NC 11        // degree 10 in the local variable t in [-1, 1]
-#define RTD_TAB_LL0 (-8.1)
-#define RTD_TAB_H 0.1625
+// rate tables: piecewise polynomials in T.  T in [2^E0, 2^E1) falls in
+// interval j = 2^SUB (e - E0) + (top SUB bits of T's mantissa), e = T's binary
+// exponent, so the index and the local variable t in [-1, 1) come from T's
+// bits (no logarithm); 2^SUB equal intervals per binade (see rate_table.cu)
+#define RTD_TAB_NF 5         // aA, aB, kR, ln(beta) + T_HI/T, ln(cce) + 118348/T
+#define RTD_TAB_E0 0         // 1 K
+#define RTD_TAB_E1 30        // 2^30 K = 1.07e9 K
+#define RTD_TAB_SUB 5
+#define RTD_TAB_NINT ((RTD_TAB_E1 - RTD_TAB_E0) << RTD_TAB_SUB)
+#define RTD_TAB_NC 7         // degree 6 in t
+// below this temperature both exp(-T_HI/T) and exp(-118348/T) factors of the
+// fits are exactly zero in double precision (checked when the table is built)
+#define RTD_TAB_TCUT 155.0
 
 namespace rtd {
 
@@ -47,7 +53,7 @@ struct Phys {
     double alphaA, alphaB, beta;  // rates_const values
     double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250
     double ln2THI;                // ln(2 T_HI)
-    const double *rtab;           // rate table [RTD_TAB_NF][RTD_TAB_NINT][RTD_TAB_NC] or null
+    const double *rtab;           // rate table [RTD_TAB_NINT][RTD_TAB_NF][RTD_TAB_NC] or null
     int bc[6];                    // -x,+x,-y,+y,-z,+z
 };
 
@@ -88,6 +94,8 @@ struct Ctl {
     int nboxes;
     unsigned int err;                 // RTD_ERR_* bits
     unsigned long long nclamp;        // post-transport flux-limit clamps
+    unsigned long long chem_next;     // chemistry: next work item to hand out
+    unsigned long long chem_fin;      // chemistry: blocks that found no more work
 };
 
 }  // namespace rtd

@@ -633,36 +633,57 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
     return r;
 }
 
-// The same rates from the tables built at set-up (rate_table.cu): Chebyshev
-// interpolants of degree 10 on 128 intervals of ll = ln(2 T_HI/T), accurate
-// to ~1e-15 relative; beta and the excitation cooling keep their
-// exp(-c/T) factor exact.  Outside 1 K .. 1e9 K the fits are evaluated directly.
+// Position of T in the rate tables (rate_table.cu): interval j and local
+// variable t in [-1, 1), both from T's bits.  For T = 2^e (1 + m), m in [0, 1),
+// j = 2^SUB (e - E0) + floor(2^SUB m) and t = 2 frac(2^SUB m) - 1, exactly.
+// Returns false outside [2^E0, 2^E1) (and for T <= 0, NaN, Inf).
+__device__ __forceinline__ bool tab_pos(double T, int &j, double &t)
+{
+    const long long bits = __double_as_longlong(T);
+    const int e = (int)(bits >> 52) - 1023;
+    if (e < RTD_TAB_E0 || e >= RTD_TAB_E1) return false;
+    constexpr int low = 52 - RTD_TAB_SUB;
+    j = ((e - RTD_TAB_E0) << RTD_TAB_SUB) + (int)((bits >> low) & ((1 << RTD_TAB_SUB) - 1));
+    // 1 + frac in [1, 2): the mantissa bits below the top SUB, moved up
+    const double y = __longlong_as_double(0x3FF0000000000000ll |
+                                          ((bits & ((1ll << low) - 1)) << RTD_TAB_SUB));
+    t = fma(y, 2.0, -3.0);
+    return true;
+}
+
+__device__ __forceinline__ double tab_poly(const double *c, double t)
+{
+    double p = __ldg(c + RTD_TAB_NC - 1);
+#pragma unroll
+    for (int i = RTD_TAB_NC - 2; i >= 0; i--) p = p * t + __ldg(c + i);
+    return p;
+}
+
+// The same rates from the tables built at set-up (rate_table.cu): degree-6
+// Chebyshev interpolants on 32 intervals of T per binade, accurate to ~1e-14
+// relative; beta and the excitation cooling keep their exp(-c/T) factor
+// exact, and below RTD_TAB_TCUT, where both factors are exactly zero in
+// double, they are not evaluated.  Outside 1 K .. 2^30 K the fits are
+// evaluated directly.
 __device__ __forceinline__ Rates rates_tab(const Phys &ph, const double *tab, double T)
 {
-    const double invT = 1.0 / T;
-    const double lam = (2.0 * rtd::T_HI) * invT;
-    const double ll = log(lam);
-    const double u = (ll - RTD_TAB_LL0) * (1.0 / RTD_TAB_H);
-    if (!(u >= 0.0 && u < (double)RTD_TAB_NINT)) return rates_at(ph, T);
-    const int j = (int)u;
-    const double t = 2.0 * (u - (double)j) - 1.0;
-    double g[RTD_TAB_NF];
-#pragma unroll
-    for (int f = 0; f < RTD_TAB_NF; f++) {
-        if (f == 0 && ph.ots) { g[0] = 0.0; continue; }
-        const double *a = tab + (f * RTD_TAB_NINT + j) * RTD_TAB_NC;
-        double p = a[RTD_TAB_NC - 1];
-#pragma unroll
-        for (int i = RTD_TAB_NC - 2; i >= 0; i--) p = p * t + a[i];
-        g[f] = p;
-    }
+    int j;
+    double t;
+    if (!tab_pos(T, j, t)) return rates_at(ph, T);
+    const double *a = tab + (size_t)j * (RTD_TAB_NF * RTD_TAB_NC);
     Rates r;
-    r.aB = g[1];
-    r.aA = ph.ots ? g[1] : g[0];
-    r.kR = g[2];
-    r.beta = exp(g[3] - 0.5 * lam);
-    const double cce = exp(g[4] - 118348.0 * invT);
-    r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
+    r.aB = tab_poly(a + 1 * RTD_TAB_NC, t);
+    r.aA = ph.ots ? r.aB : tab_poly(a, t);
+    r.kR = tab_poly(a + 2 * RTD_TAB_NC, t);
+    if (T >= RTD_TAB_TCUT) {
+        const double invT = 1.0 / T;
+        r.beta = exp(tab_poly(a + 3 * RTD_TAB_NC, t) - rtd::T_HI * invT);
+        const double cce = exp(tab_poly(a + 4 * RTD_TAB_NC, t) - 118348.0 * invT);
+        r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
+    } else {
+        r.beta = 0.0;
+        r.kC = 0.0;
+    }
     return r;
 }
 
@@ -883,15 +904,16 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
        DiagBuf db)
 {
     __shared__ int s_last;
-    extern __shared__ double s_tab[];
-    const double *tab = nullptr;
-    if (ph.rtab && !ph.rates_const) {
-        for (int i = threadIdx.x; i < RTD_TAB_NF * RTD_TAB_NINT * RTD_TAB_NC; i += blockDim.x)
-            s_tab[i] = ph.rtab[i];
+    __shared__ unsigned long long s_item;
+    const double *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
+    for (;;) {
+        // items are handed out one at a time, so blocks that draw cheap
+        // cells (cold gas) take more of them; the order of the work does
+        // not enter any result
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->chem_next, 1ull);
         __syncthreads();
-        tab = s_tab;
-    }
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int64_t it = (int64_t)s_item;
+        if (it >= nitems) break;
         const int b = find_box(boxes, nboxes, it, true);
         const BoxDev &B = boxes[b];
         const int64_t c = (it - B.citem0) * RTD_CHEM_BLOCK + threadIdx.x;
@@ -985,6 +1007,16 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
         if (s_last) {
             __threadfence();
             reduce_box(B, b, db, ctl);
+        }
+    }
+    // every block has drawn its last (empty) item before it counts itself
+    // here; the last one resets the counters for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->chem_fin, 1ull) == (unsigned long long)gridDim.x - 1ull) {
+            ctl->chem_next = 0ull;
+            ctl->chem_fin = 0ull;
+            __threadfence();
         }
     }
 }

@@ -227,6 +227,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     D.ncell = (int64_t)B.nx * B.ny * B.nz;
                     D.dx = B.dx;
                     D.nunit = B.nunit;
+                    D.inv_nunit = 1.0 / B.nunit;
                     D.dt = p->cfl * B.dx / (3.0 * p->c_red);
                     D.lam = p->c_red * D.dt / B.dx;
                     D.U = B.U;

@@ -63,6 +63,7 @@ struct BoxDev {
     int tiles_x, tiles_y, zchunks;   // transport tiling (zchunks unused: runs are balanced)
     int64_t ncell;
     double dx, nunit, dt, lam;        // lam = c dt / dx (Courant number)
+    double inv_nunit;                 // 1 / nunit
     void *U;                          // caller's state, [G][nz][ny][nx][4]
     void *Us;                         // post-transport state (library scratch)
     double *xHI, *T;

@@ -15,6 +15,8 @@
 
 #include <cstdint>
 
+#include <cstring>
+
 #include "rt_device.h"
 
 namespace rtk {
@@ -51,6 +53,90 @@ __device__ __forceinline__ void st4(V4<double> *p, const V4<double> &v)
     double2 *q = reinterpret_cast<double2 *>(p);
     q[0] = make_double2(v.x, v.y);
     q[1] = make_double2(v.z, v.w);
+}
+
+// ------------------------------------------------------------- FP64 pipe relief
+// On this GPU the FP64 pipe (2 lanes per SM and clock) bounds the chemistry,
+// while the integer pipe is nearly idle; float <-> double conversions and
+// reciprocals of the fast forms are therefore done without FP64-pipe
+// conversion instructions.
+__host__ __device__ __forceinline__ unsigned long long dbits(double d)
+{
+    unsigned long long u;
+    memcpy(&u, &d, 8);
+    return u;
+}
+__host__ __device__ __forceinline__ double dfrom(unsigned long long u)
+{
+    double d;
+    memcpy(&d, &u, 8);
+    return d;
+}
+__host__ __device__ __forceinline__ unsigned fbits(float f)
+{
+    unsigned u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+__host__ __device__ __forceinline__ float ffrom(unsigned u)
+{
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// float -> double, exact: a normal float's exponent is rebiased (127 -> 1023)
+// and its mantissa moved up 29 bits; zero, subnormals, Inf and NaN take the
+// conversion instruction
+__host__ __device__ __forceinline__ double f2d(float f)
+{
+    const unsigned u = fbits(f);
+    if ((u & 0x7f800000u) - 0x00800000u < 0x7f000000u)
+        return dfrom(((unsigned long long)(u & 0x80000000u) << 32) |
+                     (((unsigned long long)(u & 0x7fffffffu) << 29) + (896ull << 52)));
+    return (double)f;
+}
+
+// double -> float, rounded to nearest even: when the result is a normal
+// float (double exponent 897..1150) the top 23 mantissa bits are kept and
+// the 29 dropped bits decide the rounding (a carry into the exponent gives
+// the next binade, or Inf above the largest float, as IEEE rounding does);
+// everything else takes the conversion instruction
+__host__ __device__ __forceinline__ float d2f(double d)
+{
+    const unsigned long long b = dbits(d);
+    const unsigned ed = (unsigned)(b >> 52) & 0x7ffu;
+    if (ed - 897u < 254u) {
+        const unsigned long long m = b & 0x7fffffffffffffffull;
+        unsigned r = (unsigned)((m >> 29) - (896ull << 23));
+        const unsigned low = (unsigned)m & 0x1fffffffu;
+        r += (low > 0x10000000u || (low == 0x10000000u && (r & 1u))) ? 1u : 0u;
+        return ffrom(r | ((unsigned)(b >> 32) & 0x80000000u));
+    }
+    return (float)d;
+}
+
+template <typename R> __device__ __forceinline__ double to_d(R v);
+template <> __device__ __forceinline__ double to_d<float>(float v) { return f2d(v); }
+template <> __device__ __forceinline__ double to_d<double>(double v) { return v; }
+template <typename R> __device__ __forceinline__ R from_d(double v);
+template <> __device__ __forceinline__ float from_d<float>(double v) { return d2f(v); }
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+
+// 1/d for the fast forms: the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64) refined by two Newton-Raphson steps y <- y + y (1 - d y),
+// each squaring the relative error.  |d| outside [2^-1020, 2^1020) (zero,
+// subnormal, huge, Inf, NaN) takes the IEEE division instead.
+__device__ __forceinline__ double rcp_nr(double d)
+{
+    const unsigned ex = (unsigned)(dbits(d) >> 52) & 0x7ffu;
+    if (ex - 3u >= 2040u) return 1.0 / d;
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-d, y, 1.0);
+    return fma(y, e, y);
 }
 
 __device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
@@ -712,22 +798,27 @@ struct Cell {
 // N -> F -> x -> e (Sec. 2.2.4 semi-implicit update; dtau restored in the
 // absorption denominators); returns e^p and e^{p+1}
 template <int G, bool STRICT>
-__device__ __forceinline__ void chem_trial(const Phys &ph, double nunit, double n0, const double *S,
-                                           const Rates &r, double alpha, const Cell<G> &s,
-                                           double dtau, Cell<G> &o, double &ep, double &e1)
+__device__ __forceinline__ void chem_trial(const Phys &ph, double nunit, double inu, double n0,
+                                           const double *S, const Rates &r, double alpha,
+                                           const Cell<G> &s, double dtau, Cell<G> &o, double &ep,
+                                           double &e1)
 {
+    // STRICT: the oracle's operations in its order (IEEE division); the fast
+    // forms multiply by 1/nunit (inu) and by Newton reciprocals instead
     const double x = 1.0 - s.xHI;
 #pragma unroll
     for (int i = 0; i < G; i++) {
         const double den = 1.0 + ph.csig[i] * s.xHI * n0 * dtau;
         double src = S[i];
-        if (i == 0 && !ph.ots) src = src + (r.aA - r.aB) * x * x * n0 * n0 / nunit;
+        if (i == 0 && !ph.ots)
+            src = STRICT ? src + (r.aA - r.aB) * x * x * n0 * n0 / nunit
+                         : src + (r.aA - r.aB) * x * x * n0 * n0 * inu;
         if (STRICT) {
             o.N[i] = (s.N[i] + src * dtau) / den;
 #pragma unroll
             for (int k = 0; k < 3; k++) o.F[i][k] = s.F[i][k] / den;
         } else {
-            const double rd = 1.0 / den;
+            const double rd = rcp_nr(den);
             o.N[i] = (s.N[i] + src * dtau) * rd;
 #pragma unroll
             for (int k = 0; k < 3; k++) o.F[i][k] = s.F[i][k] * rd;
@@ -736,7 +827,9 @@ __device__ __forceinline__ void chem_trial(const Phys &ph, double nunit, double 
     double gam = 0.0;
 #pragma unroll
     for (int i = 0; i < G; i++) gam = gam + ph.csig[i] * (nunit * o.N[i]);
-    o.xHI = (s.xHI + alpha * x * x * n0 * dtau) / (1.0 + dtau * (r.beta * x * n0 + gam));
+    const double xnum = s.xHI + alpha * x * x * n0 * dtau;
+    const double xden = 1.0 + dtau * (r.beta * x * n0 + gam);
+    o.xHI = STRICT ? xnum / xden : xnum * rcp_nr(xden);
     const double e0 = eint(s.xHI, n0, s.T);
     ep = e0;
     if (ph.isothermal) {
@@ -750,7 +843,8 @@ __device__ __forceinline__ void chem_trial(const Phys &ph, double nunit, double 
     const double lamc = cooling(r, n0, o.xHI);   // Lambda(n0, x^{p+1}, T^p)
     const double e = e0 + dtau * heat - dtau * lamc;
     e1 = e;
-    o.T = e / (1.5 * (1.0 + (1.0 - o.xHI)) * n0 * rtd::KB);
+    const double cv = 1.5 * (1.0 + (1.0 - o.xHI)) * n0 * rtd::KB;
+    o.T = STRICT ? e / cv : e * rcp_nr(cv);
 }
 
 // advance one cell over `span` with sub-cycles: dtau = min(rest,
@@ -763,9 +857,9 @@ struct NoTrace {
 };
 
 template <int G, bool STRICT, class Trace = NoTrace>
-__device__ unsigned int chem_span(const Phys &ph, const double *tab, double nunit, double n0,
-                                  const double *S, Cell<G> &s, double span, bool use_est, int &ncyc,
-                                  Trace *tr = nullptr)
+__device__ unsigned int chem_span(const Phys &ph, const double *tab, double nunit, double inu,
+                                  double n0, const double *S, Cell<G> &s, double span, bool use_est,
+                                  int &ncyc, Trace *tr = nullptr)
 {
     unsigned int err = 0;
     double tau = 0.0;
@@ -782,15 +876,19 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, double nuni
                 heat = heat + ph.c * s.xHI * n0 * (nunit * s.N[i]) * ph.SigE[i];
             const double rate = heat - cooling(r, n0, s.xHI);
             const double e = eint(s.xHI, n0, s.T);
-            if (rate != 0.0) {
-                const double est = fabs(e / rate);
+            // est = |e/rate| is needed only when it may fall below rem; with
+            // |e| >= rem |rate| (1 + 1e-13) it is >= rem whatever the
+            // rounding, and the division is skipped
+            const double ar = fabs(rate);
+            if (rate != 0.0 && !(fabs(e) >= rem * ar * 1.0000000000001)) {
+                const double est = STRICT ? fabs(e / rate) : fabs(e) * rcp_nr(ar);
                 if (est < rem) { dtau = est; last = false; }
             }
         }
         Cell<G> o;
         double ep, e1;
         for (int h = 0;; h++) {
-            chem_trial<G, STRICT>(ph, nunit, n0, S, r, alpha, s, dtau, o, ep, e1);
+            chem_trial<G, STRICT>(ph, nunit, inu, n0, S, r, alpha, s, dtau, o, ep, e1);
             if (ph.isothermal) break;
             if (!isfinite(e1)) {            // no amount of halving repairs a NaN/Inf
                 s = o;
@@ -821,7 +919,7 @@ template <typename R> __device__ __forceinline__ R flux_nmin();
 template <> __device__ __forceinline__ float flux_nmin<float>() { return 1e-30f; }
 template <> __device__ __forceinline__ double flux_nmin<double>() { return 1e-290; }
 
-__device__ __forceinline__ double ldn(const float *p, int64_t i) { return (double)p[i]; }
+__device__ __forceinline__ double ldn(const float *p, int64_t i) { return f2d(p[i]); }
 __device__ __forceinline__ double ldn(const double *p, int64_t i) { return p[i]; }
 
 // Block reduction of one thread's diagnostics, fixed order: two FP64 sums
@@ -927,8 +1025,8 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
-                s.N[i] = (double)u.x;
-                s.F[i][0] = (double)u.y; s.F[i][1] = (double)u.z; s.F[i][2] = (double)u.w;
+                s.N[i] = to_d(u.x);
+                s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
                 // flux limit after transport, in the state's own precision;
                 // F is scaled by 1/N first so no square underflows
                 if (u.x > flux_nmin<TU>()) {
@@ -964,9 +1062,9 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (ph.nsub > 0) {
                 const double h = B.dt / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    err |= chem_span<G, STRICT>(ph, tab, B.nunit, n0, S, s, h, false, ncyc);
+                    err |= chem_span<G, STRICT>(ph, tab, B.nunit, B.inv_nunit, n0, S, s, h, false, ncyc);
             } else {
-                err |= chem_span<G, STRICT>(ph, tab, B.nunit, n0, S, s, B.dt, true, ncyc);
+                err |= chem_span<G, STRICT>(ph, tab, B.nunit, B.inv_nunit, n0, S, s, B.dt, true, ncyc);
             }
             if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
             if (err) atomicOr(&ctl->err, err);
@@ -974,9 +1072,10 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             TU f2max = TU(0);                  // largest |F/N|^2 of the cell's groups
 #pragma unroll
             for (int i = 0; i < G; i++) {
-                const V4<TU> o = {(TU)s.N[i], (TU)s.F[i][0], (TU)s.F[i][1], (TU)s.F[i][2]};
+                const V4<TU> o = {from_d<TU>(s.N[i]), from_d<TU>(s.F[i][0]), from_d<TU>(s.F[i][1]),
+                                  from_d<TU>(s.F[i][2])};
                 st4(U + (int64_t)i * B.ncell + c, o);
-                ph_tot += (double)o.x;
+                ph_tot += to_d(o.x);
                 if (o.x > flux_nmin<TU>()) {
                     const TU rn = TU(1) / o.x;
                     const TU ux = o.y * rn, uy = o.z * rn, uz = o.w * rn;

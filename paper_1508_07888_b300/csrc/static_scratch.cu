@@ -108,6 +108,7 @@ extern "C" int rt_transport_static(const rt_params *p, const rt_box *box, int ns
         B.ncell = ncell;
         B.dx = box->dx;
         B.nunit = box->nunit;
+        B.inv_nunit = 1.0 / box->nunit;
         B.dt = p->cfl * box->dx / (3.0 * p->c_red);
         B.lam = p->c_red * B.dt / box->dx;
         rtl::transport_layout(B, p->ngroups);

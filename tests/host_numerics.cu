@@ -1,0 +1,114 @@
+// Host-side checks of the chemistry kernel's numerical helpers, compiled by
+// tests/test_host_numerics.py with nvcc and run on the CPU:
+//   1. f2d (float -> double by integer operations) against the conversion
+//      instruction, for every float;
+//   2. d2f (double -> float, round to nearest even) against the conversion,
+//      on exponents around the float range with exact ties, near-ties and
+//      carries into the exponent;
+//   3. the rate table (rate_table.cu) evaluated the kernel's way (interval
+//      and local variable from T's bits) against the rate fits in long
+//      double at random temperatures.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "../paper_1508_07888_b300/csrc/launch.h"
+#include "../paper_1508_07888_b300/csrc/rt_kernels.cuh"
+
+typedef long double LD;
+static const LD THI = 157807.0L;
+// the fits, written out again from their published forms (Hui & Gnedin 1997
+// case A/B recombination and collisional ionisation; excitation cooling and
+// bremsstrahlung as documented in rate_table.cu)
+static LD aA(LD T) { LD l = 2 * THI / T; return 1.269e-13L * powl(l, 1.503L) / powl(1 + powl(l / 0.522L, 0.470L), 1.923L); }
+static LD aB(LD T) { LD l = 2 * THI / T; return 2.753e-14L * powl(l, 1.500L) / powl(1 + powl(l / 2.740L, 0.407L), 2.242L); }
+static LD kR(LD T) { LD l = 2 * THI / T; return 1.778e-29L * T * powl(l, 1.965L) / powl(1 + powl(l / 0.541L, 0.502L), 2.697L) + 1.42e-27L * 1.3L * sqrtl(T); }
+static LD beta(LD T) { LD l = 2 * THI / T; return 21.11L * powl(T, -1.5L) * expl(-l / 2) * powl(l, -1.089L) / powl(1 + powl(l / 0.354L, 0.874L), 1.101L); }
+static LD cce(LD T) { return 7.5e-19L * expl(-118348.0L / T) / (1 + sqrtl(T / 1e5L)); }
+
+int main()
+{
+    int fails = 0;
+    unsigned long long bad = 0;
+    for (unsigned long long u = 0; u <= 0xffffffffull; u++) {
+        const float f = rtk::ffrom((unsigned)u);
+        const double a = rtk::f2d(f), b = (double)f;
+        if (f != f) { if (a == a) bad++; continue; }
+        if (rtk::dbits(a) != rtk::dbits(b)) bad++;
+    }
+    printf("f2d: %llu mismatches over all floats\n", bad);
+    fails += bad != 0;
+
+    std::mt19937_64 g(7);
+    unsigned long long bad2 = 0, n = 0;
+    auto chk = [&](double d) {
+        n++;
+        const float a = rtk::d2f(d), b = (float)d;
+        if (d != d) { if (a == a) bad2++; return; }
+        if (rtk::fbits(a) != rtk::fbits(b)) bad2++;
+    };
+    for (int k = 0; k < 20000000; k++) {
+        const unsigned long long r = g();
+        const unsigned long long ex = 860 + (r % 330);
+        unsigned long long m = g() & 0xfffffffffffffull;
+        switch (k % 5) {
+        case 1: m = (m & ~0x1fffffffull) | 0x10000000ull; break;
+        case 2: m = (m & ~0x1fffffffull) | 0x0fffffffull; break;
+        case 3: m = (m & ~0x1fffffffull) | 0x10000001ull; break;
+        case 4: m = 0xfffffffffffffull - (g() & 0x3fffffffull); break;
+        }
+        chk(rtk::dfrom(((r >> 63) << 63) | (ex << 52) | m));
+    }
+    for (unsigned long long ex = 0; ex < 2048; ex++)
+        for (int s = 0; s < 2; s++)
+            for (unsigned long long m : {0ull, 1ull, 0x10000000ull, 0xfffffffffffffull, 0x8000000000000ull})
+                chk(rtk::dfrom(((unsigned long long)s << 63) | (ex << 52) | m));
+    printf("d2f: %llu mismatches over %llu doubles\n", bad2, n);
+    fails += bad2 != 0;
+
+    for (int ots = 0; ots < 2; ots++) {
+        std::vector<double> tab(rtl::rate_table_doubles());
+        if (!rtl::build_rate_table(ots != 0, tab.data())) { printf("table build failed\n"); return 1; }
+        if (ots) continue;                      // the OTS table differs in kR only
+        std::uniform_real_distribution<double> lu(0.0, 30.0 * 0.6931471805599453);
+        double w[5] = {0, 0, 0, 0, 0};
+        for (int k = 0; k < 300000; k++) {
+            const double T = std::exp(lu(g));
+            const unsigned long long bits = rtk::dbits(T);
+            const int e = (int)(bits >> 52) - 1023;
+            if (e < RTD_TAB_E0 || e >= RTD_TAB_E1) continue;
+            const int low = 52 - RTD_TAB_SUB;
+            const int j = ((e - RTD_TAB_E0) << RTD_TAB_SUB) + (int)((bits >> low) & ((1 << RTD_TAB_SUB) - 1));
+            const double y = rtk::dfrom(0x3FF0000000000000ull | ((bits & ((1ull << low) - 1)) << RTD_TAB_SUB));
+            const double t = std::fma(y, 2.0, -3.0);
+            const double *a = tab.data() + (size_t)j * RTD_TAB_NF * RTD_TAB_NC;
+            double gv[RTD_TAB_NF];
+            for (int f = 0; f < RTD_TAB_NF; f++) {
+                const double *c = a + f * RTD_TAB_NC;
+                double p = c[RTD_TAB_NC - 1];
+                for (int i = RTD_TAB_NC - 2; i >= 0; i--) p = std::fma(p, t, c[i]);
+                gv[f] = p;
+            }
+            const LD ex3[3] = {aA(T), aB(T), kR(T)};
+            for (int f = 0; f < 3; f++) w[f] = std::fmax(w[f], (double)fabsl((gv[f] - ex3[f]) / ex3[f]));
+            const double b = T >= RTD_TAB_TCUT ? std::exp(gv[3] - 157807.0 / T) : 0.0;
+            const double c = T >= RTD_TAB_TCUT ? std::exp(gv[4] - 118348.0 / T) : 0.0;
+            const LD eb = beta(T), ec = cce(T);
+            // below the cut the fits are zero in double; above it, relative
+            if (T < RTD_TAB_TCUT) {
+                if ((double)eb != 0.0 || (double)ec != 0.0) w[3] = w[4] = 1.0;
+            } else {
+                if (eb > 1e-290L) w[3] = std::fmax(w[3], (double)fabsl((b - eb) / eb));
+                if (ec > 1e-290L) w[4] = std::fmax(w[4], (double)fabsl((c - ec) / ec));
+            }
+        }
+        printf("table: max rel err aA %.2e aB %.2e kR %.2e beta %.2e cce %.2e\n", w[0], w[1], w[2], w[3], w[4]);
+        // alpha, kR: interpolation error; beta, cce: exp of arguments up to
+        // ~800 in magnitude, whose own rounding (~1e-13 relative) dominates
+        fails += !(w[0] < 3e-14 && w[1] < 3e-14 && w[2] < 3e-14 && w[3] < 1e-12 && w[4] < 1e-12);
+    }
+    printf(fails ? "FAIL\n" : "OK\n");
+    return fails ? 1 : 0;
+}

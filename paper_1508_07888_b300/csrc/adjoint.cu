@@ -283,9 +283,9 @@ k_chem_adj(const BoxDev *__restrict__ boxes, Phys ph, const double *__restrict__
             if (ph.nsub > 0) {
                 const double h = B.dt / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    chem_span<G, false, TraceBuf<G>>(ph, tab, B.nunit, B.inv_nunit, n0, S, w, h, false, ncyc, &tr);
+                    chem_span<G, false, TraceBuf<G>>(ph, tab, B, n0, S, w, h, false, ncyc, &tr);
             } else {
-                chem_span<G, false, TraceBuf<G>>(ph, tab, B.nunit, B.inv_nunit, n0, S, w, B.dt, true, ncyc, &tr);
+                chem_span<G, false, TraceBuf<G>>(ph, tab, B, n0, S, w, B.dt, true, ncyc, &tr);
             }
         };
         replay(0);

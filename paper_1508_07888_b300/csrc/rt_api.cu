@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -228,6 +229,10 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     D.dx = B.dx;
                     D.nunit = B.nunit;
                     D.inv_nunit = 1.0 / B.nunit;
+                    for (int i = 0; i < RTD_MAXG; i++) {
+                        D.gN[i] = i < G ? h->ph.csig[i] * B.nunit : 0.0;
+                        D.hN[i] = i < G ? h->ph.c * B.nunit * h->ph.SigE[i] : 0.0;
+                    }
                     D.dt = p->cfl * B.dx / (3.0 * p->c_red);
                     D.lam = p->c_red * D.dt / B.dx;
                     D.U = B.U;
@@ -263,6 +268,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMalloc(&h->d_lastdiag, sizeof(double) * RTD_NDIAG * nboxes));
                 CU(h, cudaMemset(h->d_lastdiag, 0, sizeof(double) * RTD_NDIAG * nboxes));
                 CU(h, cudaMalloc(&h->d_ctl, sizeof(rtd::Ctl)));
+                CU(h, cudaMemset(h->d_ctl, 0, sizeof(rtd::Ctl)));
                 CU(h, cudaMallocHost(&h->h_ctl, sizeof(rtd::Ctl)));
                 std::memset(h->h_ctl, 0, sizeof(rtd::Ctl));
                 CU(h, cudaMallocHost(&h->h_lastdiag, sizeof(double) * RTD_NDIAG * nboxes));

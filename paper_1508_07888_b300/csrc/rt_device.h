@@ -64,6 +64,8 @@ struct BoxDev {
     int64_t ncell;
     double dx, nunit, dt, lam;        // lam = c dt / dx (Courant number)
     double inv_nunit;                 // 1 / nunit
+    double gN[RTD_MAXG];              // c sigma_N,i nunit
+    double hN[RTD_MAXG];              // c nunit Sigma_E,i
     void *U;                          // caller's state, [G][nz][ny][nx][4]
     void *Us;                         // post-transport state (library scratch)
     double *xHI, *T;

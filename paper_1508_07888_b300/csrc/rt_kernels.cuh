@@ -86,22 +86,23 @@ __host__ __device__ __forceinline__ float ffrom(unsigned u)
 }
 
 // float -> double, exact: a normal float's exponent is rebiased (127 -> 1023)
-// and its mantissa moved up 29 bits; zero, subnormals, Inf and NaN take the
-// conversion instruction
+// and its mantissa moved up 29 bits, a zero keeps its sign; subnormals, Inf
+// and NaN take the conversion instruction
 __host__ __device__ __forceinline__ double f2d(float f)
 {
     const unsigned u = fbits(f);
     if ((u & 0x7f800000u) - 0x00800000u < 0x7f000000u)
         return dfrom(((unsigned long long)(u & 0x80000000u) << 32) |
                      (((unsigned long long)(u & 0x7fffffffu) << 29) + (896ull << 52)));
+    if ((u & 0x7fffffffu) == 0u) return dfrom((unsigned long long)u << 32);
     return (double)f;
 }
 
 // double -> float, rounded to nearest even: when the result is a normal
 // float (double exponent 897..1150) the top 23 mantissa bits are kept and
 // the 29 dropped bits decide the rounding (a carry into the exponent gives
-// the next binade, or Inf above the largest float, as IEEE rounding does);
-// everything else takes the conversion instruction
+// the next binade, or Inf above the largest float, as IEEE rounding does); a
+// zero keeps its sign; everything else takes the conversion instruction
 __host__ __device__ __forceinline__ float d2f(double d)
 {
     const unsigned long long b = dbits(d);
@@ -113,6 +114,7 @@ __host__ __device__ __forceinline__ float d2f(double d)
         r += (low > 0x10000000u || (low == 0x10000000u && (r & 1u))) ? 1u : 0u;
         return ffrom(r | ((unsigned)(b >> 32) & 0x80000000u));
     }
+    if ((b & 0x7fffffffffffffffull) == 0ull) return ffrom((unsigned)(b >> 32));   // +-0
     return (float)d;
 }
 
@@ -856,26 +858,95 @@ struct NoTrace {
     __device__ __forceinline__ void push(const Cell<G> &, double) {}
 };
 
+// One trial of the fast forms: the same update as chem_trial, regrouped
+// around per-cell constants so the FP64 pipe does less work (products with
+// n0 and nunit formed once per cell; Newton reciprocals).  Agrees with
+// chem_trial to a few ulp.
+template <int G>
+struct CellK {
+    double h[G];        // c nunit Sigma_E,i n0      (heating per stored N and neutral fraction)
+    double n02, K, cvn; // n0^2, n0^2 / nunit, (3/2) kB n0
+};
+
+template <int G>
+__device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B, const CellK<G> &k,
+                                                double n0, const double *S, const Rates &r,
+                                                double alpha, const Cell<G> &s, double e0,
+                                                double dtau, Cell<G> &o, double &e1)
+{
+    const double x = 1.0 - s.xHI;
+    const double q = s.xHI * n0 * dtau;
+    const double rec = ph.ots ? 0.0 : (r.aA - r.aB) * x * x * k.K;
+#pragma unroll
+    for (int i = 0; i < G; i++) {
+        const double rd = rcp_nr(fma(ph.csig[i], q, 1.0));
+        const double src = (i == 0 && !ph.ots) ? S[i] + rec : S[i];
+        o.N[i] = fma(src, dtau, s.N[i]) * rd;
+#pragma unroll
+        for (int m = 0; m < 3; m++) o.F[i][m] = s.F[i][m] * rd;
+    }
+    double gam = B.gN[0] * o.N[0];
+#pragma unroll
+    for (int i = 1; i < G; i++) gam = fma(B.gN[i], o.N[i], gam);
+    const double xnum = fma(alpha * x * x, n0 * dtau, s.xHI);
+    const double xden = fma(dtau, fma(r.beta * x, n0, gam), 1.0);
+    o.xHI = xnum * rcp_nr(xden);
+    if (ph.isothermal) {
+        o.T = s.T;
+        e1 = e0;
+        return;
+    }
+    double hs = k.h[0] * o.N[0];
+#pragma unroll
+    for (int i = 1; i < G; i++) hs = fma(k.h[i], o.N[i], hs);
+    const double x1 = 1.0 - o.xHI;
+    const double cool = k.n02 * x1 * fma(x1, r.kR, o.xHI * r.kC);   // Lambda(n0, x^{p+1}, T^p)
+    e1 = fma(dtau, fma(o.xHI, hs, -cool), e0);
+    o.T = e1 * rcp_nr(k.cvn * (2.0 - o.xHI));
+}
+
 template <int G, bool STRICT, class Trace = NoTrace>
-__device__ unsigned int chem_span(const Phys &ph, const double *tab, double nunit, double inu,
-                                  double n0, const double *S, Cell<G> &s, double span, bool use_est,
+__device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDev &B, double n0,
+                                  const double *S, Cell<G> &s, double span, bool use_est,
                                   int &ncyc, Trace *tr = nullptr)
 {
     unsigned int err = 0;
     double tau = 0.0;
+    CellK<G> k;
+    if (!STRICT) {
+#pragma unroll
+        for (int i = 0; i < G; i++) {
+            k.h[i] = B.hN[i] * n0;
+        }
+        k.n02 = n0 * n0;
+        k.K = k.n02 * B.inv_nunit;
+        k.cvn = (1.5 * rtd::KB) * n0;
+    }
     for (;;) {
         const double rem = span - tau;
         const Rates r = tab ? rates_tab(ph, tab, s.T) : rates_at(ph, s.T);
         const double alpha = ph.ots ? r.aB : r.aA;
         double dtau = rem;
         bool last = true;
+        // e^p (the fast forms reuse it in every trial of this sub-cycle)
+        const double ep0 = STRICT ? 0.0 : k.cvn * (2.0 - s.xHI) * s.T;
         if (!ph.isothermal && use_est) {
-            double heat = 0.0;
+            double rate, e;
+            if (STRICT) {
+                double heat = 0.0;
 #pragma unroll
-            for (int i = 0; i < G; i++)
-                heat = heat + ph.c * s.xHI * n0 * (nunit * s.N[i]) * ph.SigE[i];
-            const double rate = heat - cooling(r, n0, s.xHI);
-            const double e = eint(s.xHI, n0, s.T);
+                for (int i = 0; i < G; i++)
+                    heat = heat + ph.c * s.xHI * n0 * (B.nunit * s.N[i]) * ph.SigE[i];
+                rate = heat - cooling(r, n0, s.xHI);
+                e = eint(s.xHI, n0, s.T);
+            } else {
+                double hs = k.h[0] * s.N[0];
+#pragma unroll
+                for (int i = 1; i < G; i++) hs = fma(k.h[i], s.N[i], hs);
+                const double x = 1.0 - s.xHI;
+                rate = fma(s.xHI, hs, -(k.n02 * x * fma(x, r.kR, s.xHI * r.kC)));
+                e = ep0;
+            }
             // est = |e/rate| is needed only when it may fall below rem; with
             // |e| >= rem |rate| (1 + 1e-13) it is >= rem whatever the
             // rounding, and the division is skipped
@@ -888,7 +959,12 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, double nuni
         Cell<G> o;
         double ep, e1;
         for (int h = 0;; h++) {
-            chem_trial<G, STRICT>(ph, nunit, inu, n0, S, r, alpha, s, dtau, o, ep, e1);
+            if (STRICT) {
+                chem_trial<G, true>(ph, B.nunit, B.inv_nunit, n0, S, r, alpha, s, dtau, o, ep, e1);
+            } else {
+                ep = ep0;
+                chem_trial_fast<G>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1);
+            }
             if (ph.isothermal) break;
             if (!isfinite(e1)) {            // no amount of halving repairs a NaN/Inf
                 s = o;
@@ -1002,16 +1078,19 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
        DiagBuf db)
 {
     __shared__ int s_last;
-    __shared__ unsigned long long s_item;
+    __shared__ long long s_item;
     const double *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
+    // items are handed out one at a time from a counter, so blocks that
+    // draw cheap cells (cold gas) take more of them; the order of the work
+    // does not enter any result
     for (;;) {
-        // items are handed out one at a time, so blocks that draw cheap
-        // cells (cold gas) take more of them; the order of the work does
-        // not enter any result
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->chem_next, 1ull);
+        if (threadIdx.x == 0) {
+            const unsigned long long k = atomicAdd(&ctl->chem_next, 1ull);
+            s_item = k < (unsigned long long)nitems ? (long long)k : -1ll;
+        }
         __syncthreads();
         const int64_t it = (int64_t)s_item;
-        if (it >= nitems) break;
+        if (it < 0) break;
         const int b = find_box(boxes, nboxes, it, true);
         const BoxDev &B = boxes[b];
         const int64_t c = (it - B.citem0) * RTD_CHEM_BLOCK + threadIdx.x;
@@ -1062,9 +1141,9 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (ph.nsub > 0) {
                 const double h = B.dt / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    err |= chem_span<G, STRICT>(ph, tab, B.nunit, B.inv_nunit, n0, S, s, h, false, ncyc);
+                    err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, h, false, ncyc);
             } else {
-                err |= chem_span<G, STRICT>(ph, tab, B.nunit, B.inv_nunit, n0, S, s, B.dt, true, ncyc);
+                err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, B.dt, true, ncyc);
             }
             if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
             if (err) atomicOr(&ctl->err, err);
@@ -1087,7 +1166,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             B.T[c] = s.T;
             v.X = 1.0 - s.xHI;
             v.ph = ph_tot;
-            v.fbits = (unsigned long long)__double_as_longlong((double)sqrt(f2max));
+            v.fbits = (unsigned long long)__double_as_longlong(to_d(sqrt(f2max)));
             v.count = s.xHI < 0.5 ? 1ull : 0ull;
             v.ncyc = (unsigned long long)ncyc;
         }

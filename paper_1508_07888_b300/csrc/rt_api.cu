@@ -40,7 +40,9 @@ struct rt_handle {
     std::vector<std::vector<int>> src_uidx;  // per box: unique-table index of each given source
     std::vector<double *> d_src_S;
     rtd::DiagPart *d_partials = nullptr;
-    unsigned *d_done = nullptr;              // per-box item counters of the fused reduction
+    unsigned *d_done = nullptr;              // per-box group counters of the fused reduction
+    rtd::DiagPart *d_gpart = nullptr;        // per-group partials
+    unsigned *d_gdone = nullptr;             // per-group item counters
     double *d_rtab = nullptr;                // rate table (null: fits evaluated directly)
     double *d_lastdiag = nullptr;
     rtd::Ctl *d_ctl = nullptr;
@@ -92,6 +94,8 @@ static void release(rt_handle *h)
     cudaFree(h->d_boxes);
     cudaFree(h->d_partials);
     cudaFree(h->d_done);
+    cudaFree(h->d_gpart);
+    cudaFree(h->d_gdone);
     cudaFree(h->d_rtab);
     cudaFree(h->d_lastdiag);
     cudaFree(h->d_ctl);
@@ -214,7 +218,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
                 CU(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
                 const int G = p->ngroups;
-                int64_t titem = 0, citem = 0;
+                int64_t titem = 0, citem = 0, cgroup = 0;
                 h->bdev.resize(nboxes);
                 h->d_us.assign(nboxes, nullptr);
                 h->d_src_cell.assign(nboxes, nullptr);
@@ -245,8 +249,11 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     D.titem0 = titem;
                     titem += D.ntitems;
                     D.citem0 = citem;
-                    D.ncitems = (D.ncell + RTD_CHEM_BLOCK - 1) / RTD_CHEM_BLOCK;
+                    D.ncitems = (D.ncell + RTD_CHEM_ITEM - 1) / RTD_CHEM_ITEM;
                     citem += D.ncitems;
+                    D.cgroup0 = cgroup;
+                    D.ncgroups = (D.ncitems + RTD_CHEM_GROUP - 1) / RTD_CHEM_GROUP;
+                    cgroup += D.ncgroups;
                 }
                 h->ntitems = titem;
                 h->ncitems = citem;
@@ -254,6 +261,9 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * nboxes,
                                  cudaMemcpyHostToDevice));
                 CU(h, cudaMalloc(&h->d_partials, sizeof(rtd::DiagPart) * citem));
+                CU(h, cudaMalloc(&h->d_gpart, sizeof(rtd::DiagPart) * cgroup));
+                CU(h, cudaMalloc(&h->d_gdone, sizeof(unsigned) * cgroup));
+                CU(h, cudaMemset(h->d_gdone, 0, sizeof(unsigned) * cgroup));
                 CU(h, cudaMalloc(&h->d_done, sizeof(unsigned) * nboxes));
                 CU(h, cudaMemset(h->d_done, 0, sizeof(unsigned) * nboxes));
                 if (!p->rates_const) {
@@ -280,7 +290,8 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 const int co = rtl::chem_occupancy(fp64, h->strict, G);
                 // transport: at least 4 planes per block (each run re-reads 2)
                 h->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((titem + 3) / 4, (int64_t)to * nsm));
-                h->cgrid = (int)std::min<int64_t>(citem, (int64_t)co * nsm);
+                const int64_t wpb = RTD_CHEM_BLOCK / 32;         // warps (work items) per block
+                h->cgrid = (int)std::min<int64_t>((citem + wpb - 1) / wpb, (int64_t)co * nsm);
                 return RT_OK;
             }()))
             return bail(rc);
@@ -358,7 +369,7 @@ static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = 
 {
     rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s};
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
-    const rtd::DiagBuf db{h->d_partials, h->d_done, h->d_lastdiag};
+    const rtd::DiagBuf db{h->d_partials, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     e = h->strict ? rtl::transport_strict(Lt, h->zc, h->ph, h->d_ctl)

@@ -12,8 +12,11 @@
 // transport tile: TX x TY threads, one (x, y) column each, marching in z
 #define RTD_TX 32
 #define RTD_TY 8
-// chemistry: cells per block (one thread per cell)
+// chemistry: threads per block (independent warps, one thread per cell),
+// cells per work item (one warp), work items per diagnostics group
 #define RTD_CHEM_BLOCK 256
+#define RTD_CHEM_ITEM 32
+#define RTD_CHEM_GROUP 64
 
 // device error bits (OR-ed into Ctl::err)
 #define RTD_ERR_NONFINITE 1u
@@ -74,7 +77,8 @@ struct BoxDev {
     const double *src_S;              // [nsrc][G] source term, stored units per second
     int nsrc;
     int64_t titem0, ntitems;          // transport plane units of this box (prefix, count)
-    int64_t citem0, ncitems;          // chemistry work items of this box
+    int64_t citem0, ncitems;          // chemistry work items (32 cells) of this box
+    int64_t cgroup0, ncgroups;        // diagnostics groups (64 items) of this box
 };
 
 // Per-item diagnostic partials of the chemistry kernel and the per-box
@@ -82,11 +86,13 @@ struct BoxDev {
 struct DiagPart {
     double X, ph;                     // sum of (1 - xHI), sum of N over groups
     unsigned long long fbits;         // max |F|/N (bits of a non-negative double)
-    unsigned count, ncyc;             // cells with xHI < 0.5, chemistry sub-cycles
+    unsigned long long count, ncyc;   // cells with xHI < 0.5, chemistry sub-cycles
 };
 struct DiagBuf {
     DiagPart *part;                   // one per chemistry work item
-    unsigned *done;                   // per box: items finished in this step
+    DiagPart *gpart;                  // one per group of RTD_CHEM_GROUP items
+    unsigned *gdone;                  // per group: items finished in this step
+    unsigned *done;                   // per box: groups finished in this step
     double *last;                     // per box: RTD_NDIAG values of the last step
 };
 

@@ -998,59 +998,76 @@ template <> __device__ __forceinline__ double flux_nmin<double>() { return 1e-29
 __device__ __forceinline__ double ldn(const float *p, int64_t i) { return f2d(p[i]); }
 __device__ __forceinline__ double ldn(const double *p, int64_t i) { return p[i]; }
 
-// Block reduction of one thread's diagnostics, fixed order: two FP64 sums
-// by warp shuffles then warp order; the max and the counts on the integer
-// path.  Result valid in thread 0.
+// Diagnostics of a set of cells: two FP64 sums (ionised fraction, photons),
+// the largest |F|/N (bits of a non-negative double, so integer max), two
+// integer counts.
 struct DiagAcc {
     double X, ph;
     unsigned long long fbits, count, ncyc;
 };
 
-__device__ __forceinline__ DiagAcc block_reduce_diag(DiagAcc a)
+__device__ __forceinline__ void diag_add(DiagAcc &a, const DiagAcc &b)
 {
-    __shared__ DiagAcc red[32];
+    a.X += b.X;
+    a.ph += b.ph;
+    a.fbits = b.fbits > a.fbits ? b.fbits : a.fbits;
+    a.count += b.count;
+    a.ncyc += b.ncyc;
+}
+
+// warp reduction in a fixed order (shuffle-down tree), result in lane 0
+__device__ __forceinline__ DiagAcc warp_reduce_diag(DiagAcc a)
+{
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        a.X += __shfl_down_sync(0xffffffffu, a.X, off);
-        a.ph += __shfl_down_sync(0xffffffffu, a.ph, off);
-        const unsigned long long f = __shfl_down_sync(0xffffffffu, a.fbits, off);
-        a.fbits = f > a.fbits ? f : a.fbits;
-        a.count += __shfl_down_sync(0xffffffffu, a.count, off);
-        a.ncyc += __shfl_down_sync(0xffffffffu, a.ncyc, off);
+        DiagAcc o;
+        o.X = __shfl_down_sync(0xffffffffu, a.X, off);
+        o.ph = __shfl_down_sync(0xffffffffu, a.ph, off);
+        o.fbits = __shfl_down_sync(0xffffffffu, a.fbits, off);
+        o.count = __shfl_down_sync(0xffffffffu, a.count, off);
+        o.ncyc = __shfl_down_sync(0xffffffffu, a.ncyc, off);
+        diag_add(a, o);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) red[wid] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < nw; w++) {
-            a.X += red[w].X;
-            a.ph += red[w].ph;
-            a.fbits = red[w].fbits > a.fbits ? red[w].fbits : a.fbits;
-            a.count += red[w].count;
-            a.ncyc += red[w].ncyc;
-        }
-    }
-    __syncthreads();
     return a;
 }
 
-// Items of box b are all reduced: sum its partials in a fixed order and
-// write the step's diagnostics (ionised fraction, photons, max f,
-// n(xHI < 0.5), mean sub-cycles) into lastdiag and the caller's history.
-__device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf &db, Ctl *ctl)
+__device__ __forceinline__ DiagAcc load_part(const DiagPart *p)
+{
+    DiagAcc a;
+    a.X = __ldcg(&p->X);
+    a.ph = __ldcg(&p->ph);
+    a.fbits = __ldcg(&p->fbits);
+    a.count = __ldcg(&p->count);
+    a.ncyc = __ldcg(&p->ncyc);
+    return a;
+}
+
+__device__ __forceinline__ void store_part(DiagPart *p, const DiagAcc &a)
+{
+    p->X = a.X;
+    p->ph = a.ph;
+    p->fbits = a.fbits;
+    p->count = a.count;
+    p->ncyc = a.ncyc;
+}
+
+// sum of n partials by one warp: lane l takes l, l + 32, ... in order, then
+// the fixed tree; result in lane 0
+__device__ __forceinline__ DiagAcc warp_sum_parts(const DiagPart *p, int64_t n)
 {
     DiagAcc a = {0.0, 0.0, 0ull, 0ull, 0ull};
-    const DiagPart *p = db.part + B.citem0;
-    for (int64_t i = threadIdx.x; i < B.ncitems; i += blockDim.x) {
-        a.X += __ldcg(&p[i].X);
-        a.ph += __ldcg(&p[i].ph);
-        const unsigned long long f = __ldcg(&p[i].fbits);
-        a.fbits = f > a.fbits ? f : a.fbits;
-        a.count += __ldcg(&p[i].count);
-        a.ncyc += __ldcg(&p[i].ncyc);
-    }
-    a = block_reduce_diag(a);
-    if (threadIdx.x == 0) {
+    for (int64_t i = threadIdx.x & 31; i < n; i += 32) diag_add(a, load_part(p + i));
+    return warp_reduce_diag(a);
+}
+
+// All groups of box b are reduced: sum the group partials in a fixed order
+// and write the step's diagnostics (ionised fraction, photons, max f,
+// n(xHI < 0.5), mean sub-cycles) into lastdiag and the caller's history.
+// Called by one warp.
+__device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf &db, Ctl *ctl)
+{
+    const DiagAcc a = warp_sum_parts(db.gpart + B.cgroup0, B.ncgroups);
+    if ((threadIdx.x & 31) == 0) {
         const double nc = (double)B.ncell;
         double d[RTD_NDIAG];
         d[0] = a.X / nc;
@@ -1067,33 +1084,34 @@ __device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf
     }
 }
 
-// One work item = RTD_CHEM_BLOCK consecutive cells of one box, one thread per
-// cell.  Reads the post-transport state, runs the sub-cycled chemistry over
-// the box's dt, writes the new radiation state into the caller's U and the
-// item's diagnostic partial; the block that finishes a box's last item
-// reduces that box (no separate diagnostics launch).
+// One work item = RTD_CHEM_ITEM (32) consecutive cells of one box, one warp,
+// one thread per cell; warps draw items independently (no block barrier).
+// Reads the post-transport state, runs the sub-cycled chemistry over the
+// box's dt, writes the new radiation state into the caller's U and the
+// item's diagnostic partial.  The warp that completes a group of
+// RTD_CHEM_GROUP items sums the group; the warp that completes a box's last
+// group reduces the box (no separate diagnostics launch).  Every sum runs
+// in a fixed order of cells, so the diagnostics do not depend on scheduling.
 template <int G, typename TU, typename TN, bool STRICT>
 __global__ void __launch_bounds__(RTD_CHEM_BLOCK)
 k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ctl *ctl,
        DiagBuf db)
 {
-    __shared__ int s_last;
-    __shared__ long long s_item;
+    const int lane = threadIdx.x & 31;
     const double *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
-    // items are handed out one at a time from a counter, so blocks that
-    // draw cheap cells (cold gas) take more of them; the order of the work
-    // does not enter any result
+    // items are handed out one at a time from a counter, so warps that draw
+    // cheap cells (cold gas) take more of them; the order of the work does
+    // not enter any result
     for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned long long k = atomicAdd(&ctl->chem_next, 1ull);
-            s_item = k < (unsigned long long)nitems ? (long long)k : -1ll;
-        }
-        __syncthreads();
-        const int64_t it = (int64_t)s_item;
-        if (it < 0) break;
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(&ctl->chem_next, 1ull);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= (unsigned long long)nitems) break;
+        const int64_t it = (int64_t)k;
         const int b = find_box(boxes, nboxes, it, true);
         const BoxDev &B = boxes[b];
-        const int64_t c = (it - B.citem0) * RTD_CHEM_BLOCK + threadIdx.x;
+        const int64_t li = it - B.citem0;                 // item within the box
+        const int64_t c = li * RTD_CHEM_ITEM + lane;
         DiagAcc v = {0.0, 0.0, 0ull, 0ull, 0ull};
         if (c < B.ncell) {
             const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
@@ -1170,28 +1188,42 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             v.count = s.xHI < 0.5 ? 1ull : 0ull;
             v.ncyc = (unsigned long long)ncyc;
         }
-        v = block_reduce_diag(v);
-        if (threadIdx.x == 0) {
-            DiagPart &p = db.part[it];
-            p.X = v.X;
-            p.ph = v.ph;
-            p.fbits = v.fbits;
-            p.count = (unsigned)v.count;
-            p.ncyc = (unsigned)v.ncyc;
+        v = warp_reduce_diag(v);
+        const int64_t gl = li / RTD_CHEM_GROUP;           // group within the box
+        int last_group = 0;
+        if (lane == 0) {
+            store_part(db.part + it, v);
             __threadfence();
-            s_last = atomicAdd(&db.done[b], 1u) == (unsigned)(B.ncitems - 1);
+            const int64_t left = B.ncitems - gl * RTD_CHEM_GROUP;
+            const unsigned n_in = (unsigned)(left < RTD_CHEM_GROUP ? left : RTD_CHEM_GROUP);
+            last_group = atomicAdd(&db.gdone[B.cgroup0 + gl], 1u) == n_in - 1u;
         }
-        __syncthreads();
-        if (s_last) {
+        last_group = __shfl_sync(0xffffffffu, last_group, 0);
+        if (last_group) {
             __threadfence();
-            reduce_box(B, b, db, ctl);
+            const int64_t first = B.citem0 + gl * RTD_CHEM_GROUP;
+            const int64_t left = B.ncitems - gl * RTD_CHEM_GROUP;
+            const DiagAcc g = warp_sum_parts(db.part + first, left < RTD_CHEM_GROUP ? left : RTD_CHEM_GROUP);
+            int last_box = 0;
+            if (lane == 0) {
+                store_part(db.gpart + B.cgroup0 + gl, g);
+                db.gdone[B.cgroup0 + gl] = 0u;            // ready for the next step
+                __threadfence();
+                last_box = atomicAdd(&db.done[b], 1u) == (unsigned)(B.ncgroups - 1);
+            }
+            last_box = __shfl_sync(0xffffffffu, last_box, 0);
+            if (last_box) {
+                __threadfence();
+                reduce_box(B, b, db, ctl);
+            }
         }
     }
-    // every block has drawn its last (empty) item before it counts itself
+    // every warp has drawn its last (empty) item before it counts itself
     // here; the last one resets the counters for the next launch
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         __threadfence();
-        if (atomicAdd(&ctl->chem_fin, 1ull) == (unsigned long long)gridDim.x - 1ull) {
+        const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+        if (atomicAdd(&ctl->chem_fin, 1ull) == nw - 1ull) {
             ctl->chem_next = 0ull;
             ctl->chem_fin = 0ull;
             __threadfence();

@@ -96,6 +96,12 @@ typedef struct rt_params {
     int    bc[6];                        /* faces -x,+x,-y,+y,-z,+z, rt_bc values */
     int    max_halvings;                 /* cap of the 10% rule (e.g. 30) */
     int    precision;                    /* rt_precision */
+    int    tune;                         /* launch shape of the SPLIT form's transport (tile and
+                                            resident blocks per SM; the results do not depend
+                                            on it): 0 = default, 1 = time every shape at
+                                            rt_create on a synthetic state in scratch and keep
+                                            the fastest (cached per device and box set for the
+                                            process), 2 + k = shape k; ignored by the FP64 forms */
 } rt_params;
 
 typedef struct rt_box {
@@ -124,6 +130,8 @@ typedef struct rt_stats {
                                             diagnostics run inside the chemistry kernel, so
                                             the third entry stays 0 */
     int64_t kernel_launches[3];          /* launches timed into kernel_ms */
+    int     tile_x, tile_y;              /* transport tile (columns x rows per block) */
+    int     transport_grid, chem_grid;   /* blocks of the persistent transport / chemistry grids */
 } rt_stats;
 
 typedef struct rt_handle rt_handle;

@@ -48,6 +48,7 @@ class rt_params(C.Structure):
         ("bc", C.c_int * 6),
         ("max_halvings", C.c_int),
         ("precision", C.c_int),
+        ("tune", C.c_int),
     ]
 
 
@@ -73,6 +74,8 @@ class rt_stats(C.Structure):
         ("last_diag", C.c_double * RT_NDIAG),
         ("kernel_ms", C.c_double * 3),
         ("kernel_launches", C.c_int64 * 3),
+        ("tile_x", C.c_int), ("tile_y", C.c_int),
+        ("transport_grid", C.c_int), ("chem_grid", C.c_int),
     ]
 
 
@@ -223,7 +226,7 @@ def rt_transport_static(p: rt_params, box: rt_box, nsteps: int, stream_ptr: int 
 # ------------------------------------------------------------------ helpers
 def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, isothermal=False,
                 nsub=0, rates_const=False, alphaA=0.0, alphaB=0.0, beta=0.0, bc=(0,) * 6,
-                max_halvings=30, precision=RT_PREC_SPLIT) -> rt_params:
+                max_halvings=30, precision=RT_PREC_SPLIT, tune=0) -> rt_params:
     p = rt_params()
     p.ngroups = ngroups
     for i in range(ngroups):
@@ -236,6 +239,7 @@ def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, 
         p.bc[k] = int(bc[k])
     p.max_halvings = max_halvings
     p.precision = precision
+    p.tune = int(tune)
     return p
 
 

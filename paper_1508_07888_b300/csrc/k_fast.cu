@@ -22,6 +22,35 @@ static cudaError_t transport_attr()
     return e;
 }
 
+// the FP32 transport with a TX x TY tile: shared-memory attribute set once
+// per device, then the launch
+template <int TX, int TY>
+static cudaError_t pm_attr()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport_pm<TX, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rtk::transport_pm_smem_bytes<TX, TY>());
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
+template <int TX, int TY>
+static cudaError_t transport_pm(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
+{
+    cudaError_t e = pm_attr<TX, TY>();
+    if (e != cudaSuccess) return e;
+    rtk::k_transport_pm<TX, TY><<<L.grid, dim3(TX, TY), rtk::transport_pm_smem_bytes<TX, TY>(), L.stream>>>(
+        L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    return cudaSuccess;
+}
+
+template <int TX, int TY>
+static int pm_occupancy();
+
 cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
     dim3 blk(RTD_TX, RTD_TY);
@@ -31,17 +60,14 @@ cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &
         rtk::k_transport<double, false><<<L.grid, blk, rtk::transport_smem_bytes<double>(), L.stream>>>(
             L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
     } else {
-        static int done_dev = -1;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (done_dev != dev) {
-            cudaError_t e = cudaFuncSetAttribute(rtk::k_transport_pm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)rtk::transport_pm_smem_bytes());
-            if (e != cudaSuccess) return e;
-            done_dev = dev;
+        cudaError_t e = cudaSuccess;
+        switch (L.variant) {
+        case 0: e = transport_pm<kTileX[0], kTileY[0]>(L, zc, ph, ctl); break;
+        case 1: e = transport_pm<kTileX[1], kTileY[1]>(L, zc, ph, ctl); break;
+        case 2: e = transport_pm<kTileX[2], kTileY[2]>(L, zc, ph, ctl); break;
+        default: return cudaErrorInvalidValue;
         }
-        rtk::k_transport_pm<<<L.grid, blk, rtk::transport_pm_smem_bytes(), L.stream>>>(
-            L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -80,16 +106,37 @@ static int occ(const void *f, int threads, size_t smem = 0)
     return n > 0 ? n : 1;
 }
 
-int transport_occupancy_fast(bool fp64)
+int transport_occupancy_fast(bool fp64, int variant)
 {
     if (fp64) {
         transport_attr<double, false>();
         return occ((const void *)rtk::k_transport<double, false>, RTD_TX * RTD_TY,
                    rtk::transport_smem_bytes<double>());
     }
-    cudaFuncSetAttribute(rtk::k_transport_pm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)rtk::transport_pm_smem_bytes());
-    return occ((const void *)rtk::k_transport_pm, RTD_TX * RTD_TY, rtk::transport_pm_smem_bytes());
+    switch (variant) {
+    case 1: return pm_occupancy<kTileX[1], kTileY[1]>();
+    case 2: return pm_occupancy<kTileX[2], kTileY[2]>();
+    default: return pm_occupancy<kTileX[0], kTileY[0]>();
+    }
+}
+
+template <int TX, int TY>
+static int pm_occupancy()
+{
+    pm_attr<TX, TY>();
+    return occ((const void *)rtk::k_transport_pm<TX, TY>, TX * TY, rtk::transport_pm_smem_bytes<TX, TY>());
+}
+
+__global__ void k_fill_tune(float4 *U, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        U[i] = make_float4(1.0f, 0.3f, 0.2f, 0.1f);
+}
+
+cudaError_t fill_tune_state(void *U, int64_t n, cudaStream_t s)
+{
+    k_fill_tune<<<1024, 256, 0, s>>>(reinterpret_cast<float4 *>(U), n);
+    return cudaGetLastError();
 }
 
 int chem_occupancy_fast(bool fp64, int G)

@@ -53,17 +53,17 @@ static int occ(const void *f, int threads, size_t smem = 0)
     return n > 0 ? n : 1;
 }
 
-int transport_occupancy_fast(bool fp64);
+int transport_occupancy_fast(bool fp64, int variant);
 int chem_occupancy_fast(bool fp64, int G);
 
-int transport_occupancy(bool fp64, bool strict)
+int transport_occupancy(bool fp64, bool strict, int variant)
 {
     if (strict) {
         transport_attr_strict();
         return occ((const void *)rtk::k_transport<double, true>, RTD_TX * RTD_TY,
                    rtk::transport_smem_bytes<double>());
     }
-    return transport_occupancy_fast(fp64);
+    return transport_occupancy_fast(fp64, variant);
 }
 
 int chem_occupancy(bool fp64, bool strict, int G)

@@ -19,7 +19,14 @@ struct Launch {
     int64_t nitems;
     int grid;
     cudaStream_t stream;
+    int variant = 0;                 // tile shape of the FP32 transport (kTileX/kTileY)
 };
+
+// tile shapes (columns x rows, one thread per column) of the FP32 transport
+// kernel; the FP64 kernels always use variant 0 (RTD_TX x RTD_TY)
+constexpr int kTileVariants = 3;
+constexpr int kTileX[kTileVariants] = {RTD_TX, 16, 64};
+constexpr int kTileY[kTileVariants] = {RTD_TY, 16, 4};
 
 cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl);
 cudaError_t transport_strict(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl);
@@ -30,13 +37,18 @@ cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *c
 
 // transport tiling of a box: x/y tiles and the number of plane units
 // (ngroups x tiles_x x tiles_y x nz) the transport kernel spreads over its grid
-inline void transport_layout(rtd::BoxDev &B, int ngroups)
+inline void transport_layout(rtd::BoxDev &B, int ngroups, int variant = 0)
 {
-    B.tiles_x = (B.nx + RTD_TX - 1) / RTD_TX;
-    B.tiles_y = (B.ny + RTD_TY - 1) / RTD_TY;
+    const int tx = kTileX[variant], ty = kTileY[variant];
+    B.tiles_x = (B.nx + tx - 1) / tx;
+    B.tiles_y = (B.ny + ty - 1) / ty;
     B.zchunks = 1;
     B.ntitems = (int64_t)ngroups * B.tiles_x * B.tiles_y * B.nz;
 }
+
+// a realizable radiation state (N = 1, F = (0.3, 0.2, 0.1)) in n cells of
+// FP32 U, the input of the launch-shape tuner
+cudaError_t fill_tune_state(void *U, int64_t n, cudaStream_t s);
 
 // rate tables of the chemistry kernel (rate_table.cu); false = unusable
 bool build_rate_table(bool ots, double *out);
@@ -51,7 +63,7 @@ cudaError_t transport_adj(int G, const rtd::BoxDev *boxes, const double *U, cons
                           double *lamU, int64_t ncell, cudaStream_t s);
 
 // resident blocks per SM of each kernel (for persistent grid sizing)
-int transport_occupancy(bool fp64, bool strict);
+int transport_occupancy(bool fp64, bool strict, int variant = 0);
 int chem_occupancy(bool fp64, bool strict, int G);
 
 }  // namespace rtl

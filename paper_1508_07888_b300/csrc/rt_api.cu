@@ -13,6 +13,8 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -51,6 +53,7 @@ struct rt_handle {
     int64_t ntitems = 0, ncitems = 0;
     int zc = 32;
     int tgrid = 1, cgrid = 1;
+    int tvariant = 0;                        // tile shape of the FP32 transport (rtl::kTileX/Y)
     cudaStream_t user = nullptr, s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -128,6 +131,7 @@ static int check_params(const rt_params *p)
         return fail(nullptr, RT_ERR_ARG, "max_halvings outside [0, 60]");
     if (p->precision < RT_PREC_SPLIT || p->precision > RT_PREC_FP64_STRICT)
         return fail(nullptr, RT_ERR_ARG, "unknown precision %d", p->precision);
+    if (p->tune < 0) return fail(nullptr, RT_ERR_ARG, "tune must be >= 0");
     for (int f = 0; f < 6; f++)
         if (p->bc[f] < RT_BC_PERIODIC || p->bc[f] > RT_BC_REFLECTIVE)
             return fail(nullptr, RT_ERR_ARG, "bc[%d]=%d unknown", f, p->bc[f]);
@@ -147,6 +151,116 @@ extern "C" double rt_timestep(const rt_params *p, double dx)
     // radiative Courant condition c <= dx/dt (Sec. 2.2.3) for the unsplit
     // 3-D update: dt = C dx / (3 c)
     return p->cfl * dx / (3.0 * p->c_red);
+}
+
+// ------------------------------------------------------------------ tuner
+// Launch shape of the FP32 transport: tile (rtl::kTileX/Y) x resident blocks
+// per SM.  Every candidate computes each cell with the same arithmetic, so
+// the choice changes the time only.  tune = 1 times every candidate on the
+// handle's boxes (on a synthetic realizable state in scratch, so the
+// caller's state is not touched) and keeps the fastest; the choice is cached
+// per device, group count and box set for later handles.  tune = 2 + k
+// selects candidate k without timing.
+struct TuneChoice {
+    int variant, blocks_per_sm;
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneChoice> g_tune_cache;
+
+static void apply_layout(rt_handle *h, std::vector<rtd::BoxDev> &bd, int variant)
+{
+    int64_t titem = 0;
+    for (auto &D : bd) {
+        rtl::transport_layout(D, h->p.ngroups, variant);
+        D.titem0 = titem;
+        titem += D.ntitems;
+    }
+}
+
+static int tgrid_of(int64_t ntitems, int blocks_per_sm, int nsm)
+{
+    // at least 4 planes per block (each run re-reads 2)
+    return (int)std::max<int64_t>(1, std::min<int64_t>((ntitems + 3) / 4, (int64_t)blocks_per_sm * nsm));
+}
+
+static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
+{
+    std::vector<TuneChoice> cand;
+    for (int v = 0; v < rtl::kTileVariants; v++) {
+        const int occ = rtl::transport_occupancy(false, false, v);
+        for (int m = 1; m <= occ; m++) cand.push_back({v, m});
+    }
+    std::string key = std::to_string(dev) + "/" + std::to_string(h->p.ngroups);
+    for (const auto &D : h->bdev)
+        key += "/" + std::to_string(D.nx) + "x" + std::to_string(D.ny) + "x" + std::to_string(D.nz);
+    TuneChoice best{0, 1};
+    bool have = false;
+    if (tune >= 2) {
+        if ((size_t)(tune - 2) >= cand.size())
+            return fail(h, RT_ERR_ARG, "tune %d: only %d launch shapes", tune, (int)cand.size());
+        best = cand[tune - 2];
+        have = true;
+    } else {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { best = it->second; have = true; }
+    }
+    if (!have) {
+        // scratch copy of the descriptors whose U is a synthetic state
+        int64_t nU = 0;
+        for (const auto &D : h->bdev) nU += (int64_t)h->p.ngroups * D.ncell;
+        void *tU = nullptr;
+        rtd::BoxDev *tbox = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        auto cleanup = [&]() {
+            cudaFree(tU);
+            cudaFree(tbox);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        };
+        int rc = [&]() -> int {
+            CU(h, cudaMalloc(&tU, (size_t)nU * 16));
+            CU(h, cudaMalloc(&tbox, sizeof(rtd::BoxDev) * h->nboxes));
+            CU(h, cudaEventCreate(&e0));
+            CU(h, cudaEventCreate(&e1));
+            CU(h, rtl::fill_tune_state(tU, nU, h->s));
+            std::vector<rtd::BoxDev> bd = h->bdev;
+            int64_t off = 0;
+            for (auto &D : bd) {
+                D.U = (char *)tU + off * 16;
+                off += (int64_t)h->p.ngroups * D.ncell;
+            }
+            float best_ms = 0.f;
+            for (const auto &c : cand) {
+                apply_layout(h, bd, c.variant);
+                int64_t nt = 0;
+                for (const auto &D : bd) nt += D.ntitems;
+                CU(h, cudaMemcpyAsync(tbox, bd.data(), sizeof(rtd::BoxDev) * h->nboxes,
+                                      cudaMemcpyHostToDevice, h->s));
+                rtl::Launch L{tbox, h->nboxes, nt, tgrid_of(nt, c.blocks_per_sm, nsm), h->s, c.variant};
+                CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));      // warm-up
+                CU(h, cudaEventRecord(e0, h->s));
+                for (int r = 0; r < 5; r++) CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));
+                CU(h, cudaEventRecord(e1, h->s));
+                CU(h, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CU(h, cudaEventElapsedTime(&ms, e0, e1));
+                if (!have || ms < best_ms) { best = c; best_ms = ms; have = true; }
+            }
+            return RT_OK;
+        }();
+        cleanup();
+        if (rc) return rc;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    apply_layout(h, h->bdev, best.variant);
+    h->ntitems = 0;
+    for (const auto &D : h->bdev) h->ntitems += D.ntitems;
+    h->tvariant = best.variant;
+    h->tgrid = tgrid_of(h->ntitems, best.blocks_per_sm, nsm);
+    CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * h->nboxes, cudaMemcpyHostToDevice));
+    return RT_OK;
 }
 
 extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *boxes, int nboxes,
@@ -292,6 +406,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 h->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((titem + 3) / 4, (int64_t)to * nsm));
                 const int64_t wpb = RTD_CHEM_BLOCK / 32;         // warps (work items) per block
                 h->cgrid = (int)std::min<int64_t>((citem + wpb - 1) / wpb, (int64_t)co * nsm);
+                if (!fp64 && p->tune > 0) return tune_transport(h, p->tune, dev, nsm);
                 return RT_OK;
             }()))
             return bail(rc);
@@ -367,7 +482,7 @@ extern "C" int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *ce
 // before, between and after the kernels (the third interval stays empty)
 static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = nullptr)
 {
-    rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s};
+    rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s, h->tvariant};
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
     const rtd::DiagBuf db{h->d_partials, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
     cudaError_t e;
@@ -696,6 +811,11 @@ extern "C" int rt_query(rt_handle *h, rt_stats *st)
         st->kernel_ms[j] = h->kernel_ms[j];
         st->kernel_launches[j] = h->kernel_launches[j];
     }
+    const int v = h->fp64 ? 0 : h->tvariant;
+    st->tile_x = rtl::kTileX[v];
+    st->tile_y = rtl::kTileY[v];
+    st->transport_grid = h->tgrid;
+    st->chem_grid = h->cgrid;
     return RT_OK;
 }
 

@@ -525,25 +525,31 @@ __device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
+template <int TX, int TY>
 struct TransportSmemPM {
-    V4<float> U[TP_STAGES][TP_H][TP_W];
-    float4 H[2][4][TP_H][TP_W];        // per cell: Rx, Lx, Ry, Ly of two planes
+    V4<float> U[TP_STAGES][TY + 2][TX + 2];
+    float4 H[2][4][TY + 2][TX + 2];    // per cell: Rx, Lx, Ry, Ly of two planes
 };
 
-constexpr size_t transport_pm_smem_bytes() { return sizeof(TransportSmemPM); }
+template <int TX, int TY>
+constexpr size_t transport_pm_smem_bytes() { return sizeof(TransportSmemPM<TX, TY>); }
 
 // FP32 transport of the split form.  Same pipeline and work split as
 // k_transport; the unsplit GLF update is evaluated in its convex form
 //   U* = (1 - 3 lam) U + (lam/2) sum_d [ (U + G_d)(left_d) + (U - G_d)(right_d) ],
 // which equals U - lam sum_d (Phi_{d,+} - Phi_{d,-}) with Phi of Eq. e:glf.
 // Each cell computes its halves once per plane; x/y neighbours read them from
-// shared memory, the z halves stay in registers.
-__global__ void __launch_bounds__(RTD_TX *RTD_TY)
+// shared memory, the z halves stay in registers.  The tile (TX x TY columns,
+// one thread each) is a template parameter so the launch shape can be tuned
+// per box set; every shape computes each cell with the same arithmetic.
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
 k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
 {
-    constexpr int TX = RTD_TX, TY = RTD_TY, S = TP_STAGES;
+    static_assert(2 * TX + 2 * TY <= TX * TY, "one halo cell per thread at most");
+    constexpr int S = TP_STAGES;
     extern __shared__ __align__(16) unsigned char tp_smem_raw[];
-    TransportSmemPM &sm = *reinterpret_cast<TransportSmemPM *>(tp_smem_raw);
+    TransportSmemPM<TX, TY> &sm = *reinterpret_cast<TransportSmemPM<TX, TY> *>(tp_smem_raw);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     if (blockIdx.x == 0 && tid == 0) ctl->step += 1;

@@ -91,3 +91,35 @@ def test_group_table_rejects_bad_edges():
         B.rt_group_table([10.0, 20.0], 5e4)
     with pytest.raises(B.RTError):
         B.rt_group_table([13.6, 13.0], 5e4)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of rt_params, rt_box and rt_stats have the sizes and
+    field offsets a C compiler gives the declarations in include/rt_m1.h."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    structs = {"rt_params": B.rt_params, "rt_box": B.rt_box, "rt_stats": B.rt_stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rt_m1.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            a, b, v = ln.split()
+            got[(a, b)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

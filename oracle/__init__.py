@@ -126,6 +126,9 @@ def lib():
                                         C.c_double, _dp]),
             "orc_run": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                   _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _i64p]),
+            "orc_run_crta": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                       _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _i64p,
+                                       C.c_int64, _i64p, _dp, _dp, _dp]),
             "orc_sigma_HI": (C.c_double, [C.c_double]),
             "orc_transport_cells": (None, [PP, C.c_int, C.c_int, C.c_int, C.c_double, _dp, C.c_int,
                                            C.c_int, _i64p, _dp]),
@@ -268,6 +271,43 @@ def run(p: Params, U, xHI, T, n0, dx: float, nunit: float, nsteps: int,
     err = lib().orc_run(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
                         _ptr(T), _ptr(n0), Sp, nsteps, _ptr(hist), C.byref(ncl))
     return RunResult(U, xHI, T, hist, err, ncl.value)
+
+
+@dataclass
+class CrtaResult:
+    coarse: RunResult
+    xHI_fine: np.ndarray
+    T_fine: np.ndarray
+
+
+def run_crta(p: Params, U, xHI, T, n0, dx: float, nunit: float, nsteps: int, S,
+             parent, n0_fine, xHI_fine, T_fine) -> CrtaResult:
+    """run() with a CRTA fine level (Sec. 5): refined cells f run the chemistry
+    with the post-transport radiation and the source of their coarse parent
+    parent[f] (linear cell index); their radiation result is not kept."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    xHI = np.array(xHI, dtype=np.float64, order="C", copy=True)
+    T = np.array(T, dtype=np.float64, order="C", copy=True)
+    n0 = np.ascontiguousarray(n0, dtype=np.float64)
+    G, nz, ny, nx, _ = U.shape
+    parent = np.ascontiguousarray(parent, dtype=np.int64)
+    nf = len(parent)
+    n0f = np.ascontiguousarray(n0_fine, dtype=np.float64)
+    xf = np.array(xHI_fine, dtype=np.float64, copy=True)
+    Tf = np.array(T_fine, dtype=np.float64, copy=True)
+    assert n0f.shape == xf.shape == Tf.shape == (nf,)
+    assert nf == 0 or (parent.min() >= 0 and parent.max() < nx * ny * nz)
+    hist = np.zeros((nsteps, NDIAG))
+    ncl = C.c_int64()
+    Sp = None
+    if S is not None:
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        assert S.shape == (G, nx * ny * nz)
+        Sp = _ptr(S)
+    err = lib().orc_run_crta(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
+                             _ptr(T), _ptr(n0), Sp, nsteps, _ptr(hist), C.byref(ncl), nf,
+                             _ptr(parent), _ptr(n0f), _ptr(xf), _ptr(Tf))
+    return CrtaResult(RunResult(U, xHI, T, hist, err, ncl.value), xf, Tf)
 
 
 def step_cells(p: Params, U, xHI, T, n0, dx: float, nunit: float, cells, S=None):

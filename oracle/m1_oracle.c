@@ -591,9 +591,31 @@ int orc_step_cells(const orc_params *p, int nx, int ny, int nz, double dx, doubl
 /*    hist[step][5] = {ionised fraction (volume weighted), photon total,*/
 /*    max |F|/(cN), count(xHI < 0.5), mean sub-cycles per cell}        */
 /* ------------------------------------------------------------------ */
+/* nsteps steps with an optional CRTA fine level (Sec. 5, second
+ * approximation: transport only on the coarse grid, thermochemistry also on
+ * refined cells, which see the coarse radiation field injected unchanged).
+ * Reading: each of the nfine refined cells runs the same sub-cycled
+ * chemistry as a coarse cell over the coarse dt, starting from the
+ * post-transport N, F of its parent coarse cell parent[f] and with the
+ * parent's source term per unit volume; the refined cell's own radiation
+ * result is not kept, since radiation lives on the coarse grid only. */
+int orc_run_crta(const orc_params *p, int nx, int ny, int nz, double dx, double nunit,
+                 double *U, double *xHI, double *T, const double *n0, const double *S,
+                 int nsteps, double *hist, int64_t *nclamp_out, int64_t nfine,
+                 const int64_t *parent, const double *n0f, double *xHIf, double *Tf);
+
 int orc_run(const orc_params *p, int nx, int ny, int nz, double dx, double nunit,
             double *U, double *xHI, double *T, const double *n0, const double *S,
             int nsteps, double *hist, int64_t *nclamp_out)
+{
+    return orc_run_crta(p, nx, ny, nz, dx, nunit, U, xHI, T, n0, S, nsteps, hist, nclamp_out,
+                        0, NULL, NULL, NULL, NULL);
+}
+
+int orc_run_crta(const orc_params *p, int nx, int ny, int nz, double dx, double nunit,
+                 double *U, double *xHI, double *T, const double *n0, const double *S,
+                 int nsteps, double *hist, int64_t *nclamp_out, int64_t nfine,
+                 const int64_t *parent, const double *n0f, double *xHIf, double *Tf)
 {
     size_t ncell = (size_t)nx * ny * nz;
     int G = p->G;
@@ -626,6 +648,18 @@ int orc_run(const orc_params *p, int nx, int ny, int nz, double dx, double nunit
             for (int i = 0; i < G; i++)
                 for (int m = 0; m < 4; m++) U[4 * (ncell * i + id) + m] = Uc[4 * i + m];
             cyc_sum += ncyc;
+        }
+        /* refined cells: the parent's post-transport radiation and source */
+#pragma omp parallel for num_threads(orc_threads) schedule(dynamic, 256) reduction(|:err)
+        for (int64_t f = 0; f < nfine; f++) {
+            size_t id = (size_t)parent[f];
+            double Uc[4 * ORC_MAXG], Sc[ORC_MAXG];
+            for (int i = 0; i < G; i++) {
+                for (int m = 0; m < 4; m++) Uc[4 * i + m] = Us[4 * (ncell * i + id) + m];
+                Sc[i] = S ? S[ncell * i + id] : 0.0;
+            }
+            int ncyc = 0;
+            err |= orc_chem_cell(p, dt, nunit, n0f[f], Sc, Uc, &xHIf[f], &Tf[f], &ncyc);
         }
         if (hist) {
             double X = 0.0, ph = 0.0, fmax = 0.0, nion = 0.0;

@@ -61,7 +61,7 @@ def lognormal_field(n, sigma: float, slope: float, seed: int, nbar: float = 1e-3
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (-slope / 4.0)
-    g = np.fft.irfftn(wk * amp, s=shape)
+    g = np.fft.irfftn(wk * amp, s=shape, axes=tuple(range(len(shape))))
     g = (g - g.mean()) / g.std()
     return f32(nbar * np.exp(sigma * g))
 
@@ -209,6 +209,34 @@ def target_perturbation(nsrc: int, seed: int = 5, scale: float = 0.1) -> np.ndar
     """Multiplicative luminosity perturbation exp(scale * z), z ~ N(0, 1)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.exp(scale * rng.standard_normal(nsrc))
+
+
+@dataclass
+class FineLevel:
+    """Refined cells of a CRTA fine level: parent coarse cell (linear index),
+    density and initial state of each refined cell."""
+    parent: np.ndarray     # int64 [nfine]
+    n0: np.ndarray         # [nfine], cm^-3, float32-representable
+    xHI: np.ndarray        # [nfine]
+    T: np.ndarray          # [nfine]
+
+
+def refine_densest(box: "Box", frac: float = 0.125, sigma: float = 0.5, seed: int = 7,
+                   children: int = 8) -> FineLevel:
+    """Split the densest `frac` of the coarse cells into `children` refined
+    cells each (ties to the lower index); a child's density is its parent's
+    times a lognormal factor (width sigma) normalised so the children's mean
+    is the parent's density.  Children start in the parent's initial state."""
+    n0 = box.n0.reshape(-1)
+    k = max(1, int(round(frac * n0.size)))
+    order = np.lexsort((np.arange(n0.size), -n0))
+    parents = np.sort(order[:k]).astype(np.int64)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = np.exp(sigma * rng.standard_normal((k, children)))
+    w /= w.mean(axis=1, keepdims=True)
+    nf = f32((n0[parents][:, None] * w).reshape(-1))
+    parent = np.repeat(parents, children)
+    return FineLevel(parent=parent, n0=nf, xHI=np.full(nf.size, box.xHI0), T=np.full(nf.size, box.T0))
 
 
 def random_realizable_state(shape, ngroups: int, seed: int, nmax: float = 1.0):

@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=5)
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-crta", action="store_true")
     return ap.parse_args()
 
 
@@ -348,6 +349,47 @@ def ensemble_run(B, ws, K=3):
             "rt_steps_per_run": w.steps, "launches_per_step": 2, "graph": True}
 
 
+def crta_run(K=3, nsteps=100):
+    """CRTA fine level (Sec. 5): the 128^3 workload with its densest eighth
+    refined into 8 children each (2,097,152 refined cells, densities
+    lognormal around the parent's), 100 steps per run; the fine chemistry
+    runs after the coarse chemistry of every step, timed by CUDA events."""
+    import torch
+    from paper_1508_07888_b300 import binding as B
+    from paper_1508_07888_b300 import inputs as I
+    w = workload()
+    fine = I.refine_densest(w.boxes[0], frac=0.125, seed=7)
+    r = DeviceRun(w, B.RT_PREC_SPLIT)
+    x0 = torch.as_tensor(fine.xHI, device="cuda")
+    T0 = torch.as_tensor(fine.T, device="cuda")
+    xf, Tf = r.solver.set_fine(0, fine.parent, fine.n0, fine.xHI, fine.T)
+    def reset():
+        r.reset()
+        xf.copy_(x0)
+        Tf.copy_(T0)
+    reset()
+    r.run(nsteps)
+    B.rt_set_profiling(r.solver.h, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        reset()
+        r.run(nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = B.rt_query(r.solver.h)
+    r.close()
+    nf = fine.parent.size
+    fine_ms = st.kernel_ms[2] / max(st.kernel_launches[2], 1)
+    return {"workload": "reion_128^3_g3 + densest 1/8 refined x8", "fine_cells": int(nf),
+            "rt_steps_per_run": nsteps, "ms_per_run": ms / K,
+            "fine_ms_per_step": fine_ms,
+            "fine_cell_updates_per_s": nf / (fine_ms * 1e-3),
+            "all_cell_updates_per_s": (w.cells + nf) * nsteps * K / (ms * 1e-3)}
+
+
 def adjoint_run():
     """The adjoint workload (64^3, 16 sources, 1 group, 4 fixed chemistry
     intervals, 200 steps, checkpoints every 20): forward and reverse time of
@@ -544,6 +586,7 @@ def main():
 
     ens = None if args.no_ensemble else ensemble_run(B, ws)
     adj = None if args.no_adjoint else adjoint_run()
+    crta = None if args.no_crta else crta_run()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -565,7 +608,7 @@ def main():
                             "launches": kern[k]["launches"]} for k in kern},
             "launch": launch,
             "fp64_form": fp64, "e2e": e2e, "cpu_baseline": cpu,
-            "ensemble": ens, "adjoint": adj,
+            "ensemble": ens, "adjoint": adj, "crta": crta,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "final_diag": dict(zip(B.DIAG_NAMES, diag)),
         }

@@ -126,9 +126,8 @@ typedef struct rt_stats {
     int64_t cells;                       /* cells over all boxes */
     double  last_diag[RT_NDIAG];         /* diagnostics of box 0 after the last step */
     double  kernel_ms[3];                /* with profiling on: summed CUDA-event time of the
-                                            transport and chemistry kernels; the per-box
-                                            diagnostics run inside the chemistry kernel, so
-                                            the third entry stays 0 */
+                                            transport, chemistry (with the fused per-box
+                                            diagnostics) and CRTA fine-level kernels */
     int64_t kernel_launches[3];          /* launches timed into kernel_ms */
     int     tile_x, tile_y;              /* transport tile (columns x rows per block) */
     int     transport_grid, chem_grid;   /* blocks of the persistent transport / chemistry grids */
@@ -148,6 +147,25 @@ RT_API int rt_create(rt_handle **h, const rt_params *p, const rt_box *boxes, int
  * is S_i = (sum_k Q_k frac_i) / (dx^3 nunit), duplicates summed in list order.
  * Replaces the box's previous sources; nsrc = 0 removes them. */
 RT_API int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *cell, const double *Q);
+
+/* CRTA fine level of `box` (Sec. 5, coarse radiative transport
+ * approximation: radiation is transported on the coarse grid only, while
+ * the thermochemistry also runs on refined cells, which see the coarse
+ * radiation field injected unchanged).  After the coarse chemistry of every
+ * later step, each of the nfine refined cells runs the same sub-cycled
+ * chemistry over the box's dt, starting from the post-transport N, F of its
+ * parent coarse cell and with the parent's source term per unit volume; its
+ * radiation result is not kept.
+ *   parent  device, nfine int64: linear index of the parent cell in the box
+ *           (validated and copied by the library)
+ *   n0      device, nfine densities (cm^-3), float (SPLIT) or double
+ *   xHI, T  device, nfine doubles: the refined cells' state, updated in place
+ * The caller owns n0, xHI and T, which must stay valid while registered.
+ * nfine = 0 removes the box's fine level.  Synchronises the handle's stream.
+ * rt_adjoint differentiates the coarse run only and leaves the fine level
+ * untouched. */
+RT_API int rt_set_fine(rt_handle *h, int box, int64_t nfine, const int64_t *parent, const void *n0,
+                       double *xHI, double *T);
 
 /* Advance all boxes by nsteps (>= 0) steps, in place.  hist: device pointer to
  * nsteps*nboxes*RT_NDIAG doubles ([step][box][diag]) or NULL.  Returns the

@@ -81,8 +81,8 @@ class rt_stats(C.Structure):
 
 EXPORTS = ("rt_create", "rt_set_sources", "rt_step", "rt_upload", "rt_download", "rt_query",
            "rt_set_profiling", "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table",
-           "rt_transport_static", "rt_adjoint")
-KERNELS = ("transport", "chemistry", "diagnostics")   # diagnostics: fused into chemistry
+           "rt_transport_static", "rt_adjoint", "rt_set_fine")
+KERNELS = ("transport", "chemistry", "fine_chemistry")   # chemistry includes the diagnostics
 
 _lib = None
 
@@ -107,6 +107,7 @@ def lib(build_if_missing: bool = True):
     sig = {
         "rt_create": (C.c_int, [C.POINTER(vp), C.POINTER(rt_params), C.POINTER(rt_box), C.c_int, vp]),
         "rt_set_sources": (C.c_int, [vp, C.c_int, C.c_int, i64p, dp]),
+        "rt_set_fine": (C.c_int, [vp, C.c_int, C.c_int64, vp, vp, vp, vp]),
         "rt_step": (C.c_int, [vp, C.c_int, vp]),
         "rt_upload": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
         "rt_download": (C.c_int, [vp, C.c_int, vp, vp, vp]),
@@ -165,6 +166,13 @@ def rt_set_sources(h, box: int, cells, Q):
     assert cells.shape == Q.shape
     _check(lib().rt_set_sources(h, box, len(cells), cells.ctypes.data_as(C.POINTER(C.c_int64)),
                                 Q.ctypes.data_as(C.POINTER(C.c_double))), h)
+
+
+def rt_set_fine(h, box: int, nfine: int, parent_ptr: int, n0_ptr: int, xHI_ptr: int, T_ptr: int):
+    """CRTA fine level of a box (device pointers; nfine = 0 removes it)."""
+    _check(lib().rt_set_fine(h, box, int(nfine), C.c_void_p(parent_ptr or None),
+                             C.c_void_p(n0_ptr or None), C.c_void_p(xHI_ptr or None),
+                             C.c_void_p(T_ptr or None)), h)
 
 
 def rt_step(h, nsteps: int, hist_ptr: int = 0) -> int:
@@ -295,6 +303,22 @@ class Solver:
 
     def set_sources(self, box: int, cells, Q):
         rt_set_sources(self.h, box, cells, Q)
+
+    def set_fine(self, box: int, parent, n0, xHI, T):
+        """CRTA fine level of a box from torch device tensors (kept referenced:
+        the library keeps pointers to n0, xHI and T)."""
+        t = self.torch
+        fp = t.float64 if self.fp64 else t.float32
+        parent = t.as_tensor(parent, dtype=t.int64, device="cuda").contiguous()
+        n0 = t.as_tensor(n0, dtype=fp, device="cuda").contiguous()
+        xHI = t.as_tensor(xHI, dtype=t.float64, device="cuda").contiguous()
+        T = t.as_tensor(T, dtype=t.float64, device="cuda").contiguous()
+        assert parent.shape == n0.shape == xHI.shape == T.shape and parent.dim() == 1
+        self.fine = getattr(self, "fine", {})
+        self.fine[box] = (parent, n0, xHI, T)
+        rt_set_fine(self.h, box, parent.numel(), parent.data_ptr(), n0.data_ptr(),
+                    xHI.data_ptr(), T.data_ptr())
+        return xHI, T
 
     def step(self, nsteps: int, hist=None) -> int:
         return rt_step(self.h, nsteps, hist.data_ptr() if hist is not None else 0)

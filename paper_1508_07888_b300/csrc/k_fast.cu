@@ -99,6 +99,31 @@ cudaError_t chem_fast(bool fp64, int G, const Launch &L, const rtd::Phys &ph, rt
 
 
 
+template <int G>
+static void chem_fine_g(bool fp64, const Launch &L, const rtd::FineDev *fines, const rtd::Phys &ph,
+                        rtd::Ctl *ctl)
+{
+    if (fp64)
+        rtk::k_chem_fine<G, double, double, false><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(
+            L.boxes, fines, L.nboxes, L.nitems, ph, ctl);
+    else
+        rtk::k_chem_fine<G, float, float, false><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(
+            L.boxes, fines, L.nboxes, L.nitems, ph, ctl);
+}
+
+cudaError_t chem_fine_fast(bool fp64, int G, const Launch &L, const rtd::FineDev *fines,
+                           const rtd::Phys &ph, rtd::Ctl *ctl)
+{
+    switch (G) {
+    case 1: chem_fine_g<1>(fp64, L, fines, ph, ctl); break;
+    case 2: chem_fine_g<2>(fp64, L, fines, ph, ctl); break;
+    case 3: chem_fine_g<3>(fp64, L, fines, ph, ctl); break;
+    case 4: chem_fine_g<4>(fp64, L, fines, ph, ctl); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 static int occ(const void *f, int threads, size_t smem = 0)
 {
     int n = 0;

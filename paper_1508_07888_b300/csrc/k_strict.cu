@@ -46,6 +46,23 @@ cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *c
     return cudaGetLastError();
 }
 
+cudaError_t chem_fine_strict(int G, const Launch &L, const rtd::FineDev *fines, const rtd::Phys &ph,
+                             rtd::Ctl *ctl)
+{
+#define FINE_G(g)                                                                                \
+    rtk::k_chem_fine<g, double, double, true><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(          \
+        L.boxes, fines, L.nboxes, L.nitems, ph, ctl)
+    switch (G) {
+    case 1: FINE_G(1); break;
+    case 2: FINE_G(2); break;
+    case 3: FINE_G(3); break;
+    case 4: FINE_G(4); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef FINE_G
+    return cudaGetLastError();
+}
+
 static int occ(const void *f, int threads, size_t smem = 0)
 {
     int n = 0;

@@ -34,6 +34,11 @@ cudaError_t chem_fast(bool fp64, int G, const Launch &L, const rtd::Phys &ph, rt
                       const rtd::DiagBuf &db);
 cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
                         const rtd::DiagBuf &db);
+// CRTA fine level: L.nitems work items of 32 refined cells over fines[nboxes]
+cudaError_t chem_fine_fast(bool fp64, int G, const Launch &L, const rtd::FineDev *fines,
+                           const rtd::Phys &ph, rtd::Ctl *ctl);
+cudaError_t chem_fine_strict(int G, const Launch &L, const rtd::FineDev *fines, const rtd::Phys &ph,
+                             rtd::Ctl *ctl);
 
 // transport tiling of a box: x/y tiles and the number of plane units
 // (ngroups x tiles_x x tiles_y x nz) the transport kernel spreads over its grid

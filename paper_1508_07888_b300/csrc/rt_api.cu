@@ -54,6 +54,12 @@ struct rt_handle {
     int zc = 32;
     int tgrid = 1, cgrid = 1;
     int tvariant = 0;                        // tile shape of the FP32 transport (rtl::kTileX/Y)
+    int nsm = 1, chem_occ = 1;               // SMs, resident chemistry blocks per SM
+    std::vector<rtd::FineDev> fdev;          // CRTA fine level per box (host mirror)
+    rtd::FineDev *d_fines = nullptr;
+    std::vector<int64_t *> d_fparent;        // library copies of the parent indices
+    int64_t nfitems = 0;
+    int fgrid = 1;
     cudaStream_t user = nullptr, s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -99,6 +105,8 @@ static void release(rt_handle *h)
     cudaFree(h->d_done);
     cudaFree(h->d_gpart);
     cudaFree(h->d_gdone);
+    cudaFree(h->d_fines);
+    for (auto q : h->d_fparent) cudaFree(q);
     cudaFree(h->d_rtab);
     cudaFree(h->d_lastdiag);
     cudaFree(h->d_ctl);
@@ -406,6 +414,13 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 h->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((titem + 3) / 4, (int64_t)to * nsm));
                 const int64_t wpb = RTD_CHEM_BLOCK / 32;         // warps (work items) per block
                 h->cgrid = (int)std::min<int64_t>((citem + wpb - 1) / wpb, (int64_t)co * nsm);
+                h->nsm = nsm;
+                h->chem_occ = co;
+                h->fdev.assign(nboxes, rtd::FineDev{});
+                h->d_fparent.assign(nboxes, nullptr);
+                CU(h, cudaMalloc(&h->d_fines, sizeof(rtd::FineDev) * nboxes));
+                CU(h, cudaMemcpy(h->d_fines, h->fdev.data(), sizeof(rtd::FineDev) * nboxes,
+                                 cudaMemcpyHostToDevice));
                 if (!fp64 && p->tune > 0) return tune_transport(h, p->tune, dev, nsm);
                 return RT_OK;
             }()))
@@ -480,7 +495,8 @@ extern "C" int rt_set_sources(rt_handle *h, int box, int nsrc, const int64_t *ce
 // one step of the hot path on stream s: transport, then chemistry with the
 // per-box diagnostics fused into it; ev (profiling) = 4 events recorded
 // before, between and after the kernels (the third interval stays empty)
-static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = nullptr)
+static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = nullptr,
+                                bool fine = true)
 {
     rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s, h->tvariant};
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
@@ -495,6 +511,12 @@ static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = 
                   : rtl::chem_fast(h->fp64, h->p.ngroups, Lc, h->ph, h->d_ctl, db);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+    if (fine && h->nfitems > 0) {           // CRTA fine level: reads U* of this step
+        rtl::Launch Lf{h->d_boxes, h->nboxes, h->nfitems, h->fgrid, s};
+        e = h->strict ? rtl::chem_fine_strict(h->p.ngroups, Lf, h->d_fines, h->ph, h->d_ctl)
+                      : rtl::chem_fine_fast(h->fp64, h->p.ngroups, Lf, h->d_fines, h->ph, h->d_ctl);
+        if (e != cudaSuccess) return e;
+    }
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -518,6 +540,69 @@ static int build_graph(rt_handle *h)
         return fail(h, RT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     }
     return RT_OK;
+}
+
+extern "C" int rt_set_fine(rt_handle *h, int box, int64_t nfine, const int64_t *parent,
+                           const void *n0, double *xHI, double *T)
+{
+    if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
+    if (box < 0 || box >= h->nboxes) return fail(h, RT_ERR_ARG, "box %d out of range", box);
+    if (nfine < 0) return fail(h, RT_ERR_ARG, "nfine < 0");
+    if (nfine > 0 && (!parent || !n0 || !xHI || !T))
+        return fail(h, RT_ERR_ARG, "NULL fine-level array");
+    try {
+        const int64_t ncell = h->bdev[box].ncell;
+        std::vector<int64_t> hp((size_t)nfine);
+        if (nfine > 0) {
+            const void *ptrs[4] = {parent, n0, xHI, T};
+            for (const void *q : ptrs) {
+                cudaPointerAttributes a;
+                if (cudaPointerGetAttributes(&a, q) != cudaSuccess ||
+                    (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+                    cudaGetLastError();
+                    return fail(h, RT_ERR_ARG, "fine-level arrays must be device memory");
+                }
+            }
+            CU(h, cudaMemcpy(hp.data(), parent, sizeof(int64_t) * nfine, cudaMemcpyDeviceToHost));
+            for (int64_t f = 0; f < nfine; f++)
+                if (hp[f] < 0 || hp[f] >= ncell)
+                    return fail(h, RT_ERR_ARG, "parent[%lld] = %lld outside [0, %lld)", (long long)f,
+                                (long long)hp[f], (long long)ncell);
+        }
+        CU(h, cudaStreamSynchronize(h->s));             // no step in flight uses the old level
+        cudaFree(h->d_fparent[box]);
+        h->d_fparent[box] = nullptr;
+        if (nfine > 0) {
+            CU(h, cudaMalloc(&h->d_fparent[box], sizeof(int64_t) * nfine));
+            CU(h, cudaMemcpy(h->d_fparent[box], hp.data(), sizeof(int64_t) * nfine,
+                             cudaMemcpyHostToDevice));
+        }
+        rtd::FineDev &F = h->fdev[box];
+        F.parent = h->d_fparent[box];
+        F.n0 = nfine > 0 ? n0 : nullptr;
+        F.xHI = nfine > 0 ? xHI : nullptr;
+        F.T = nfine > 0 ? T : nullptr;
+        F.nfine = nfine;
+        int64_t item = 0;
+        for (auto &D : h->fdev) {
+            D.fitem0 = item;
+            D.nfitems = (D.nfine + RTD_CHEM_ITEM - 1) / RTD_CHEM_ITEM;
+            item += D.nfitems;
+        }
+        h->nfitems = item;
+        const int64_t wpb = RTD_CHEM_BLOCK / 32;
+        h->fgrid = (int)std::max<int64_t>(1, std::min<int64_t>((item + wpb - 1) / wpb,
+                                                               (int64_t)h->chem_occ * h->nsm));
+        CU(h, cudaMemcpy(h->d_fines, h->fdev.data(), sizeof(rtd::FineDev) * h->nboxes,
+                         cudaMemcpyHostToDevice));
+        if (h->graph) {                                 // re-captured with the new level
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        return RT_OK;
+    } catch (...) {
+        return fail(h, RT_ERR_ARG, "unexpected host exception in rt_set_fine");
+    }
 }
 
 extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
@@ -570,7 +655,8 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
     CU(h, cudaStreamSynchronize(h->s));
     if (h->profiling) {
         for (int k = 0; k < nsteps; k++) {
-            for (int j = 0; j < 2; j++) {          // transport, chemistry (+ fused diagnostics)
+            for (int j = 0; j < 3; j++) {          // transport, chemistry (+ diagnostics), fine level
+                if (j == 2 && h->nfitems == 0) continue;
                 float ms = 0.f;
                 CU(h, cudaEventElapsedTime(&ms, h->prof_ev[4 * (size_t)k + j],
                                            h->prof_ev[4 * (size_t)k + j + 1]));
@@ -687,7 +773,7 @@ extern "C" int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, cons
                 CU(h, cudaMemcpyAsync(ckx + ncell * q, D.xHI, bS, cudaMemcpyDeviceToDevice, s));
                 CU(h, cudaMemcpyAsync(ckT + ncell * q, D.T, bS, cudaMemcpyDeviceToDevice, s));
             }
-            CU(h, enqueue_step(h, s));
+            CU(h, enqueue_step(h, s, nullptr, false));
         }
         CU(h, cudaMemcpyAsync(endU, D.U, bU, cudaMemcpyDeviceToDevice, s));
         CU(h, cudaMemcpyAsync(endx, D.xHI, bS, cudaMemcpyDeviceToDevice, s));
@@ -710,7 +796,7 @@ extern "C" int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, cons
                 CU(h, cudaMemcpyAsync(segU + nU * j, D.U, bU, cudaMemcpyDeviceToDevice, s));
                 CU(h, cudaMemcpyAsync(segx + ncell * j, D.xHI, bS, cudaMemcpyDeviceToDevice, s));
                 CU(h, cudaMemcpyAsync(segT + ncell * j, D.T, bS, cudaMemcpyDeviceToDevice, s));
-                CU(h, enqueue_step(h, s));
+                CU(h, enqueue_step(h, s, nullptr, false));
                 CU(h, cudaMemcpyAsync(segUs + nU * j, D.Us, bU, cudaMemcpyDeviceToDevice, s));
             }
             for (int k = k1 - 1; k >= k0; k--) {

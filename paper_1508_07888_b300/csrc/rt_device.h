@@ -104,7 +104,19 @@ struct Ctl {
     unsigned int err;                 // RTD_ERR_* bits
     unsigned long long nclamp;        // post-transport flux-limit clamps
     unsigned long long chem_next;     // chemistry: next work item to hand out
-    unsigned long long chem_fin;      // chemistry: blocks that found no more work
+    unsigned long long chem_fin;      // chemistry: warps that found no more work
+    unsigned long long fine_next;     // CRTA fine level: next work item
+    unsigned long long fine_fin;      // CRTA fine level: warps that found no more work
+};
+
+// CRTA fine level of one box: refined cells that run the chemistry with the
+// post-transport radiation and the source of their coarse parent cell.
+struct FineDev {
+    const int64_t *parent;            // [nfine] parent's linear cell index (library copy)
+    const void *n0;                   // [nfine] caller's densities (float SPLIT, double FP64)
+    double *xHI, *T;                  // [nfine] caller's state, read/write
+    int64_t nfine;
+    int64_t fitem0, nfitems;          // work items (32 refined cells) of this box
 };
 
 }  // namespace rtd

@@ -25,6 +25,7 @@ using rtd::BoxDev;
 using rtd::Ctl;
 using rtd::DiagBuf;
 using rtd::DiagPart;
+using rtd::FineDev;
 using rtd::Phys;
 
 // ------------------------------------------------------------- vector I/O
@@ -1238,5 +1239,89 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
 }
 
 
+
+// CRTA fine level (Sec. 5): one work item = 32 refined cells of one box, one
+// warp.  Each refined cell takes its parent's post-transport N, F (the field
+// the coarse chemistry used, still in U*) and source term, its own density
+// and state, and runs the same sub-cycled chemistry over the box's dt; its
+// radiation result is discarded (radiation is transported on the coarse grid
+// only).  Runs after the coarse chemistry of the step.
+__device__ __forceinline__ int find_fine_box(const FineDev *fines, int nboxes, int64_t item)
+{
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fines[mid].fitem0 <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int G, typename TU, typename TN, bool STRICT>
+__global__ void __launch_bounds__(RTD_CHEM_BLOCK)
+k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines, int nboxes,
+            int64_t nitems, Phys ph, Ctl *ctl)
+{
+    const int lane = threadIdx.x & 31;
+    const double *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
+    for (;;) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(&ctl->fine_next, 1ull);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= (unsigned long long)nitems) break;
+        const int64_t it = (int64_t)k;
+        const int b = find_fine_box(fines, nboxes, it);
+        const BoxDev &B = boxes[b];
+        const FineDev &F = fines[b];
+        const int64_t f = (it - F.fitem0) * RTD_CHEM_ITEM + lane;
+        if (f >= F.nfine) continue;
+        const int64_t c = F.parent[f];
+        const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
+        Cell<G> s;
+#pragma unroll
+        for (int i = 0; i < G; i++) {
+            const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
+            s.N[i] = to_d(u.x);
+            s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
+        }
+        s.xHI = F.xHI[f];
+        s.T = F.T[f];
+        const double n0 = ldn(reinterpret_cast<const TN *>(F.n0), f);
+        double S[G];
+#pragma unroll
+        for (int i = 0; i < G; i++) S[i] = 0.0;
+        if (B.nsrc > 0) {
+            int lo = 0, hi = B.nsrc - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (B.src_cell[mid] < c) lo = mid + 1; else hi = mid;
+            }
+            if (B.src_cell[lo] == c)
+#pragma unroll
+                for (int i = 0; i < G; i++) S[i] = B.src_S[(int64_t)lo * G + i];
+        }
+        int ncyc = 0;
+        unsigned int err = 0;
+        if (ph.nsub > 0) {
+            const double h = B.dt / ph.nsub;
+            for (int q = 0; q < ph.nsub; q++) err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, h, false, ncyc);
+        } else {
+            err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, B.dt, true, ncyc);
+        }
+        if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
+        if (err) atomicOr(&ctl->err, err);
+        F.xHI[f] = s.xHI;
+        F.T[f] = s.T;
+    }
+    // the last warp to finish resets the counters for the next launch
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+        if (atomicAdd(&ctl->fine_fin, 1ull) == nw - 1ull) {
+            ctl->fine_next = 0ull;
+            ctl->fine_fin = 0ull;
+            __threadfence();
+        }
+    }
+}
 
 }  // namespace rtk

@@ -47,7 +47,13 @@ class _Params(C.Structure):
         ("beta", C.c_double),
         ("bc", C.c_int * 6),
         ("max_halvings", C.c_int),
+        ("flux", C.c_int),
+        ("hll", C.POINTER(C.c_double)),
+        ("hll_nf", C.c_int),
+        ("hll_nm", C.c_int),
     ]
+
+FLUX_GLF, FLUX_HLL = 0, 1
 
 
 @dataclass
@@ -68,6 +74,9 @@ class Params:
     beta: float = 0.0
     bc: Sequence[int] = field(default_factory=lambda: [BC_PERIODIC] * 6)
     max_halvings: int = 30
+    flux: int = FLUX_GLF
+    hll_nf: int = 64                # HLL speed table nodes in f (0..1) and mu (-1..1)
+    hll_nm: int = 64
 
     @property
     def G(self) -> int:
@@ -91,6 +100,11 @@ class Params:
         for k in range(6):
             p.bc[k] = int(self.bc[k])
         p.max_halvings = int(self.max_halvings)
+        p.flux = int(self.flux)
+        if self.flux == FLUX_HLL:
+            tab = hll_speed_table(self.hll_nf, self.hll_nm)
+            p.hll = tab.ctypes.data_as(C.POINTER(C.c_double))
+            p.hll_nf, p.hll_nm = self.hll_nf, self.hll_nm
         return p
 
 
@@ -138,6 +152,9 @@ def lib():
             "orc_chem_cell_adj": (C.c_int, [PP, C.c_double, C.c_double, C.c_double, _dp, _dp,
                                             C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp]),
             "orc_flux_jacobian": (None, [C.c_int, _dp, _dp]),
+            "orc_flux_jacobian_fmu": (None, [C.c_double, C.c_double, _dp]),
+            "orc_hll_speeds": (None, [PP, C.c_int, _dp, _dp, _dp]),
+            "orc_face_flux": (None, [PP, C.c_int, _dp, _dp, _dp]),
             "orc_transport_adj": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp,
                                             _dp]),
             "orc_adjoint": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -349,6 +366,58 @@ def flux_jacobian(d: int, U4) -> np.ndarray:
     J = np.zeros((4, 4))
     lib().orc_flux_jacobian(d, _ptr(U), _ptr(J))
     return J
+
+
+def flux_jacobian_fmu(f: float, mu: float) -> np.ndarray:
+    """Jacobian of the x flux at N = 1, F = f (mu, sqrt(1 - mu^2), 0) on the
+    closure's smooth branch (valid up to and at f = 1)."""
+    J = np.zeros((4, 4))
+    lib().orc_flux_jacobian_fmu(float(f), float(mu), _ptr(J))
+    return J
+
+
+_HLL_TABLES: dict = {}
+
+
+def hll_speed_table(nf: int = 64, nm: int = 64) -> np.ndarray:
+    """Largest eigenvalue of the x-flux Jacobian (units of c) at the nodes
+    f_i = 1 - (i/nf)^2, mu_j = -1 + 2j/nm: [nf + 1, nm + 1].  For f < 1 the
+    eigenvalues come from numpy's general eigenvalue routine (they are real
+    for the M1 system); at f = 1 all four equal mu (free streaming along the
+    flux direction), where that routine loses digits on the repeated root."""
+    key = (nf, nm)
+    if key not in _HLL_TABLES:
+        t = np.zeros((nf + 1, nm + 1))
+        for i in range(nf + 1):
+            f = 1.0 - (i / nf) ** 2
+            for j in range(nm + 1):
+                mu = -1.0 + 2.0 * j / nm
+                if i == 0:
+                    t[i, j] = mu
+                    continue
+                ev = np.linalg.eigvals(flux_jacobian_fmu(f, mu))
+                assert np.max(np.abs(ev.imag)) < 1e-6, (i, j, ev)
+                t[i, j] = np.max(ev.real)
+        _HLL_TABLES[key] = np.ascontiguousarray(t)
+    return _HLL_TABLES[key]
+
+
+def face_flux(p: Params, d: int, L, R) -> np.ndarray:
+    """Intercell flux (p.flux: GLF or HLL) between states L and R along d."""
+    Lc = np.ascontiguousarray(L, dtype=np.float64)
+    Rc = np.ascontiguousarray(R, dtype=np.float64)
+    out = np.zeros(4)
+    lib().orc_face_flux(C.byref(p.to_c()), d, _ptr(Lc), _ptr(Rc), _ptr(out))
+    return out
+
+
+def hll_speeds(p: Params, d: int, U4) -> tuple[float, float]:
+    """(lmin, lmax) of a state along axis d from the interpolated table."""
+    U = np.ascontiguousarray(U4, dtype=np.float64)
+    a, b = C.c_double(), C.c_double()
+    pc = p.to_c()
+    lib().orc_hll_speeds(C.byref(pc), d, _ptr(U), C.byref(a), C.byref(b))
+    return a.value, b.value
 
 
 def transport_adj(p: Params, U, lamS, lam: float) -> np.ndarray:

@@ -60,6 +60,10 @@
  *   R10 group averages (Eq. e:siggroup and the sigma_E, <E> definitions) over
  *      a black-body photon spectrum; source photons split by the group
  *      fraction of that spectrum (Eq. e:sgroup).
+ *   R11 HLL flux (the paper plans it, Sec. 2.2.3, without formulas): the
+ *      Harten-Lax-van Leer flux with the extreme eigenvalues of the M1 flux
+ *      Jacobian as wave speeds, tabulated in (f, mu) and interpolated
+ *      bilinearly (see face_flux).
  */
 #include <math.h>
 #include <stdint.h>
@@ -104,6 +108,10 @@ typedef struct {
     double alphaA, alphaB, beta; /* cm^3/s, used when rates_const */
     int    bc[6];                /* faces -x,+x,-y,+y,-z,+z: 0 periodic, 1 transmissive, 2 reflective */
     int    max_halvings;         /* cap of the 10% rule */
+    int    flux;                 /* intercell flux: 0 GLF (Eq. e:glf), 1 HLL (R11) */
+    const double *hll;           /* HLL: lambda_max at f_i = 1 - (i/hll_nf)^2, mu_j = -1 + 2j/hll_nm,
+                                    [hll_nf + 1][hll_nm + 1], row-major */
+    int    hll_nf, hll_nm;
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -179,6 +187,97 @@ void orc_glf_flux(int d, const double *L, const double *R, double *Phi)
     for (int m = 0; m < 4; m++)
         Phi[m] = 0.5 * ((GL[m] + GR[m]) - (R[m] - L[m]));
 }
+
+/* ---- HLL intercell flux (R11) ----
+ * The paper names the HLL flux as the less diffusive alternative it plans
+ * after GLF.  Reading: the Harten-Lax-van Leer flux
+ *   Phi = (l+ G_L - l- G_R + l+ l- (U_R - U_L)) / (l+ - l-),
+ *   l+ = max(0, lmax_L, lmax_R),  l- = min(0, lmin_L, lmin_R),
+ * with the extreme eigenvalues of the Jacobian of the physical flux along the
+ * face normal (units of c).  They depend on f = |F|/(cN) and mu = F_d/|F|
+ * only; lmax(f, mu) is the bilinear interpolant, in z = sqrt(1 - f) and mu,
+ * of its values at the nodes of a table (computed outside this file from
+ * the Jacobian below; the eigenvalues split like sqrt(1 - f) from their
+ * common value mu at f = 1, so they are smooth in z), and
+ * lmin(f, mu) = -lmax(f, -mu) by reflection.  A state with N <= 0 or F = 0
+ * takes f = 0 (isotropic speeds).  GLF is the special case l+ = -l- = 1. */
+static double hll_lmax(const orc_params *p, double f, double mu)
+{
+    int nf = p->hll_nf, nm = p->hll_nm;
+    double x = sqrt(1.0 - f) * nf, y = (mu + 1.0) * 0.5 * nm;
+    int i = (int)x, j = (int)y;
+    if (i > nf - 1) i = nf - 1;
+    if (i < 0) i = 0;
+    if (j > nm - 1) j = nm - 1;
+    if (j < 0) j = 0;
+    double tx = x - i, ty = y - j;
+    const double *T = p->hll;
+    double v00 = T[i * (nm + 1) + j], v01 = T[i * (nm + 1) + j + 1];
+    double v10 = T[(i + 1) * (nm + 1) + j], v11 = T[(i + 1) * (nm + 1) + j + 1];
+    return (v00 * (1.0 - tx) + v10 * tx) * (1.0 - ty) + (v01 * (1.0 - tx) + v11 * tx) * ty;
+}
+
+/* wave-speed bounds of state U along axis d */
+static void hll_speeds(const orc_params *p, int d, const double *U, double *lmin, double *lmax)
+{
+    double f = 0.0, mu = 0.0;
+    double N = U[0];
+    if (N > 0.0) {
+        double F = sqrt(U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
+        if (F > 0.0) {
+            f = F / N;
+            if (f > 1.0) f = 1.0;
+            mu = U[1 + d] / F;
+        }
+    }
+    *lmax = hll_lmax(p, f, mu);
+    *lmin = -hll_lmax(p, f, -mu);
+}
+
+/* intercell flux at a face along d from the states and physical fluxes of
+ * its left and right cells (GLF or HLL) */
+static void face_flux(const orc_params *p, int d, const double *UL, const double *GL,
+                      const double *UR, const double *GR, double *Phi)
+{
+    if (p->flux == 0) {
+        for (int m = 0; m < 4; m++) Phi[m] = 0.5 * ((GL[m] + GR[m]) - (UR[m] - UL[m]));
+        return;
+    }
+    double a0, a1, b0, b1;
+    hll_speeds(p, d, UL, &a0, &a1);
+    hll_speeds(p, d, UR, &b0, &b1);
+    double lp = a1 > b1 ? a1 : b1, lm = a0 < b0 ? a0 : b0;
+    if (lp < 0.0) lp = 0.0;
+    if (lm > 0.0) lm = 0.0;
+    if (!(lp - lm > 0.0)) {
+        /* no wave crosses the face (two beams along it, f = 1, mu = 0 on
+           both sides): their fluxes along d vanish; take the mean */
+        for (int m = 0; m < 4; m++) Phi[m] = 0.5 * (GL[m] + GR[m]);
+        return;
+    }
+    for (int m = 0; m < 4; m++)
+        Phi[m] = (lp * GL[m] - lm * GR[m] + lp * lm * (UR[m] - UL[m])) / (lp - lm);
+}
+
+void orc_hll_speeds(const orc_params *p, int d, const double *U, double *lmin, double *lmax)
+{
+    hll_speeds(p, d, U, lmin, lmax);
+}
+
+static void phys_flux(int d, const double *U, double *Gd);
+
+/* the face flux of p->flux between states L and R along d */
+void orc_face_flux(const orc_params *p, int d, const double *L, const double *R, double *Phi)
+{
+    double GL[4], GR[4];
+    phys_flux(d, L, GL);
+    phys_flux(d, R, GR);
+    face_flux(p, d, L, GL, R, GR, Phi);
+}
+
+/* Jacobian of the x flux at N = 1, F = f (mu, sqrt(1 - mu^2), 0), on the
+ * closure's smooth branch (f <= 1; also at f = 1), for the HLL speed table */
+void orc_flux_jacobian_fmu(double f, double mu, double J[4][4]);
 
 /* neighbour state of cell (x,y,z) along axis d, side = -1 or +1, with the
  * global boundary conditions of Sec. 4.2: periodic by default; transmissive
@@ -263,12 +362,11 @@ void orc_transport(const orc_params *p, int nx, int ny, int nz, double lam,
                                 flux_from(d, Us[side], Pg, Gs[side]);
                             }
                         }
-                        for (int m = 0; m < 4; m++) {
-                            /* Eq. e:glf at faces i-1/2 (left neighbour, cell) and i+1/2 */
-                            double Fm = 0.5 * ((Gs[0][m] + Gc[m]) - (Uc[m] - Us[0][m]));
-                            double Fp = 0.5 * ((Gc[m] + Gs[1][m]) - (Us[1][m] - Uc[m]));
-                            diff[d][m] = Fp - Fm;
-                        }
+                        /* faces i-1/2 (left neighbour, cell) and i+1/2 (cell, right) */
+                        double Fm[4], Fp[4];
+                        face_flux(p, d, Us[0], Gs[0], Uc, Gc, Fm);
+                        face_flux(p, d, Uc, Gc, Us[1], Gs[1], Fp);
+                        for (int m = 0; m < 4; m++) diff[d][m] = Fp[m] - Fm[m];
                     }
                     for (int m = 0; m < 4; m++)
                         Og[4 * id + m] = Uc[m] - lam * ((diff[0][m] + diff[1][m]) + diff[2][m]);
@@ -300,11 +398,10 @@ void orc_transport_cells(const orc_params *p, int nx, int ny, int nz, double lam
                 orc_closure(Us[side], Ps, NULL, NULL);
                 flux_from(d, Us[side], Ps, Gs[side]);
             }
-            for (int m = 0; m < 4; m++) {
-                double Fm = 0.5 * ((Gs[0][m] + Gc[m]) - (Uc[m] - Us[0][m]));
-                double Fp = 0.5 * ((Gc[m] + Gs[1][m]) - (Us[1][m] - Uc[m]));
-                diff[d][m] = Fp - Fm;
-            }
+            double Fm[4], Fp[4];
+            face_flux(p, d, Us[0], Gs[0], Uc, Gc, Fm);
+            face_flux(p, d, Uc, Gc, Us[1], Gs[1], Fp);
+            for (int m = 0; m < 4; m++) diff[d][m] = Fp[m] - Fm[m];
         }
         for (int m = 0; m < 4; m++)
             out[4 * k + m] = Uc[m] - lam * ((diff[0][m] + diff[1][m]) + diff[2][m]);
@@ -955,6 +1052,8 @@ int orc_chem_cell_adj(const orc_params *p, double dt, double nunit, double n0, c
     return n;
 }
 
+static void jacobian_smooth(int d, const double *u, double f2, double J[4][4]);
+
 /* Jacobian J[r][m] = d G_d[r] / d U[m] of the physical flux along d (the
  * closure P = N D of orc_closure, with its clamp branch frozen). */
 void orc_flux_jacobian(int d, const double *U, double J[4][4])
@@ -978,6 +1077,15 @@ void orc_flux_jacobian(int d, const double *U, double J[4][4])
         }
         return;
     }
+    jacobian_smooth(d, u, f2, J);
+}
+
+/* smooth-branch Jacobian of the flux along d at N = 1 (it is homogeneous of
+ * degree 0 in (N, F)), velocity u = F/N, f2 = |u|^2 <= 1 */
+static void jacobian_smooth(int d, const double *u, double f2, double J[4][4])
+{
+    memset(J, 0, sizeof(double) * 16);
+    J[0][1 + d] = 1.0;
     double s = sqrt(4.0 - 3.0 * f2);
     double a = ((1.0 + s) - 2.0 * f2) / (5.0 + 2.0 * s);
     double g = (6.0 + 3.0 / (2.0 + s)) / (5.0 + 2.0 * s);
@@ -998,6 +1106,13 @@ void orc_flux_jacobian(int d, const double *U, double J[4][4])
     }
 }
 
+void orc_flux_jacobian_fmu(double f, double mu, double J[4][4])
+{
+    double st = 1.0 - mu * mu;
+    double u[3] = {f * mu, f * sqrt(st > 0.0 ? st : 0.0), 0.0};
+    jacobian_smooth(0, u, f * f, J);
+}
+
 /* Adjoint of orc_transport on a periodic box: lamU = (dUs/dU)^T lamS for
  * every group, with
  *   (Us = U* the post-transport state)
@@ -1009,6 +1124,7 @@ int orc_transport_adj(const orc_params *p, int nx, int ny, int nz, double lam, c
 {
     for (int f = 0; f < 6; f++)
         if (p->bc[f] != 0) return -1;
+    if (p->flux != 0) return -1;                 /* the adjoint is of the GLF step */
     size_t ncell = (size_t)nx * ny * nz;
     int n[3] = {nx, ny, nz};
     size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};

@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-crta", action="store_true")
+    ap.add_argument("--no-hll", action="store_true")
     return ap.parse_args()
 
 
@@ -179,11 +180,12 @@ class DeviceRun:
     """The workload resident in HBM (all its boxes in one handle); reset()
     restores the initial state."""
 
-    def __init__(self, w, precision):
+    def __init__(self, w, precision, flux=0):
         import torch
         from paper_1508_07888_b300 import binding as B
         self.torch, self.B, self.w = torch, B, w
         self.p = make_params(w, precision)
+        self.p.flux = flux
         fp = torch.float64 if precision != B.RT_PREC_SPLIT else torch.float32
         self.init, states = [], []
         for box in w.boxes:
@@ -390,6 +392,36 @@ def crta_run(K=3, nsteps=100):
             "all_cell_updates_per_s": (w.cells + nf) * nsteps * K / (ms * 1e-3)}
 
 
+def hll_run(K=3):
+    """The HLL flux (the less diffusive flux the paper plans) on the same
+    128^3 workload, split form, 500 steps per run: whole-step throughput and
+    the transport kernel's time and HBM rate (algorithmic 32 B per
+    cell-group)."""
+    import torch
+    from paper_1508_07888_b300 import binding as B
+    w = workload()
+    r = DeviceRun(w, B.RT_PREC_SPLIT, flux=1)
+    r.reset()
+    r.run(w.steps)
+    B.rt_set_profiling(r.solver.h, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        r.reset()
+        r.run(w.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = B.rt_query(r.solver.h)
+    r.close()
+    t_ms = st.kernel_ms[0] / max(st.kernel_launches[0], 1)
+    return {"value": w.cells * w.steps * K / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms / K,
+            "transport_ms_per_launch": t_ms,
+            "transport_gbs": 32.0 * w.ngroups * w.cells / (t_ms * 1e-3) / 1e9,
+            "chemistry_ms_per_launch": st.kernel_ms[1] / max(st.kernel_launches[1], 1)}
+
+
 def adjoint_run():
     """The adjoint workload (64^3, 16 sources, 1 group, 4 fixed chemistry
     intervals, 200 steps, checkpoints every 20): forward and reverse time of
@@ -587,6 +619,7 @@ def main():
     ens = None if args.no_ensemble else ensemble_run(B, ws)
     adj = None if args.no_adjoint else adjoint_run()
     crta = None if args.no_crta else crta_run()
+    hll = None if args.no_hll else hll_run()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -608,7 +641,7 @@ def main():
                             "launches": kern[k]["launches"]} for k in kern},
             "launch": launch,
             "fp64_form": fp64, "e2e": e2e, "cpu_baseline": cpu,
-            "ensemble": ens, "adjoint": adj, "crta": crta,
+            "ensemble": ens, "adjoint": adj, "crta": crta, "hll": hll,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "final_diag": dict(zip(B.DIAG_NAMES, diag)),
         }

@@ -78,6 +78,12 @@ typedef enum rt_bc {
     RT_BC_REFLECTIVE = 2     /* ghost = copy with the normal flux component inverted */
 } rt_bc;
 
+typedef enum rt_flux {
+    RT_FLUX_GLF = 0,         /* global Lax-Friedrichs (Eq. e:glf), the paper's flux */
+    RT_FLUX_HLL = 1          /* Harten-Lax-van Leer with the M1 signal speeds (the less
+                                diffusive flux the paper plans, Sec. 2.2.3); see rt_hll_speeds */
+} rt_flux;
+
 typedef struct rt_params {
     int    ngroups;                      /* 1..RT_MAX_GROUPS */
     double sigN[RT_MAX_GROUPS];          /* cm^2, number-weighted group cross-section (Eq. e:siggroup) */
@@ -101,7 +107,9 @@ typedef struct rt_params {
                                             on it): 0 = default, 1 = time every shape at
                                             rt_create on a synthetic state in scratch and keep
                                             the fastest (cached per device and box set for the
-                                            process), 2 + k = shape k; ignored by the FP64 forms */
+                                            process), 2 + k = shape k; ignored by the FP64 forms
+                                            and by the HLL flux */
+    int    flux;                         /* rt_flux; rt_adjoint and rt_transport_static need GLF */
 } rt_params;
 
 typedef struct rt_box {
@@ -221,6 +229,15 @@ RT_API void rt_destroy(rt_handle *h);
 /* Host helper: dt of the radiative Courant condition (Sec. 2.2.3, 3-D
  * reading dt = cfl dx / (3 c_red)); returns a negative value on bad input. */
 RT_API double rt_timestep(const rt_params *p, double dx);
+
+/* Host helper: wave-speed table of the HLL flux (rt_params.flux = RT_FLUX_HLL).
+ * lmax[i][j], (nf + 1) x (nm + 1) doubles, row-major: the largest eigenvalue
+ * (units of c) of the Jacobian of the M1 flux (Levermore closure) along an
+ * axis, at f = |F|/(cN) = 1 - (i/nf)^2 and mu = F_axis/|F| = -1 + 2j/nm; the
+ * kernels use the 64 x 64 table, interpolated bilinearly in (sqrt(1 - f), mu),
+ * and lambda_min(f, mu) = -lambda_max(f, -mu).  Returns RT_ERR_ARG on bad
+ * sizes or a NULL pointer. */
+RT_API int rt_hll_speeds(int nf, int nm, double *lmax);
 
 /* Host helper: group averages of the hydrogen photo-ionisation cross-section
  * over a black-body photon spectrum of temperature T_bb (Eq. e:siggroup and

@@ -49,6 +49,7 @@ class rt_params(C.Structure):
         ("max_halvings", C.c_int),
         ("precision", C.c_int),
         ("tune", C.c_int),
+        ("flux", C.c_int),
     ]
 
 
@@ -81,7 +82,7 @@ class rt_stats(C.Structure):
 
 EXPORTS = ("rt_create", "rt_set_sources", "rt_step", "rt_upload", "rt_download", "rt_query",
            "rt_set_profiling", "rt_last_error", "rt_destroy", "rt_timestep", "rt_group_table",
-           "rt_transport_static", "rt_adjoint", "rt_set_fine")
+           "rt_transport_static", "rt_adjoint", "rt_set_fine", "rt_hll_speeds")
 KERNELS = ("transport", "chemistry", "fine_chemistry")   # chemistry includes the diagnostics
 
 _lib = None
@@ -108,6 +109,7 @@ def lib(build_if_missing: bool = True):
         "rt_create": (C.c_int, [C.POINTER(vp), C.POINTER(rt_params), C.POINTER(rt_box), C.c_int, vp]),
         "rt_set_sources": (C.c_int, [vp, C.c_int, C.c_int, i64p, dp]),
         "rt_set_fine": (C.c_int, [vp, C.c_int, C.c_int64, vp, vp, vp, vp]),
+        "rt_hll_speeds": (C.c_int, [C.c_int, C.c_int, dp]),
         "rt_step": (C.c_int, [vp, C.c_int, vp]),
         "rt_upload": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
         "rt_download": (C.c_int, [vp, C.c_int, vp, vp, vp]),
@@ -166,6 +168,16 @@ def rt_set_sources(h, box: int, cells, Q):
     assert cells.shape == Q.shape
     _check(lib().rt_set_sources(h, box, len(cells), cells.ctypes.data_as(C.POINTER(C.c_int64)),
                                 Q.ctypes.data_as(C.POINTER(C.c_double))), h)
+
+
+RT_FLUX_GLF, RT_FLUX_HLL = 0, 1
+
+
+def rt_hll_speeds(nf: int = 64, nm: int = 64) -> np.ndarray:
+    """The library's HLL wave-speed table, [nf + 1, nm + 1] (host helper)."""
+    out = np.zeros((nf + 1, nm + 1))
+    _check(lib().rt_hll_speeds(nf, nm, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
 
 
 def rt_set_fine(h, box: int, nfine: int, parent_ptr: int, n0_ptr: int, xHI_ptr: int, T_ptr: int):
@@ -234,7 +246,7 @@ def rt_transport_static(p: rt_params, box: rt_box, nsteps: int, stream_ptr: int 
 # ------------------------------------------------------------------ helpers
 def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, isothermal=False,
                 nsub=0, rates_const=False, alphaA=0.0, alphaB=0.0, beta=0.0, bc=(0,) * 6,
-                max_halvings=30, precision=RT_PREC_SPLIT, tune=0) -> rt_params:
+                max_halvings=30, precision=RT_PREC_SPLIT, tune=0, flux=0) -> rt_params:
     p = rt_params()
     p.ngroups = ngroups
     for i in range(ngroups):
@@ -248,6 +260,7 @@ def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, 
     p.max_halvings = max_halvings
     p.precision = precision
     p.tune = int(tune)
+    p.flux = int(flux)
     return p
 
 

@@ -8,18 +8,30 @@ namespace rtl {
 
 // dynamic shared memory of the transport pipeline (above the 48 KB default
 // for FP64); set once per kernel and device before its first launch
-template <typename R, bool STRICT>
+template <typename R, bool STRICT, int FLUX>
 static cudaError_t transport_attr()
 {
     static int done_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (done_dev == dev) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport<R, STRICT>,
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport<R, STRICT, FLUX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rtk::transport_smem_bytes<R>());
+                                         (int)rtk::transport_smem_bytes<R, FLUX>());
     if (e == cudaSuccess) done_dev = dev;
     return e;
+}
+
+// the canonical transport kernel (FP64 forms, and the HLL flux in FP32)
+template <typename R, int FLUX>
+static cudaError_t transport_generic(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
+{
+    cudaError_t e = transport_attr<R, false, FLUX>();
+    if (e != cudaSuccess) return e;
+    rtk::k_transport<R, false, FLUX>
+        <<<L.grid, dim3(RTD_TX, RTD_TY), rtk::transport_smem_bytes<R, FLUX>(), L.stream>>>(
+            L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    return cudaSuccess;
 }
 
 // the FP32 transport with a TX x TY tile: shared-memory attribute set once
@@ -53,22 +65,21 @@ static int pm_occupancy();
 
 cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
-    dim3 blk(RTD_TX, RTD_TY);
-    if (fp64) {
-        cudaError_t e = transport_attr<double, false>();
-        if (e != cudaSuccess) return e;
-        rtk::k_transport<double, false><<<L.grid, blk, rtk::transport_smem_bytes<double>(), L.stream>>>(
-            L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    cudaError_t e = cudaSuccess;
+    if (ph.flux == RTD_FLUX_HLL) {
+        e = fp64 ? transport_generic<double, RTD_FLUX_HLL>(L, zc, ph, ctl)
+                 : transport_generic<float, RTD_FLUX_HLL>(L, zc, ph, ctl);
+    } else if (fp64) {
+        e = transport_generic<double, RTD_FLUX_GLF>(L, zc, ph, ctl);
     } else {
-        cudaError_t e = cudaSuccess;
         switch (L.variant) {
         case 0: e = transport_pm<kTileX[0], kTileY[0]>(L, zc, ph, ctl); break;
         case 1: e = transport_pm<kTileX[1], kTileY[1]>(L, zc, ph, ctl); break;
         case 2: e = transport_pm<kTileX[2], kTileY[2]>(L, zc, ph, ctl); break;
         default: return cudaErrorInvalidValue;
         }
-        if (e != cudaSuccess) return e;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -131,13 +142,19 @@ static int occ(const void *f, int threads, size_t smem = 0)
     return n > 0 ? n : 1;
 }
 
-int transport_occupancy_fast(bool fp64, int variant)
+template <typename R, int FLUX>
+static int generic_occupancy()
 {
-    if (fp64) {
-        transport_attr<double, false>();
-        return occ((const void *)rtk::k_transport<double, false>, RTD_TX * RTD_TY,
-                   rtk::transport_smem_bytes<double>());
-    }
+    transport_attr<R, false, FLUX>();
+    return occ((const void *)rtk::k_transport<R, false, FLUX>, RTD_TX * RTD_TY,
+               rtk::transport_smem_bytes<R, FLUX>());
+}
+
+int transport_occupancy_fast(bool fp64, int variant, int flux)
+{
+    if (flux == RTD_FLUX_HLL)
+        return fp64 ? generic_occupancy<double, RTD_FLUX_HLL>() : generic_occupancy<float, RTD_FLUX_HLL>();
+    if (fp64) return generic_occupancy<double, RTD_FLUX_GLF>();
     switch (variant) {
     case 1: return pm_occupancy<kTileX[1], kTileY[1]>();
     case 2: return pm_occupancy<kTileX[2], kTileY[2]>();

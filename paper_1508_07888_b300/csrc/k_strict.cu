@@ -7,27 +7,35 @@
 
 namespace rtl {
 
+template <int FLUX>
 static cudaError_t transport_attr_strict()
 {
     static int done_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (done_dev == dev) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport<double, true>,
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport<double, true, FLUX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rtk::transport_smem_bytes<double>());
+                                         (int)rtk::transport_smem_bytes<double, FLUX>());
     if (e == cudaSuccess) done_dev = dev;
     return e;
 }
 
+template <int FLUX>
+static cudaError_t transport_strict_f(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
+{
+    cudaError_t e = transport_attr_strict<FLUX>();
+    if (e != cudaSuccess) return e;
+    rtk::k_transport<double, true, FLUX>
+        <<<L.grid, dim3(RTD_TX, RTD_TY), rtk::transport_smem_bytes<double, FLUX>(), L.stream>>>(
+            L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t transport_strict(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
-    dim3 blk(RTD_TX, RTD_TY);
-    cudaError_t e = transport_attr_strict();
-    if (e != cudaSuccess) return e;
-    rtk::k_transport<double, true><<<L.grid, blk, rtk::transport_smem_bytes<double>(), L.stream>>>(
-        L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
-    return cudaGetLastError();
+    return ph.flux == RTD_FLUX_HLL ? transport_strict_f<RTD_FLUX_HLL>(L, zc, ph, ctl)
+                                   : transport_strict_f<RTD_FLUX_GLF>(L, zc, ph, ctl);
 }
 
 cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, const rtd::DiagBuf &db)
@@ -70,17 +78,22 @@ static int occ(const void *f, int threads, size_t smem = 0)
     return n > 0 ? n : 1;
 }
 
-int transport_occupancy_fast(bool fp64, int variant);
+int transport_occupancy_fast(bool fp64, int variant, int flux);
 int chem_occupancy_fast(bool fp64, int G);
 
-int transport_occupancy(bool fp64, bool strict, int variant)
+int transport_occupancy(bool fp64, bool strict, int variant, int flux)
 {
     if (strict) {
-        transport_attr_strict();
-        return occ((const void *)rtk::k_transport<double, true>, RTD_TX * RTD_TY,
-                   rtk::transport_smem_bytes<double>());
+        if (flux == RTD_FLUX_HLL) {
+            transport_attr_strict<RTD_FLUX_HLL>();
+            return occ((const void *)rtk::k_transport<double, true, RTD_FLUX_HLL>, RTD_TX * RTD_TY,
+                       rtk::transport_smem_bytes<double, RTD_FLUX_HLL>());
+        }
+        transport_attr_strict<RTD_FLUX_GLF>();
+        return occ((const void *)rtk::k_transport<double, true, RTD_FLUX_GLF>, RTD_TX * RTD_TY,
+                   rtk::transport_smem_bytes<double, RTD_FLUX_GLF>());
     }
-    return transport_occupancy_fast(fp64, variant);
+    return transport_occupancy_fast(fp64, variant, flux);
 }
 
 int chem_occupancy(bool fp64, bool strict, int G)

@@ -68,7 +68,7 @@ cudaError_t transport_adj(int G, const rtd::BoxDev *boxes, const double *U, cons
                           double *lamU, int64_t ncell, cudaStream_t s);
 
 // resident blocks per SM of each kernel (for persistent grid sizing)
-int transport_occupancy(bool fp64, bool strict, int variant = 0);
+int transport_occupancy(bool fp64, bool strict, int variant = 0, int flux = RTD_FLUX_GLF);
 int chem_occupancy(bool fp64, bool strict, int G);
 
 }  // namespace rtl

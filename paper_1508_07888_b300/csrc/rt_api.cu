@@ -46,6 +46,8 @@ struct rt_handle {
     rtd::DiagPart *d_gpart = nullptr;        // per-group partials
     unsigned *d_gdone = nullptr;             // per-group item counters
     double *d_rtab = nullptr;                // rate table (null: fits evaluated directly)
+    double *d_hll_d = nullptr;               // HLL wave speeds (FP64, FP32 copies)
+    float *d_hll_f = nullptr;
     double *d_lastdiag = nullptr;
     rtd::Ctl *d_ctl = nullptr;
     rtd::Ctl *h_ctl = nullptr;               // pinned mirror
@@ -105,6 +107,8 @@ static void release(rt_handle *h)
     cudaFree(h->d_done);
     cudaFree(h->d_gpart);
     cudaFree(h->d_gdone);
+    cudaFree(h->d_hll_d);
+    cudaFree(h->d_hll_f);
     cudaFree(h->d_fines);
     for (auto q : h->d_fparent) cudaFree(q);
     cudaFree(h->d_rtab);
@@ -140,6 +144,8 @@ static int check_params(const rt_params *p)
     if (p->precision < RT_PREC_SPLIT || p->precision > RT_PREC_FP64_STRICT)
         return fail(nullptr, RT_ERR_ARG, "unknown precision %d", p->precision);
     if (p->tune < 0) return fail(nullptr, RT_ERR_ARG, "tune must be >= 0");
+    if (p->flux != RT_FLUX_GLF && p->flux != RT_FLUX_HLL)
+        return fail(nullptr, RT_ERR_ARG, "unknown flux %d", p->flux);
     for (int f = 0; f < 6; f++)
         if (p->bc[f] < RT_BC_PERIODIC || p->bc[f] > RT_BC_REFLECTIVE)
             return fail(nullptr, RT_ERR_ARG, "bc[%d]=%d unknown", f, p->bc[f]);
@@ -397,6 +403,21 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                         h->ph.rtab = h->d_rtab;
                     }
                 }
+                h->ph.flux = p->flux;
+                if (p->flux == RT_FLUX_HLL) {           // wave-speed table, FP64 and FP32 copies
+                    const int nt = (RTD_HLL_NF + 1) * (RTD_HLL_NM + 1);
+                    std::vector<double> td(nt);
+                    std::vector<float> tf(nt);
+                    if (rt_hll_speeds(RTD_HLL_NF, RTD_HLL_NM, td.data()) != RT_OK)
+                        return fail(h, RT_ERR_ARG, "HLL speed table");
+                    for (int i = 0; i < nt; i++) tf[i] = (float)td[i];
+                    CU(h, cudaMalloc(&h->d_hll_d, sizeof(double) * nt));
+                    CU(h, cudaMalloc(&h->d_hll_f, sizeof(float) * nt));
+                    CU(h, cudaMemcpy(h->d_hll_d, td.data(), sizeof(double) * nt, cudaMemcpyHostToDevice));
+                    CU(h, cudaMemcpy(h->d_hll_f, tf.data(), sizeof(float) * nt, cudaMemcpyHostToDevice));
+                    h->ph.hll_d = h->d_hll_d;
+                    h->ph.hll_f = h->d_hll_f;
+                }
                 CU(h, cudaMalloc(&h->d_lastdiag, sizeof(double) * RTD_NDIAG * nboxes));
                 CU(h, cudaMemset(h->d_lastdiag, 0, sizeof(double) * RTD_NDIAG * nboxes));
                 CU(h, cudaMalloc(&h->d_ctl, sizeof(rtd::Ctl)));
@@ -408,7 +429,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 int dev = 0, nsm = 1;
                 CU(h, cudaGetDevice(&dev));
                 CU(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-                const int to = rtl::transport_occupancy(fp64, h->strict);
+                const int to = rtl::transport_occupancy(fp64, h->strict, 0, p->flux);
                 const int co = rtl::chem_occupancy(fp64, h->strict, G);
                 // transport: at least 4 planes per block (each run re-reads 2)
                 h->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((titem + 3) / 4, (int64_t)to * nsm));
@@ -421,7 +442,8 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMalloc(&h->d_fines, sizeof(rtd::FineDev) * nboxes));
                 CU(h, cudaMemcpy(h->d_fines, h->fdev.data(), sizeof(rtd::FineDev) * nboxes,
                                  cudaMemcpyHostToDevice));
-                if (!fp64 && p->tune > 0) return tune_transport(h, p->tune, dev, nsm);
+                if (!fp64 && p->flux == RT_FLUX_GLF && p->tune > 0)
+                    return tune_transport(h, p->tune, dev, nsm);
                 return RT_OK;
             }()))
             return bail(rc);
@@ -711,6 +733,7 @@ extern "C" int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, cons
     try {
         if (h->nboxes != 1) return fail(h, RT_ERR_ARG, "rt_adjoint needs a single-box handle");
         if (!h->fp64) return fail(h, RT_ERR_ARG, "rt_adjoint needs an FP64 precision form");
+        if (h->p.flux != RT_FLUX_GLF) return fail(h, RT_ERR_ARG, "rt_adjoint needs the GLF flux");
         for (int f = 0; f < 6; f++)
             if (h->p.bc[f] != RT_BC_PERIODIC)
                 return fail(h, RT_ERR_ARG, "rt_adjoint needs periodic boundaries");
@@ -897,7 +920,7 @@ extern "C" int rt_query(rt_handle *h, rt_stats *st)
         st->kernel_ms[j] = h->kernel_ms[j];
         st->kernel_launches[j] = h->kernel_launches[j];
     }
-    const int v = h->fp64 ? 0 : h->tvariant;
+    const int v = (h->fp64 || h->p.flux != RT_FLUX_GLF) ? 0 : h->tvariant;
     st->tile_x = rtl::kTileX[v];
     st->tile_y = rtl::kTileY[v];
     st->transport_grid = h->tgrid;

@@ -25,6 +25,12 @@
 
 #define RTD_MAXCYC 1000000   // sub-cycles per cell and step before giving up
 
+// intercell flux (rt_flux) and the HLL wave-speed table size (rt_hll_speeds)
+#define RTD_FLUX_GLF 0
+#define RTD_FLUX_HLL 1
+#define RTD_HLL_NF 64
+#define RTD_HLL_NM 64
+
 // rate tables: piecewise polynomials in T.  T in [2^E0, 2^E1) falls in
 // interval j = 2^SUB (e - E0) + (top SUB bits of T's mantissa), e = T's binary
 // exponent, so the index and the local variable t in [-1, 1) come from T's
@@ -57,6 +63,9 @@ struct Phys {
     double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250
     double ln2THI;                // ln(2 T_HI)
     const double *rtab;           // rate table [RTD_TAB_NINT][RTD_TAB_NF][RTD_TAB_NC] or null
+    int flux;                     // RTD_FLUX_GLF / RTD_FLUX_HLL
+    const float *hll_f;           // HLL wave speeds [RTD_HLL_NF + 1][RTD_HLL_NM + 1], FP32 copy
+    const double *hll_d;          // the same in FP64
     int bc[6];                    // -x,+x,-y,+y,-z,+z
 };
 

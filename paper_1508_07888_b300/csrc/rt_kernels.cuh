@@ -220,6 +220,75 @@ __device__ __forceinline__ void glf(const V4<R> &uL, const R PL[6], const V4<R> 
     Phi[3] = R(0.5) * ((PL[pidx(d, 2)] + PR[pidx(d, 2)]) - (uR.w - uL.w));
 }
 
+// HLL signal speeds (units of c) of state u along the three axes from the
+// wave-speed table (rt_hll_speeds: lambda_max at f = 1 - (i/NF)^2,
+// mu = -1 + 2j/NM), interpolated bilinearly in (z = sqrt(1 - f), mu), and
+// lambda_min(f, mu) = -lambda_max(f, -mu); f = |F|/N clamped to 1, mu =
+// F_d/|F|; N <= 0 or F = 0 take f = 0 (isotropic speeds).
+template <typename R>
+__device__ __forceinline__ R hll_lookup(const R *tab, R z, R mu)
+{
+    const R x = z * R(RTD_HLL_NF), y = (mu + R(1)) * R(0.5) * R(RTD_HLL_NM);
+    int i = (int)x, j = (int)y;
+    i = i > RTD_HLL_NF - 1 ? RTD_HLL_NF - 1 : (i < 0 ? 0 : i);
+    j = j > RTD_HLL_NM - 1 ? RTD_HLL_NM - 1 : (j < 0 ? 0 : j);
+    const R tx = x - R(i), ty = y - R(j);
+    const R *t0 = tab + i * (RTD_HLL_NM + 1) + j, *t1 = t0 + (RTD_HLL_NM + 1);
+    const R v00 = t0[0], v01 = t0[1], v10 = t1[0], v11 = t1[1];
+    return (v00 * (R(1) - tx) + v10 * tx) * (R(1) - ty) + (v01 * (R(1) - tx) + v11 * tx) * ty;
+}
+
+// (f, z) of a state; the caller takes mu = F_d / Fn along each axis
+template <typename R, bool STRICT>
+__device__ __forceinline__ void hll_fz(const V4<R> &u, R &Fn, R &z)
+{
+    R f = R(0);
+    Fn = R(0);
+    if (u.x > R(0)) {
+        Fn = rsqrt_(u.y * u.y + u.z * u.z + u.w * u.w);
+        if (Fn > R(0)) {
+            f = Fn / u.x;
+            if (f > R(1)) f = R(1);
+        }
+    }
+    z = rsqrt_(R(1) - f);
+}
+
+template <typename R, int d>
+__device__ __forceinline__ void hll_speed(const R *tab, const V4<R> &u, R Fn, R z, R &smin, R &smax)
+{
+    const R mu = Fn > R(0) ? comp(u, 1 + d) / Fn : R(0);
+    smax = hll_lookup(tab, z, mu);
+    smin = -hll_lookup(tab, z, -mu);
+}
+
+// HLL flux along axis d between (uL, PL) with speeds [aL, bL] and (uR, PR)
+// with speeds [aR, bR]: Phi = (l+ G_L - l- G_R + l+ l- (U_R - U_L))/(l+ - l-),
+// l+ = max(0, bL, bR), l- = min(0, aL, aR); when no wave crosses the face
+// (l+ = l- = 0: beams along it on both sides, whose fluxes vanish) the mean
+// of the two fluxes
+template <typename R, bool STRICT, int d>
+__device__ __forceinline__ void hll(const V4<R> &uL, const R PL[6], R aL, R bL, const V4<R> &uR,
+                                    const R PR[6], R aR, R bR, R Phi[4])
+{
+    R lp = bL > bR ? bL : bR, lm = aL < aR ? aL : aR;
+    if (lp < R(0)) lp = R(0);
+    if (lm > R(0)) lm = R(0);
+    const R GL[4] = {comp(uL, 1 + d), PL[pidx(d, 0)], PL[pidx(d, 1)], PL[pidx(d, 2)]};
+    const R GR[4] = {comp(uR, 1 + d), PR[pidx(d, 0)], PR[pidx(d, 1)], PR[pidx(d, 2)]};
+    if (!(lp - lm > R(0))) {
+#pragma unroll
+        for (int m = 0; m < 4; m++) Phi[m] = R(0.5) * (GL[m] + GR[m]);
+        return;
+    }
+    const R den = lp - lm, ll = lp * lm, rden = R(1) / den;
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const R num = lp * GL[m] - lm * GR[m] + ll * (comp(uR, m) - comp(uL, m));
+        Phi[m] = STRICT ? num / den : num * rden;
+    }
+}
+
 // ghost state beyond a box face (Sec. 4.2): transmissive copies the cell,
 // reflective copies it with the normal flux component inverted
 template <typename R>
@@ -274,14 +343,20 @@ __device__ __forceinline__ void cp_cell(V4<R> *dst, const V4<R> *src)
 constexpr int TP_STAGES = 5;
 constexpr int TP_W = RTD_TX + 2, TP_H = RTD_TY + 2;
 
+template <typename R, int FLUX>
+struct TransportSmem {                 // HLL: also the x/y signal speeds of two planes
+    V4<R> U[TP_STAGES][TP_H][TP_W];
+    R P[2][6][TP_H][TP_W];
+    R Sp[2][4][TP_H][TP_W];            // xmin, xmax, ymin, ymax
+};
 template <typename R>
-struct TransportSmem {
+struct TransportSmem<R, RTD_FLUX_GLF> {
     V4<R> U[TP_STAGES][TP_H][TP_W];
     R P[2][6][TP_H][TP_W];
 };
 
-template <typename R>
-constexpr size_t transport_smem_bytes() { return sizeof(TransportSmem<R>); }
+template <typename R, int FLUX = RTD_FLUX_GLF>
+constexpr size_t transport_smem_bytes() { return sizeof(TransportSmem<R, FLUX>); }
 
 // Work is counted in plane units: (box, group, y-tile, x-tile, z), z
 // fastest.  Block b of a grid of n takes the units [b U/n, (b+1) U/n) and
@@ -308,14 +383,18 @@ __device__ __forceinline__ int find_box_unit(const BoxDev *boxes, int nboxes, in
     return lo;
 }
 
-template <typename R, bool STRICT>
+template <typename R, bool STRICT, int FLUX>
 __global__ void __launch_bounds__(RTD_TX *RTD_TY)
 k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*unused*/, Phys ph,
             Ctl *ctl)
 {
     constexpr int TX = RTD_TX, TY = RTD_TY, S = TP_STAGES;
+    constexpr bool HLL = FLUX == RTD_FLUX_HLL;
     extern __shared__ __align__(16) unsigned char tp_smem_raw[];
-    TransportSmem<R> &sm = *reinterpret_cast<TransportSmem<R> *>(tp_smem_raw);
+    TransportSmem<R, FLUX> &sm = *reinterpret_cast<TransportSmem<R, FLUX> *>(tp_smem_raw);
+    const R *htab = nullptr;
+    if (HLL) htab = reinterpret_cast<const R *>(sizeof(R) == 4 ? (const void *)ph.hll_f
+                                                                : (const void *)ph.hll_d);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
@@ -407,6 +486,16 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                 closure<R, STRICT>(un, Pn);
 #pragma unroll
                 for (int k = 0; k < 6; k++) sm.P[pslot][k][ty + 1][tx + 1] = Pn[k];
+                if constexpr (HLL) {
+                    R Fn, zz, a, b;
+                    hll_fz<R, STRICT>(un, Fn, zz);
+                    hll_speed<R, 0>(htab, un, Fn, zz, a, b);
+                    sm.Sp[pslot][0][ty + 1][tx + 1] = a;
+                    sm.Sp[pslot][1][ty + 1][tx + 1] = b;
+                    hll_speed<R, 1>(htab, un, Fn, zz, a, b);
+                    sm.Sp[pslot][2][ty + 1][tx + 1] = a;
+                    sm.Sp[pslot][3][ty + 1][tx + 1] = b;
+                }
             }
             if (hx >= 0) {
                 V4<R> &h = sm.U[slot][hy][hx];
@@ -417,6 +506,16 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                 closure<R, STRICT>(h, Ph);
 #pragma unroll
                 for (int k = 0; k < 6; k++) sm.P[pslot][k][hy][hx] = Ph[k];
+                if constexpr (HLL) {
+                    R Fn, zz, a, b;
+                    hll_fz<R, STRICT>(h, Fn, zz);
+                    hll_speed<R, 0>(htab, h, Fn, zz, a, b);
+                    sm.Sp[pslot][0][hy][hx] = a;
+                    sm.Sp[pslot][1][hy][hx] = b;
+                    hll_speed<R, 1>(htab, h, Fn, zz, a, b);
+                    sm.Sp[pslot][2][hy][hx] = a;
+                    sm.Sp[pslot][3][hy][hx] = b;
+                }
             }
             if (q == 0 || !act) continue;
             // update plane c = q - 1 (z = z0 + q - 2) unless c is the ghost plane 0
@@ -426,7 +525,16 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
 #pragma unroll
             for (int k = 0; k < 6; k++) Pc[k] = sm.P[cp][k][ty + 1][tx + 1];
             R Fzp[4];
-            glf<R, 2>(uc, Pc, un, Pn, Fzp);
+            if constexpr (HLL) {
+                R Fc, zc_, Fq, zq, a0, b0, a1, b1;
+                hll_fz<R, STRICT>(uc, Fc, zc_);
+                hll_fz<R, STRICT>(un, Fq, zq);
+                hll_speed<R, 2>(htab, uc, Fc, zc_, a0, b0);
+                hll_speed<R, 2>(htab, un, Fq, zq, a1, b1);
+                hll<R, STRICT, 2>(uc, Pc, a0, b0, un, Pn, a1, b1, Fzp);
+            } else {
+                glf<R, 2>(uc, Pc, un, Pn, Fzp);
+            }
             if (c >= 1) {
                 R Pl[6], Pr[6], Pd[6], Pu[6];
 #pragma unroll
@@ -439,10 +547,23 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                 const V4<R> ul = sm.U[cs][ty + 1][tx], ur = sm.U[cs][ty + 1][tx + 2];
                 const V4<R> ud = sm.U[cs][ty][tx + 1], uu = sm.U[cs][ty + 2][tx + 1];
                 R Fxm[4], Fxp[4], Fym[4], Fyp[4];
-                glf<R, 0>(ul, Pl, uc, Pc, Fxm);
-                glf<R, 0>(uc, Pc, ur, Pr, Fxp);
-                glf<R, 1>(ud, Pd, uc, Pc, Fym);
-                glf<R, 1>(uc, Pc, uu, Pu, Fyp);
+                if constexpr (HLL) {
+                    const R cxa = sm.Sp[cp][0][ty + 1][tx + 1], cxb = sm.Sp[cp][1][ty + 1][tx + 1];
+                    const R cya = sm.Sp[cp][2][ty + 1][tx + 1], cyb = sm.Sp[cp][3][ty + 1][tx + 1];
+                    hll<R, STRICT, 0>(ul, Pl, sm.Sp[cp][0][ty + 1][tx], sm.Sp[cp][1][ty + 1][tx], uc, Pc,
+                                      cxa, cxb, Fxm);
+                    hll<R, STRICT, 0>(uc, Pc, cxa, cxb, ur, Pr, sm.Sp[cp][0][ty + 1][tx + 2],
+                                      sm.Sp[cp][1][ty + 1][tx + 2], Fxp);
+                    hll<R, STRICT, 1>(ud, Pd, sm.Sp[cp][2][ty][tx + 1], sm.Sp[cp][3][ty][tx + 1], uc, Pc,
+                                      cya, cyb, Fym);
+                    hll<R, STRICT, 1>(uc, Pc, cya, cyb, uu, Pu, sm.Sp[cp][2][ty + 2][tx + 1],
+                                      sm.Sp[cp][3][ty + 2][tx + 1], Fyp);
+                } else {
+                    glf<R, 0>(ul, Pl, uc, Pc, Fxm);
+                    glf<R, 0>(uc, Pc, ur, Pr, Fxp);
+                    glf<R, 1>(ud, Pd, uc, Pc, Fym);
+                    glf<R, 1>(uc, Pc, uu, Pu, Fyp);
+                }
                 R o[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) {

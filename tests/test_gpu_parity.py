@@ -226,3 +226,51 @@ def test_tuned_full_step_matches_default():
     for a, b in zip(out[:4], ref[:4]):
         np.testing.assert_array_equal(a, b)
     assert st.tile_x * st.tile_y == 256 and st.chem_grid > 0
+
+
+@pytest.mark.parametrize("shape", [(7, 5, 3), (9, 33, 17), (33, 9, 40)])
+@pytest.mark.parametrize("bc", BCS)
+def test_hll_transport_parity(shape, bc):
+    """The HLL flux (rt_params.flux = 1): three pure transport steps against
+    the oracle's HLL transport.  The two sides build their wave-speed tables
+    independently (agreeing to ~1e-12), which bounds the FP64 agreement."""
+    G = 3
+    w, st = _empty_workload(shape, G, bc, seed=sum(shape) * 3 + 1)
+    to, tp = tables(w)
+    zero = [0.0] * G
+    ora = run_oracle(w, 3, to, st, sigN=zero, flux=O.FLUX_HLL)[0]
+    for prec in ("strict", "fp64", "split"):
+        gpu = run_gpu(w, 3, prec, tp, st, sigN=zero, flux=1)[0][0]
+        assert gpu[4] == B.RT_OK
+        U, Uo = gpu[0], ora[0]
+        scale = np.max(np.abs(Uo[..., 0]))
+        err = np.max(np.abs(U - Uo)) / scale
+        assert err <= (2e-6 if prec == "split" else 1e-10), (prec, err)
+
+
+def test_hll_full_step_parity_and_sharper_than_glf():
+    """Sources, absorption and chemistry with the HLL flux: FP64 against the
+    oracle <= 1e-9; the run differs from the GLF run."""
+    w = _small_reion()
+    ora = run_oracle(w, 30, flux=O.FLUX_HLL)[0]
+    (gpu,), st = run_gpu(w, 30, "fp64", flux=1)
+    assert gpu[4] == B.RT_OK
+    err = field_errors(gpu, ora, 3)
+    assert max(err.values()) <= 1e-9, err
+    assert st.realizability_clamps == 0
+    (glf,), _ = run_gpu(w, 30, "fp64")
+    assert np.max(np.abs(glf[1] - gpu[1])) > 1e-3
+
+
+def test_hll_rejected_where_unsupported():
+    import torch
+    w = _small_reion(n=8, nsrc=1)
+    s = make_solver(w, "fp64", flux=1)
+    st = s.states[0]
+    z = torch.zeros(1, dtype=torch.float64, device="cuda")
+    d = torch.zeros(w.boxes[0].ncell, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.RTError) as e:
+        B.rt_adjoint(s.h, st.U.data_ptr(), st.xHI.data_ptr(), st.T.data_ptr(), 1, 1,
+                     z.data_ptr(), len(w.boxes[0].src_Q), d.data_ptr())
+    assert e.value.code == B.RT_ERR_ARG and "GLF" in str(e.value)
+    s.close()

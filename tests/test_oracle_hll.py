@@ -175,3 +175,13 @@ def test_narrow_beam_spreads_less_than_with_glf():
         y = np.arange(shape[1]) - 16
         out[flux] = (w * y * y).sum() / w.sum()
     assert out[O.FLUX_HLL] < 0.5 * out[O.FLUX_GLF], out
+
+
+def test_library_table_matches_the_oracle():
+    """The library's wave-speed table (its own Jacobian by forward-mode
+    differentiation, the decoupled transverse mode taken out, Newton on the
+    remaining cubic) against the oracle's (its Jacobian, numpy eigenvalues):
+    two independent computations of the same numbers (no GPU needed)."""
+    from paper_1508_07888_b300 import binding as B
+    np.testing.assert_allclose(B.rt_hll_speeds(64, 64), O.hll_speed_table(64, 64), rtol=0,
+                               atol=2e-12)

@@ -24,7 +24,7 @@ import numpy as np
 from . import build as _build
 
 MAXG = 4
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 0, 1, 2, 3
 ERR_NONFINITE, ERR_SUBCYCLE = 1, 4
 NDIAG = 5
 
@@ -51,6 +51,7 @@ class _Params(C.Structure):
         ("hll", C.POINTER(C.c_double)),
         ("hll_nf", C.c_int),
         ("hll_nm", C.c_int),
+        ("inflow", (C.c_double * MAXG) * 6),
     ]
 
 FLUX_GLF, FLUX_HLL = 0, 1
@@ -77,6 +78,7 @@ class Params:
     flux: int = FLUX_GLF
     hll_nf: int = 64                # HLL speed table nodes in f (0..1) and mu (-1..1)
     hll_nm: int = 64
+    inflow: Sequence = ()           # bc 3: [face] -> stored N^ per group of the incoming beam
 
     @property
     def G(self) -> int:
@@ -101,6 +103,9 @@ class Params:
             p.bc[k] = int(self.bc[k])
         p.max_halvings = int(self.max_halvings)
         p.flux = int(self.flux)
+        for f, row in enumerate(self.inflow):
+            for g, v in enumerate(row):
+                p.inflow[f][g] = float(v)
         if self.flux == FLUX_HLL:
             tab = hll_speed_table(self.hll_nf, self.hll_nm)
             p.hll = tab.ctypes.data_as(C.POINTER(C.c_double))
@@ -366,6 +371,12 @@ def flux_jacobian(d: int, U4) -> np.ndarray:
     J = np.zeros((4, 4))
     lib().orc_flux_jacobian(d, _ptr(U), _ptr(J))
     return J
+
+
+def inflow_density(photon_flux: float, frac, c: float, nunit: float) -> np.ndarray:
+    """Stored density N^ per group of an incoming beam (F = c N) carrying
+    photon_flux photons/cm^2/s split over the groups by frac."""
+    return np.asarray(frac, dtype=np.float64) * photon_flux / (c * nunit)
 
 
 def flux_jacobian_fmu(f: float, mu: float) -> np.ndarray:

@@ -64,6 +64,9 @@
  *      Harten-Lax-van Leer flux with the extreme eigenvalues of the M1 flux
  *      Jacobian as wave speeds, tabulated in (f, mu) and interpolated
  *      bilinearly (see face_flux).
+ *   R12 inflow boundary (the clump test of Sec. 6.5 feeds a photon flux in
+ *      through the x = 0 face): the ghost state is a beam, F = c N along the
+ *      inward normal, whose photon number flux c N is the given one.
  */
 #include <math.h>
 #include <stdint.h>
@@ -112,6 +115,8 @@ typedef struct {
     const double *hll;           /* HLL: lambda_max at f_i = 1 - (i/hll_nf)^2, mu_j = -1 + 2j/hll_nm,
                                     [hll_nf + 1][hll_nm + 1], row-major */
     int    hll_nf, hll_nm;
+    double inflow[6][ORC_MAXG];  /* bc 3 (inflow, R12): stored photon density N^ of the
+                                    incoming beam per face and group */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -279,11 +284,13 @@ void orc_face_flux(const orc_params *p, int d, const double *L, const double *R,
  * closure's smooth branch (f <= 1; also at f = 1), for the HLL speed table */
 void orc_flux_jacobian_fmu(double f, double mu, double J[4][4]);
 
-/* neighbour state of cell (x,y,z) along axis d, side = -1 or +1, with the
- * global boundary conditions of Sec. 4.2: periodic by default; transmissive
- * copies the cell itself; reflective copies it and inverts the normal flux. */
+/* neighbour state of cell (x,y,z) of group g along axis d, side = -1 or +1,
+ * with the global boundary conditions of Sec. 4.2: periodic by default;
+ * transmissive copies the cell itself; reflective copies it and inverts the
+ * normal flux; inflow (R12) is a beam of the face's given density moving
+ * into the box along the normal (F = c N). */
 static void neighbour(const orc_params *p, const double *Ug, int nx, int ny, int nz,
-                      int x, int y, int z, int d, int side, double *out)
+                      int x, int y, int z, int d, int side, int g, double *out)
 {
     int c[3] = {x, y, z};
     int n[3] = {nx, ny, nz};
@@ -299,6 +306,13 @@ static void neighbour(const orc_params *p, const double *Ug, int nx, int ny, int
         c[d] = (c[d] + n[d]) % n[d];
         const double *s = Ug + 4 * (((size_t)c[2] * ny + c[1]) * nx + c[0]);
         memcpy(out, s, 4 * sizeof(double));
+        return;
+    }
+    if (bc == 3) {
+        double N = p->inflow[face][g];
+        out[0] = N;
+        out[1] = out[2] = out[3] = 0.0;
+        out[1 + d] = side < 0 ? N : -N;
         return;
     }
     const double *s = Ug + 4 * (((size_t)z * ny + y) * nx + x);
@@ -357,7 +371,7 @@ void orc_transport(const orc_params *p, int nx, int ny, int nz, double lam,
                                 memcpy(Us[side], Ug + 4 * nid, 4 * sizeof(double));
                                 flux_from(d, Us[side], P + 6 * nid, Gs[side]);
                             } else {
-                                neighbour(p, Ug, nx, ny, nz, x, y, z, d, sgn, Us[side]);
+                                neighbour(p, Ug, nx, ny, nz, x, y, z, d, sgn, g, Us[side]);
                                 orc_closure(Us[side], Pg, NULL, NULL);
                                 flux_from(d, Us[side], Pg, Gs[side]);
                             }
@@ -394,7 +408,7 @@ void orc_transport_cells(const orc_params *p, int nx, int ny, int nz, double lam
             double Gc[4], Us[2][4], Ps[6], Gs[2][4];
             flux_from(d, Uc, Pc, Gc);
             for (int side = 0; side < 2; side++) {
-                neighbour(p, Ug, nx, ny, nz, x, y, z, d, side ? +1 : -1, Us[side]);
+                neighbour(p, Ug, nx, ny, nz, x, y, z, d, side ? +1 : -1, g, Us[side]);
                 orc_closure(Us[side], Ps, NULL, NULL);
                 flux_from(d, Us[side], Ps, Gs[side]);
             }

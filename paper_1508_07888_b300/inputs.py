@@ -37,7 +37,7 @@ GROUPS_2 = (13.6, 24.6, 1000.0)
 GROUPS_1 = (13.6, 1000.0)
 ALPHA_B_1E4 = 2.59e-13           # cm^3/s, case-B recombination at 1e4 K (textbook)
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 0, 1, 2, 3
 
 
 def f32(a):
@@ -91,6 +91,7 @@ class Box:
     xHI0: float = 1.0 - 1.2e-3
     T0: float = 100.0
     dx: float = DX_REF
+    T_field: np.ndarray | None = None   # initial temperature per cell (overrides T0)
 
     @property
     def shape(self):
@@ -104,7 +105,7 @@ class Box:
         nz, ny, nx = self.shape
         U = np.zeros((ngroups, nz, ny, nx, 4))
         xHI = np.full(self.shape, self.xHI0)
-        T = np.full(self.shape, self.T0)
+        T = np.full(self.shape, self.T0) if self.T_field is None else np.array(self.T_field, dtype=np.float64)
         return U, xHI, T
 
 
@@ -126,6 +127,7 @@ class Workload:
     beta: float = 0.0
     bc: list = field(default_factory=lambda: [BC_PERIODIC] * 6)
     cfl: float = 0.9
+    inflow: list = field(default_factory=lambda: [0.0] * 6)   # photons/cm^2/s per face (BC_INFLOW)
 
     @property
     def ngroups(self) -> int:
@@ -158,6 +160,28 @@ def stromgren(n: int = 32, steps: int = 100, c_frac: float = 0.1) -> Workload:
                     c_frac=c_frac, steps=steps, ots=True, isothermal=True,
                     rates_const=True, alphaA=ALPHA_B_1E4, alphaB=ALPHA_B_1E4, beta=0.0,
                     bc=[BC_REFLECTIVE, BC_TRANSMISSIVE] * 3)
+
+
+def shadow(n: int = 64, steps: int = 3000, c_frac: float = 1.0) -> Workload:
+    """The clump test of Sec. 6.5 with static gas (radiative transfer and
+    thermochemistry only): a 6.6 kpc box, background 200 atoms/m^3 at
+    8000 K, a clump of radius 0.8 kpc centred on (5.4, 3.3, 3.3) kpc with
+    40 000 atoms/m^3 at 100 K, a 1e5 K black-body photon flux of
+    1e10 photons/m^2/s entering through x = 0, transmissive at x = 6.6 kpc,
+    periodic in y and z; 3 groups.  The I-front runs at ~0.17 c in the
+    background gas, so the full c is kept (a reduced c below that speed would
+    hold the front back)."""
+    dx = 6.6 * KPC / n
+    c = (np.arange(n) + 0.5) * dx
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    r2 = (x - 5.4 * KPC) ** 2 + (y - 3.3 * KPC) ** 2 + (z - 3.3 * KPC) ** 2
+    clump = r2 <= (0.8 * KPC) ** 2
+    n0 = f32(np.where(clump, 4e4 * 1e-6, 200.0 * 1e-6))
+    T = np.where(clump, 100.0, 8000.0)
+    box = Box(n0=n0, src_cells=np.zeros(0, dtype=np.int64), src_Q=np.zeros(0), dx=dx, T_field=T)
+    return Workload(name=f"shadow_{n}^3", boxes=[box], edges_eV=GROUPS_3, T_bb=1e5, c_frac=c_frac,
+                    steps=steps, bc=[BC_INFLOW, BC_TRANSMISSIVE] + [BC_PERIODIC] * 4,
+                    inflow=[1e10 * 1e-4, 0.0, 0.0, 0.0, 0.0, 0.0])
 
 
 def reion(n: int = 128, steps: int = 500, nsrc: int = 64, sigma: float = 1.0,

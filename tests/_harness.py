@@ -27,11 +27,15 @@ def tables(w: I.Workload):
     return to, tp
 
 
-def oracle_params(w: I.Workload, table: dict, **over) -> O.Params:
+def oracle_params(w: I.Workload, table: dict, box=None, **over) -> O.Params:
     kw = dict(sigN=table["sigN"], sigE=table["sigE"], Eavg=table["Eavg"], frac=table["frac"],
               c=w.c_red, cfl=w.cfl, ots=w.ots, isothermal=w.isothermal, nsub=w.nsub,
               rates_const=w.rates_const, alphaA=w.alphaA, alphaB=w.alphaB, beta=w.beta,
               bc=list(w.bc))
+    if any(w.inflow):
+        box = box if box is not None else w.boxes[0]
+        kw["inflow"] = [O.inflow_density(w.inflow[f], table["frac"], w.c_red, w.nunit(box))
+                        for f in range(6)]
     kw.update(over)
     return O.Params(**kw)
 
@@ -53,12 +57,12 @@ def gpu_params(w: I.Workload, table: dict, precision: str, **over) -> B.rt_param
 def run_oracle(w: I.Workload, steps: int, table=None, states=None, threads=None, **over):
     """Returns per box: (U, xHI, T, hist, err, nclamp)."""
     table = table if table is not None else tables(w)[0]
-    p = oracle_params(w, table, **over)
     if threads is None:
         threads = min(8, os.cpu_count() or 1)
     O.set_threads(threads)
     out = []
     for bi, box in enumerate(w.boxes):
+        p = oracle_params(w, table, box=box, **over)
         nunit = w.nunit(box)
         U, xHI, T = states[bi] if states is not None else box.initial_state(w.ngroups)
         S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)

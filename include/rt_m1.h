@@ -75,7 +75,10 @@ typedef enum rt_precision {
 typedef enum rt_bc {
     RT_BC_PERIODIC = 0,      /* Sec. 4.2 default */
     RT_BC_TRANSMISSIVE = 1,  /* ghost = copy of the boundary cell */
-    RT_BC_REFLECTIVE = 2     /* ghost = copy with the normal flux component inverted */
+    RT_BC_REFLECTIVE = 2,    /* ghost = copy with the normal flux component inverted */
+    RT_BC_INFLOW = 3         /* ghost = a beam entering the box along the normal, F = c N,
+                                carrying rt_params.inflow[face] photons/cm^2/s split over the
+                                groups by frac (the clump test of Sec. 6.5); x faces only */
 } rt_bc;
 
 typedef enum rt_flux {
@@ -110,6 +113,7 @@ typedef struct rt_params {
                                             process), 2 + k = shape k; ignored by the FP64 forms
                                             and by the HLL flux */
     int    flux;                         /* rt_flux; rt_adjoint and rt_transport_static need GLF */
+    double inflow[6];                    /* photons/cm^2/s entering through each RT_BC_INFLOW face */
 } rt_params;
 
 typedef struct rt_box {

@@ -50,6 +50,7 @@ class rt_params(C.Structure):
         ("precision", C.c_int),
         ("tune", C.c_int),
         ("flux", C.c_int),
+        ("inflow", C.c_double * 6),
     ]
 
 
@@ -246,7 +247,8 @@ def rt_transport_static(p: rt_params, box: rt_box, nsteps: int, stream_ptr: int 
 # ------------------------------------------------------------------ helpers
 def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, isothermal=False,
                 nsub=0, rates_const=False, alphaA=0.0, alphaB=0.0, beta=0.0, bc=(0,) * 6,
-                max_halvings=30, precision=RT_PREC_SPLIT, tune=0, flux=0) -> rt_params:
+                max_halvings=30, precision=RT_PREC_SPLIT, tune=0, flux=0,
+                inflow=(0.0,) * 6) -> rt_params:
     p = rt_params()
     p.ngroups = ngroups
     for i in range(ngroups):
@@ -261,6 +263,8 @@ def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, 
     p.precision = precision
     p.tune = int(tune)
     p.flux = int(flux)
+    for k in range(6):
+        p.inflow[k] = float(inflow[k])
     return p
 
 

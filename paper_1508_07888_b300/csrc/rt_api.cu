@@ -146,9 +146,14 @@ static int check_params(const rt_params *p)
     if (p->tune < 0) return fail(nullptr, RT_ERR_ARG, "tune must be >= 0");
     if (p->flux != RT_FLUX_GLF && p->flux != RT_FLUX_HLL)
         return fail(nullptr, RT_ERR_ARG, "unknown flux %d", p->flux);
-    for (int f = 0; f < 6; f++)
-        if (p->bc[f] < RT_BC_PERIODIC || p->bc[f] > RT_BC_REFLECTIVE)
+    for (int f = 0; f < 6; f++) {
+        if (p->bc[f] < RT_BC_PERIODIC || p->bc[f] > RT_BC_INFLOW)
             return fail(nullptr, RT_ERR_ARG, "bc[%d]=%d unknown", f, p->bc[f]);
+        if (p->bc[f] == RT_BC_INFLOW && f >= 2)
+            return fail(nullptr, RT_ERR_ARG, "inflow boundaries on the x faces only");
+        if (p->bc[f] == RT_BC_INFLOW && !(p->inflow[f] >= 0.0 && std::isfinite(p->inflow[f])))
+            return fail(nullptr, RT_ERR_ARG, "inflow[%d] must be finite and >= 0", f);
+    }
     for (int d = 0; d < 3; d++)
         if ((p->bc[2 * d] == RT_BC_PERIODIC) != (p->bc[2 * d + 1] == RT_BC_PERIODIC))
             return fail(nullptr, RT_ERR_ARG, "axis %d: periodic on one face only", d);
@@ -340,6 +345,9 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
         for (int k = 0; k < 5; k++) ph.lnfit[k] = std::log(fit_scale[k]);
         ph.ln2THI = std::log(2.0 * rtd::T_HI);
         for (int f = 0; f < 6; f++) ph.bc[f] = p->bc[f];
+        for (int f = 0; f < 2; f++)                      // inflow: c N per group, per unit nunit
+            for (int i = 0; i < p->ngroups; i++)
+                ph.inflow_c[f][i] = p->bc[f] == RT_BC_INFLOW ? p->inflow[f] * p->frac[i] / p->c_red : 0.0;
 
         if ((rc = [&]() -> int {
                 CU(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));

@@ -67,6 +67,7 @@ struct Phys {
     const float *hll_f;           // HLL wave speeds [RTD_HLL_NF + 1][RTD_HLL_NM + 1], FP32 copy
     const double *hll_d;          // the same in FP64
     int bc[6];                    // -x,+x,-y,+y,-z,+z
+    double inflow_c[2][RTD_MAXG]; // inflow faces -x, +x: beam density N per group times nunit
 };
 
 // One box (array in device memory, indexed by work items).

@@ -427,14 +427,24 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
         // this thread's halo cell (at most one): smem position (hx, hy),
         // source (sx, sy) inside the box, negated component (0 = none)
         int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0;
+        R hin = R(0);                     // inflow ghost: beam density, sign = direction
+        bool hif = false;                 // the halo cell is an inflow ghost
         {
             int t = tid;
             if (t < nty) {                                   // left column
                 hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1;
-                if (sx < 0) { if (ph.bc[0] == 0) sx = nx - 1; else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; } }
+                if (sx < 0) {
+                    if (ph.bc[0] == 0) sx = nx - 1;
+                    else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; }
+                    if (ph.bc[0] == 3) { hif = true; hin = (R)(ph.inflow_c[0][g] * B.inv_nunit); }
+                }
             } else if ((t -= nty) < nty) {                   // right column
                 hx = ntx + 1; hy = t + 1; sy = y0 + t; sx = x0 + ntx;
-                if (sx >= nx) { if (ph.bc[1] == 0) sx = 0; else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; } }
+                if (sx >= nx) {
+                    if (ph.bc[1] == 0) sx = 0;
+                    else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; }
+                    if (ph.bc[1] == 3) { hif = true; hin = -(R)(ph.inflow_c[1][g] * B.inv_nunit); }
+                }
             } else if ((t -= nty) < ntx) {                   // bottom row
                 hx = t + 1; hy = 0; sx = x0 + t; sy = y0 - 1;
                 if (sy < 0) { if (ph.bc[2] == 0) sy = ny - 1; else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; } }
@@ -460,7 +470,10 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                 const int64_t pl = (int64_t)src_plane(q, zneg) * sxy;
                 const int slot = q % S;
                 if (act) cp_cell(&sm.U[slot][ty + 1][tx + 1], Ug + pl + own_col);
-                if (hx >= 0) cp_cell(&sm.U[slot][hy][hx], Ug + pl + halo_col);
+                if (hx >= 0) {
+                    if (hif) sm.U[slot][hy][hx] = V4<R>{hin < R(0) ? -hin : hin, hin, R(0), R(0)};
+                    else cp_cell(&sm.U[slot][hy][hx], Ug + pl + halo_col);
+                }
             }
             cp_async_commit();
         };
@@ -705,14 +718,24 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         // halo cell of this thread and which half of it the tile needs:
         // 0 = Rx (left column), 1 = Lx (right), 2 = Ry (bottom), 3 = Ly (top)
         int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0, hk = 0;
+        float hin = 0.0f;                 // inflow ghost: beam density, sign = direction
+        bool hif = false;                 // the halo cell is an inflow ghost
         {
             int t = tid;
             if (t < nty) {
                 hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1; hk = 0;
-                if (sx < 0) { if (ph.bc[0] == 0) sx = nx - 1; else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; } }
+                if (sx < 0) {
+                    if (ph.bc[0] == 0) sx = nx - 1;
+                    else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; }
+                    if (ph.bc[0] == 3) { hif = true; hin = (float)(ph.inflow_c[0][g] * B.inv_nunit); }
+                }
             } else if ((t -= nty) < nty) {
                 hx = ntx + 1; hy = t + 1; sy = y0 + t; sx = x0 + ntx; hk = 1;
-                if (sx >= nx) { if (ph.bc[1] == 0) sx = 0; else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; } }
+                if (sx >= nx) {
+                    if (ph.bc[1] == 0) sx = 0;
+                    else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; }
+                    if (ph.bc[1] == 3) { hif = true; hin = -(float)(ph.inflow_c[1][g] * B.inv_nunit); }
+                }
             } else if ((t -= nty) < ntx) {
                 hx = t + 1; hy = 0; sx = x0 + t; sy = y0 - 1; hk = 2;
                 if (sy < 0) { if (ph.bc[2] == 0) sy = ny - 1; else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; } }
@@ -736,7 +759,10 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
                 else if (zz >= nz) zz = ph.bc[5] == 0 ? 0 : nz - 1;
                 const int64_t pl = (int64_t)zz * sxy;
                 if (act) cp_async16(&sm.U[slot_i][ty + 1][tx + 1], gown + pl);
-                if (hx >= 0) cp_async16(&sm.U[slot_i][hy][hx], ghalo + pl);
+                if (hx >= 0) {
+                    if (hif) sm.U[slot_i][hy][hx] = V4<float>{fabsf(hin), hin, 0.0f, 0.0f};
+                    else cp_async16(&sm.U[slot_i][hy][hx], ghalo + pl);
+                }
             }
             cp_async_commit();
             zi++;

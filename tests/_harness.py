@@ -43,7 +43,7 @@ def oracle_params(w: I.Workload, table: dict, box=None, **over) -> O.Params:
 def gpu_params(w: I.Workload, table: dict, precision: str, **over) -> B.rt_params:
     kw = dict(cfl=w.cfl, ots=w.ots, isothermal=w.isothermal, nsub=w.nsub,
               rates_const=w.rates_const, alphaA=w.alphaA, alphaB=w.alphaB, beta=w.beta,
-              bc=w.bc, precision=PREC[precision])
+              bc=w.bc, precision=PREC[precision], inflow=w.inflow)
     for k in ("sigN", "sigE", "Eavg", "frac"):
         if k in over:
             table = dict(table, **{k: over.pop(k)})

@@ -63,7 +63,8 @@
  *   R11 HLL flux (the paper plans it, Sec. 2.2.3, without formulas): the
  *      Harten-Lax-van Leer flux with the extreme eigenvalues of the M1 flux
  *      Jacobian as wave speeds, tabulated in (f, mu) and interpolated
- *      bilinearly (see face_flux).
+ *      bilinearly (see face_flux), and |F| <= cN enforced after each HLL
+ *      transport step (see hll_limit).
  *   R12 inflow boundary (the clump test of Sec. 6.5 feeds a photon flux in
  *      through the x = 0 face): the ghost state is a beam, F = c N along the
  *      inward normal, whose photon number flux c N is the given one.
@@ -264,6 +265,22 @@ static void face_flux(const orc_params *p, int d, const double *UL, const double
         Phi[m] = (lp * GL[m] - lm * GR[m] + lp * lm * (UR[m] - UL[m])) / (lp - lm);
 }
 
+/* After an HLL transport step the flux is limited to |F| <= cN, F scaled
+ * down where it exceeds it (R11).  With the speeds lambda = mu of f = 1 the
+ * HLL update amplifies the excess |F| - cN that rounding leaves in beam
+ * cells (e' = (1 + lam) e - lam e_left along the beam), so without the
+ * limiter beams blow up; GLF's unit speeds damp the same mode. */
+static void hll_limit(double *U)
+{
+    double F = sqrt(U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
+    if (F > U[0]) {
+        double r = U[0] > 0.0 ? U[0] / F : 0.0;
+        U[1] *= r;
+        U[2] *= r;
+        U[3] *= r;
+    }
+}
+
 void orc_hll_speeds(const orc_params *p, int d, const double *U, double *lmin, double *lmax)
 {
     hll_speeds(p, d, U, lmin, lmax);
@@ -384,6 +401,7 @@ void orc_transport(const orc_params *p, int nx, int ny, int nz, double lam,
                     }
                     for (int m = 0; m < 4; m++)
                         Og[4 * id + m] = Uc[m] - lam * ((diff[0][m] + diff[1][m]) + diff[2][m]);
+                    if (p->flux == 1) hll_limit(Og + 4 * id);
                 }
     }
     free(P);
@@ -419,6 +437,7 @@ void orc_transport_cells(const orc_params *p, int nx, int ny, int nz, double lam
         }
         for (int m = 0; m < 4; m++)
             out[4 * k + m] = Uc[m] - lam * ((diff[0][m] + diff[1][m]) + diff[2][m]);
+        if (p->flux == 1) hll_limit(out + 4 * k);
     }
 }
 

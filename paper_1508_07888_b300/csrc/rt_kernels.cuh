@@ -585,6 +585,17 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                     const R dzf = Fzp[m] - Fzm[m];
                     o[m] = comp(uc, m) - lam * ((dxf + dyf) + dzf);
                 }
+                if constexpr (HLL) {
+                    // |F| <= N after an HLL step: the speeds mu of f = 1 would
+                    // amplify the excess that rounding leaves in beam cells
+                    const R Fn = rsqrt_(o[1] * o[1] + o[2] * o[2] + o[3] * o[3]);
+                    if (Fn > o[0]) {
+                        const R r = o[0] > R(0) ? o[0] / Fn : R(0);
+                        o[1] *= r;
+                        o[2] *= r;
+                        o[3] *= r;
+                    }
+                }
                 const int z = z0 + c - 1;
                 st4(Og + (int64_t)z * sxy + own_col, V4<R>{o[0], o[1], o[2], o[3]});
             }

@@ -21,10 +21,10 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("flux", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "strict", "split"])
 def test_small_clump_parity(flux, prec):
-    w = I.shadow(n=24, steps=60)
-    ora = run_oracle(w, 60, flux=flux)[0]
+    w = I.shadow(n=24, steps=150)
+    ora = run_oracle(w, 150, flux=flux)[0]
     assert ora[4] == 0
-    (gpu,), st = run_gpu(w, 60, prec, flux=flux)
+    (gpu,), st = run_gpu(w, 150, prec, flux=flux)
     assert gpu[4] == B.RT_OK
     if prec == "split":
         ex, eT = linf_rel(gpu[1], ora[1]), linf_rel(gpu[2], ora[2])

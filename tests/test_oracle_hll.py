@@ -185,3 +185,27 @@ def test_library_table_matches_the_oracle():
     from paper_1508_07888_b300 import binding as B
     np.testing.assert_allclose(B.rt_hll_speeds(64, 64), O.hll_speed_table(64, 64), rtol=0,
                                atol=2e-12)
+
+
+def test_beam_stays_realizable_under_rounding_noise():
+    """Rounding leaves beam cells with |F| slightly above cN; with the speeds
+    mu of f = 1 the HLL update would amplify that excess step after step.
+    With the limiter a beam entering an absorbing clump stays realizable
+    when every step's state is perturbed at the 1e-13 level."""
+    w = I.shadow(n=12, steps=60)
+    box = w.boxes[0]
+    t = {k: I.f32(v) for k, v in O.group_table(w.edges_eV, w.T_bb).items()}
+    nunit = w.nunit(box)
+    p = O.Params(sigN=t["sigN"], sigE=t["sigE"], Eavg=t["Eavg"], frac=t["frac"], c=w.c_red,
+                 bc=list(w.bc), flux=O.FLUX_HLL,
+                 inflow=[O.inflow_density(w.inflow[f], t["frac"], w.c_red, nunit)
+                         for f in range(6)])
+    U, x, T = box.initial_state(3)
+    rng = np.random.default_rng(1)
+    for _ in range(60):
+        r = O.run(p, U, x, T, box.n0, box.dx, nunit, 1, None)
+        assert r.err == 0
+        U = r.U * (1 + 1e-13 * rng.standard_normal(r.U.shape))
+        x, T = r.xHI, r.T
+        N, F = U[..., 0], np.linalg.norm(U[..., 1:], axis=-1)
+        assert np.all(F <= N * (1 + 1e-12) + 1e-300)

@@ -151,11 +151,18 @@ __device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
 // fixes the order), chi = (3+4f^2)/(5+2 sqrt(4-3f^2)), f = |Fhat|/Nhat
 // clamped to 1, evaluated as (3chi-1)/2 = f^2 g, g = (6 + 3/(2+s))/(5+2s),
 // s = sqrt(4-3f^2).  P = (xx, xy, xz, yy, yz, zz).
+// smallest N the closure and the HLL speeds resolve: FP32 subnormals (below
+// ~1.2e-38) would overflow 1/N, so the FP32 path treats N <= 1e-37 as N = 0
+// (P = 0, isotropic speeds); FP64 uses N > 0 as the oracle does
+template <typename R> __device__ __forceinline__ R closure_nmin();
+template <> __device__ __forceinline__ float closure_nmin<float>() { return 1e-37f; }
+template <> __device__ __forceinline__ double closure_nmin<double>() { return 0.0; }
+
 template <typename R, bool STRICT>
 __device__ __forceinline__ void closure(const V4<R> &u, R P[6])
 {
     const R N = u.x;
-    if (N > R(0)) {
+    if (N > closure_nmin<R>()) {
         R ux, uy, uz;
         if (STRICT) {
             ux = u.y / N; uy = u.z / N; uz = u.w / N;
@@ -244,7 +251,7 @@ __device__ __forceinline__ void hll_fz(const V4<R> &u, R &Fn, R &z)
 {
     R f = R(0);
     Fn = R(0);
-    if (u.x > R(0)) {
+    if (u.x > closure_nmin<R>()) {
         Fn = rsqrt_(u.y * u.y + u.z * u.z + u.w * u.w);
         if (Fn > R(0)) {
             f = Fn / u.x;

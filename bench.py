@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-crta", action="store_true")
     ap.add_argument("--no-hll", action="store_true")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="rt_params.tune of the split form: 1 = time the transport's launch "
+                         "shapes at create, 2 + k = shape k (profiling runs fix the shape)")
     return ap.parse_args()
 
 
@@ -167,9 +170,13 @@ def group_table(w):
     return {k: I.f32(v) for k, v in t.items()}
 
 
-def make_params(w, precision, tune=1):
+TUNE = 1
+
+
+def make_params(w, precision, tune=None):
     """tune = 1: the library times the transport's launch shapes at create
     (outside every timed region) and keeps the fastest."""
+    tune = TUNE if tune is None else tune
     from paper_1508_07888_b300 import binding as B
     return B.make_params(w.ngroups, group_table(w), w.c_red, cfl=w.cfl, ots=w.ots,
                          isothermal=w.isothermal, nsub=w.nsub, bc=w.bc, precision=precision,
@@ -504,7 +511,9 @@ def chem_flops_per_subcycle(G: int, ots: bool) -> float:
 
 
 def main():
+    global TUNE
     args = parse()
+    TUNE = args.tune
     ws, rank, local = dist_setup(args)
     w = workload()
     box = w.boxes[0]

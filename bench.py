@@ -507,7 +507,7 @@ def peaks():
 def chem_flops_per_subcycle(G: int, ots: bool) -> float:
     """Algorithmic FP64 flops of one accepted chemistry sub-cycle (a5-a8 and
     the rate fits), counted from the formulas as written."""
-    return 22.0 * G + 182.0 - (27.0 if ots else 0.0)
+    return 22.0 * G + 111.0 - (14.0 if ots else 0.0)
 
 
 def main():
@@ -606,13 +606,13 @@ def main():
               "unit": "GB/s", "frac": t_ach / hbm_peak,
               "traffic": traffic.get("transport"),
               "algorithmic_bytes_per_launch": t_bytes, "peak_note": peak_note}
-    # chemistry: FP64 flops of one accepted sub-cycle, counted from the update
-    # formulas as written (+ - x / each 1, a Horner step 2, exp and log 1):
-    # rates from the table 116 (5 degree-10 polynomials 100, the variable and
-    # the two exp(-c/T) factors 16; 96 with OTS, which skips alpha_A), the
-    # dtau estimate 4 G + 19, the trial 18 G + 47 (+7 for the recombination
-    # photons of group 1 without OTS, in the 47) -> 22 G + 182, against the
-    # FP64 pipe peak: 148 SMs x 2 DFMA/clock x 2 flop x 2032 MHz
+    # chemistry: FP64 flops of one accepted sub-cycle, counted from the
+    # formulas as written (+ - x / each 1; pow, exp, sqrt 1): the rate fits 45
+    # (lambda 1, alpha_A 7, alpha_B 7, recombination + free-free cooling 11,
+    # beta 11, excitation cooling 6, k_C 2; OTS needs no alpha_A), the dtau
+    # estimate 4 G + 19, the trial 18 G + 47 (7 of them the recombination
+    # photons of group 1 without OTS) -> 22 G + 111, against the FP64 pipe
+    # peak: 148 SMs x 2 DFMA/clock x 2 flop x 2032 MHz
     fp64_peak = 148 * 2 * 2 * 2032e6 / 1e12
     c_flops = chem_flops_per_subcycle(G, w.ots) * box.ncell * mean_sub
     c_ach = c_flops / (per_launch["chemistry"] * 1e-3) / 1e12

@@ -160,6 +160,11 @@ def lib():
             "orc_flux_jacobian_fmu": (None, [C.c_double, C.c_double, _dp]),
             "orc_hll_speeds": (None, [PP, C.c_int, _dp, _dp, _dp]),
             "orc_face_flux": (None, [PP, C.c_int, _dp, _dp, _dp]),
+            "orc_advance_a": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_double,
+                                           C.c_double]),
+            "orc_run_cosmo": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                        _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, C.c_double,
+                                        C.c_double, C.c_double, _dp]),
             "orc_transport_adj": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp,
                                             _dp]),
             "orc_adjoint": (C.c_int, [PP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -293,6 +298,39 @@ def run(p: Params, U, xHI, T, n0, dx: float, nunit: float, nsteps: int,
     err = lib().orc_run(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
                         _ptr(T), _ptr(n0), Sp, nsteps, _ptr(hist), C.byref(ncl))
     return RunResult(U, xHI, T, hist, err, ncl.value)
+
+
+@dataclass
+class CosmoResult:
+    run: RunResult
+    a: float          # expansion factor after the run
+
+
+def advance_a(a: float, dt: float, H0: float, Om: float, OL: float) -> float:
+    """a after dt (s) from a: one Runge-Kutta step of da/dt = a H0 sqrt(Om/a^3 + OL)."""
+    return lib().orc_advance_a(a, dt, H0, Om, OL)
+
+
+def run_cosmo(p: Params, U, xHI, T_sc, n0, dx: float, nunit: float, nsteps: int, S,
+              H0: float, Om: float, OL: float, a0: float) -> CosmoResult:
+    """run() in supercomoving units (Sec. 3): U = comoving N^, F^ (units of
+    nunit), T_sc = a^2 T, n0 comoving density, dx comoving cell size; a(t)
+    from a0 by the Friedmann equation.  The history holds no |F|/N maximum
+    (0)."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    xHI = np.array(xHI, dtype=np.float64, order="C", copy=True)
+    T = np.array(T_sc, dtype=np.float64, order="C", copy=True)
+    n0 = np.ascontiguousarray(n0, dtype=np.float64)
+    G, nz, ny, nx, _ = U.shape
+    hist = np.zeros((nsteps, NDIAG))
+    Sp = None
+    if S is not None:
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        Sp = _ptr(S)
+    a = C.c_double(a0)
+    err = lib().orc_run_cosmo(C.byref(p.to_c()), nx, ny, nz, dx, nunit, _ptr(U), _ptr(xHI),
+                              _ptr(T), _ptr(n0), Sp, nsteps, _ptr(hist), H0, Om, OL, C.byref(a))
+    return CosmoResult(RunResult(U, xHI, T, hist, err, 0), a.value)
 
 
 @dataclass

@@ -68,6 +68,7 @@
  *   R12 inflow boundary (the clump test of Sec. 6.5 feeds a photon flux in
  *      through the x = 0 face): the ghost state is a beam, F = c N along the
  *      inward normal, whose photon number flux c N is the given one.
+ *   R13 supercomoving units (Sec. 3) for the radiation path: see section 7.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1265,4 +1266,96 @@ int orc_adjoint(const orc_params *p, int nx, int ny, int nz, double dx, double n
     }
     free(Uk); free(Us); free(xk); free(Tk); free(lU); free(lS); free(lx); free(lT);
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* 7. supercomoving units (Sec. 3; R13)                                 */
+/* ------------------------------------------------------------------ */
+/* R13 The paper transforms to supercomoving variables, N~ = a^3 N r_s^3,
+ * F~ = a^4 r_s^2 t_s F, x~ = x/(a r_s), dt~ = dt/(a^2 t_s) (r_s, t_s the
+ * length and time units), in which the equations keep their standard form.
+ * For the radiation path this makes the transport the usual M1 step with
+ * the light speed c~ = a c t_s / r_s, so at the fixed Courant number the
+ * transport is unchanged; the thermochemistry acts on physical quantities.
+ * The state is stored as
+ *   N^ = a^3 N / nunit,  F^ = a^3 F / (c nunit)  (comoving, units of nunit),
+ *   T~ = a^2 T           (constant under adiabatic expansion of a
+ *                         gamma = 5/3 gas at rest in comoving coordinates),
+ * n0 is the comoving hydrogen density (the physical one at a = 1) and dx
+ * the comoving cell size.  Step k at a_k:
+ *   (1) transport with lam = c dt_com / dx, dt_com = cfl dx / (3 c);
+ *   (2) chemistry of every cell over dt_k = a_k dt_com with N, F, S, n0
+ *       scaled by 1/a_k^3 and T = T~ / a_k^2;
+ *   (3) back to the stored units with a_k^3 and T~ = a_k^2 T; F^ also by
+ *       a_k / a_(k+1), since F^ follows F~ / c~ and c~ grows like a;
+ *   (4) a_(k+1) from a_k over dt_k by the Friedmann equation
+ *       da/dt = a H0 sqrt(Om / a^3 + OL), one classical Runge-Kutta step. */
+static double dadt_cosmo(double a, double H0, double Om, double OL)
+{
+    return a * H0 * sqrt(Om / (a * a * a) + OL);
+}
+
+double orc_advance_a(double a, double dt, double H0, double Om, double OL)
+{
+    double k1 = dadt_cosmo(a, H0, Om, OL);
+    double k2 = dadt_cosmo(a + 0.5 * dt * k1, H0, Om, OL);
+    double k3 = dadt_cosmo(a + 0.5 * dt * k2, H0, Om, OL);
+    double k4 = dadt_cosmo(a + dt * k3, H0, Om, OL);
+    return a + dt * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+}
+
+int orc_run_cosmo(const orc_params *p, int nx, int ny, int nz, double dx, double nunit,
+                  double *U, double *xHI, double *T, const double *n0, const double *S,
+                  int nsteps, double *hist, double H0, double Om, double OL, double *a_io)
+{
+    size_t ncell = (size_t)nx * ny * nz;
+    int G = p->G;
+    double *Us = (double *)malloc(sizeof(double) * 4 * ncell * G);
+    if (!Us) return -1;
+    double dt_com = orc_timestep(p, dx);
+    double lam = p->c * dt_com / dx;
+    double a = *a_io;
+    int err = 0;
+    for (int step = 0; step < nsteps; step++) {
+        double dtk = a * dt_com;
+        double a1 = orc_advance_a(a, dtk, H0, Om, OL);
+        double ia3 = 1.0 / (a * a * a), a3 = a * a * a, a2 = a * a, fr = a / a1;
+        orc_transport(p, nx, ny, nz, lam, U, Us);
+        double cyc_sum = 0.0;
+#pragma omp parallel for num_threads(orc_threads) schedule(dynamic, 256) reduction(|:err) reduction(+:cyc_sum)
+        for (size_t id = 0; id < ncell; id++) {
+            double Uc[4 * ORC_MAXG], Sc[ORC_MAXG];
+            for (int i = 0; i < G; i++) {
+                for (int m = 0; m < 4; m++) Uc[4 * i + m] = Us[4 * (ncell * i + id) + m] * ia3;
+                Sc[i] = S ? S[ncell * i + id] * ia3 : 0.0;
+            }
+            double Tp = T[id] / a2;
+            int ncyc = 0;
+            err |= orc_chem_cell(p, dtk, nunit, n0[id] * ia3, Sc, Uc, &xHI[id], &Tp, &ncyc);
+            for (int i = 0; i < G; i++) {
+                U[4 * (ncell * i + id)] = Uc[4 * i] * a3;
+                for (int m = 1; m < 4; m++) U[4 * (ncell * i + id) + m] = Uc[4 * i + m] * a3 * fr;
+            }
+            T[id] = Tp * a2;
+            cyc_sum += ncyc;
+        }
+        if (hist) {
+            double X = 0.0, ph = 0.0, nion = 0.0;
+            for (size_t id = 0; id < ncell; id++) {
+                X += 1.0 - xHI[id];
+                if (xHI[id] < 0.5) nion += 1.0;
+            }
+            for (size_t k = 0; k < ncell * G; k++) ph += U[4 * k];
+            double *h = hist + 5 * (size_t)step;
+            h[0] = X / (double)ncell;
+            h[1] = ph * nunit * (dx * dx * dx);
+            h[2] = 0.0;
+            h[3] = nion;
+            h[4] = cyc_sum / (double)ncell;
+        }
+        a = a1;
+    }
+    free(Us);
+    *a_io = a;
+    return err;
 }

@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-crta", action="store_true")
     ap.add_argument("--no-hll", action="store_true")
+    ap.add_argument("--no-cosmo", action="store_true")
     ap.add_argument("--tune", type=int, default=1,
                     help="rt_params.tune of the split form: 1 = time the transport's launch "
                          "shapes at create, 2 + k = shape k (profiling runs fix the shape)")
@@ -429,6 +430,37 @@ def hll_run(K=3):
             "chemistry_ms_per_launch": st.kernel_ms[1] / max(st.kernel_launches[1], 1)}
 
 
+def cosmo_run(K=3):
+    """The 128^3 workload in supercomoving units (Sec. 3): a0 = 0.1,
+    H0 = 67.7 km/s/Mpc, omega_m = 0.31, omega_l = 0.69, split form, 500
+    steps per run; throughput against the static run shows the cost of the
+    per-step scalings."""
+    import torch
+    from paper_1508_07888_b300 import binding as B
+    w = workload()
+    r = DeviceRun(w, B.RT_PREC_SPLIT)
+    r.p.cosmo, r.p.H0, r.p.omega_m, r.p.omega_l, r.p.a0 = 1, 2.194e-18, 0.31, 0.69, 0.1
+    r.solver.close()
+    r.solver = B.Solver(r.p, r.states)
+    for i, box in enumerate(w.boxes):
+        r.solver.set_sources(i, box.src_cells, box.src_Q)
+    r.reset()
+    r.run(w.steps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        r.reset()
+        r.run(w.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    a = B.rt_query(r.solver.h).a
+    r.close()
+    return {"value": w.cells * w.steps * K / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms / K,
+            "a_after_all_runs": a, "a0": 0.1}
+
+
 def adjoint_run():
     """The adjoint workload (64^3, 16 sources, 1 group, 4 fixed chemistry
     intervals, 200 steps, checkpoints every 20): forward and reverse time of
@@ -629,6 +661,7 @@ def main():
     adj = None if args.no_adjoint else adjoint_run()
     crta = None if args.no_crta else crta_run()
     hll = None if args.no_hll else hll_run()
+    cosmo = None if args.no_cosmo else cosmo_run()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -650,7 +683,7 @@ def main():
                             "launches": kern[k]["launches"]} for k in kern},
             "launch": launch,
             "fp64_form": fp64, "e2e": e2e, "cpu_baseline": cpu,
-            "ensemble": ens, "adjoint": adj, "crta": crta, "hll": hll,
+            "ensemble": ens, "adjoint": adj, "crta": crta, "hll": hll, "cosmo": cosmo,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "final_diag": dict(zip(B.DIAG_NAMES, diag)),
         }

@@ -114,6 +114,14 @@ typedef struct rt_params {
                                             and by the HLL flux */
     int    flux;                         /* rt_flux; rt_adjoint and rt_transport_static need GLF */
     double inflow[6];                    /* photons/cm^2/s entering through each RT_BC_INFLOW face */
+    int    cosmo;                        /* 1: supercomoving units (Sec. 3).  U holds the comoving
+                                            N^ = a^3 N / nunit and F^ = a^3 F / (c_red nunit), T holds
+                                            T~ = a^2 T, n0 and dx are comoving (their a = 1 values);
+                                            each step runs the chemistry in physical units at its a
+                                            and advances a over dt = a dt_com by the Friedmann
+                                            equation.  Every box must have the same dx. */
+    double H0, omega_m, omega_l;         /* cosmo: Hubble constant (1/s), matter and vacuum densities */
+    double a0;                           /* cosmo: expansion factor at rt_create (> 0) */
 } rt_params;
 
 typedef struct rt_box {
@@ -143,6 +151,7 @@ typedef struct rt_stats {
     int64_t kernel_launches[3];          /* launches timed into kernel_ms */
     int     tile_x, tile_y;              /* transport tile (columns x rows per block) */
     int     transport_grid, chem_grid;   /* blocks of the persistent transport / chemistry grids */
+    double  a;                           /* cosmo: current expansion factor (1 otherwise) */
 } rt_stats;
 
 typedef struct rt_handle rt_handle;

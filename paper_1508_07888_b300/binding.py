@@ -51,6 +51,9 @@ class rt_params(C.Structure):
         ("tune", C.c_int),
         ("flux", C.c_int),
         ("inflow", C.c_double * 6),
+        ("cosmo", C.c_int),
+        ("H0", C.c_double), ("omega_m", C.c_double), ("omega_l", C.c_double),
+        ("a0", C.c_double),
     ]
 
 
@@ -78,6 +81,7 @@ class rt_stats(C.Structure):
         ("kernel_launches", C.c_int64 * 3),
         ("tile_x", C.c_int), ("tile_y", C.c_int),
         ("transport_grid", C.c_int), ("chem_grid", C.c_int),
+        ("a", C.c_double),
     ]
 
 
@@ -248,7 +252,8 @@ def rt_transport_static(p: rt_params, box: rt_box, nsteps: int, stream_ptr: int 
 def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, isothermal=False,
                 nsub=0, rates_const=False, alphaA=0.0, alphaB=0.0, beta=0.0, bc=(0,) * 6,
                 max_halvings=30, precision=RT_PREC_SPLIT, tune=0, flux=0,
-                inflow=(0.0,) * 6) -> rt_params:
+                inflow=(0.0,) * 6, cosmo=None) -> rt_params:
+    """cosmo: None, or (H0 [1/s], omega_m, omega_l, a0) for supercomoving units."""
     p = rt_params()
     p.ngroups = ngroups
     for i in range(ngroups):
@@ -265,6 +270,9 @@ def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, 
     p.flux = int(flux)
     for k in range(6):
         p.inflow[k] = float(inflow[k])
+    if cosmo is not None:
+        p.cosmo = 1
+        p.H0, p.omega_m, p.omega_l, p.a0 = (float(v) for v in cosmo)
     return p
 
 

@@ -28,6 +28,20 @@
 
 #define RT_GRAPH_STEPS 16
 
+// supercomoving runs advance in chunks of at most this many steps (the a of
+// each step of a chunk is computed on the host and read by the chemistry)
+static constexpr int kCosmoChunk = 4096;
+
+// a after dt (s) from a: one classical Runge-Kutta step of the Friedmann
+// equation da/dt = a H0 sqrt(omega_m / a^3 + omega_l)
+static double friedmann_step(double a, double dt, const rt_params &p)
+{
+    auto rate = [&](double x) { return x * p.H0 * std::sqrt(p.omega_m / (x * x * x) + p.omega_l); };
+    const double k1 = rate(a), k2 = rate(a + 0.5 * dt * k1), k3 = rate(a + 0.5 * dt * k2),
+                 k4 = rate(a + dt * k3);
+    return a + dt * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+}
+
 struct rt_handle {
     rt_params p;
     rtd::Phys ph;
@@ -62,6 +76,8 @@ struct rt_handle {
     std::vector<int64_t *> d_fparent;        // library copies of the parent indices
     int64_t nfitems = 0;
     int fgrid = 1;
+    double a_now = 1.0;                      // cosmo: expansion factor
+    double *d_acos = nullptr, *h_acos = nullptr;   // cosmo: a per step of one chunk
     cudaStream_t user = nullptr, s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -109,6 +125,8 @@ static void release(rt_handle *h)
     cudaFree(h->d_gdone);
     cudaFree(h->d_hll_d);
     cudaFree(h->d_hll_f);
+    cudaFree(h->d_acos);
+    cudaFreeHost(h->h_acos);
     cudaFree(h->d_fines);
     for (auto q : h->d_fparent) cudaFree(q);
     cudaFree(h->d_rtab);
@@ -146,6 +164,11 @@ static int check_params(const rt_params *p)
     if (p->tune < 0) return fail(nullptr, RT_ERR_ARG, "tune must be >= 0");
     if (p->flux != RT_FLUX_GLF && p->flux != RT_FLUX_HLL)
         return fail(nullptr, RT_ERR_ARG, "unknown flux %d", p->flux);
+    if (p->cosmo != 0 && p->cosmo != 1) return fail(nullptr, RT_ERR_ARG, "cosmo must be 0 or 1");
+    if (p->cosmo && (!(p->a0 > 0.0) || !(p->H0 >= 0.0) || !(p->omega_m >= 0.0) ||
+                     !(p->omega_l >= 0.0) || !(p->omega_m + p->omega_l > 0.0) ||
+                     !std::isfinite(p->a0 + p->H0 + p->omega_m + p->omega_l)))
+        return fail(nullptr, RT_ERR_ARG, "cosmo needs a0 > 0, H0 >= 0, omega_m, omega_l >= 0");
     for (int f = 0; f < 6; f++) {
         if (p->bc[f] < RT_BC_PERIODIC || p->bc[f] > RT_BC_INFLOW)
             return fail(nullptr, RT_ERR_ARG, "bc[%d]=%d unknown", f, p->bc[f]);
@@ -412,6 +435,16 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     }
                 }
                 h->ph.flux = p->flux;
+                if (p->cosmo) {
+                    for (int b = 1; b < nboxes; b++)
+                        if (boxes[b].dx != boxes[0].dx)
+                            return fail(h, RT_ERR_ARG, "cosmo: every box needs the same dx");
+                    CU(h, cudaMalloc(&h->d_acos, sizeof(double) * (kCosmoChunk + 1)));
+                    CU(h, cudaMallocHost(&h->h_acos, sizeof(double) * (kCosmoChunk + 1)));
+                    h->ph.cosmo = 1;
+                    h->ph.acos = h->d_acos;
+                    h->a_now = p->a0;
+                }
                 if (p->flux == RT_FLUX_HLL) {           // wave-speed table, FP64 and FP32 copies
                     const int nt = (RTD_HLL_NF + 1) * (RTD_HLL_NM + 1);
                     std::vector<double> td(nt);
@@ -635,6 +668,8 @@ extern "C" int rt_set_fine(rt_handle *h, int box, int64_t nfine, const int64_t *
     }
 }
 
+static int step_chunk(rt_handle *h, int nsteps, double *hist);
+
 extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
 {
     if (!h) return fail(nullptr, RT_ERR_STATE, "NULL handle");
@@ -648,6 +683,20 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
             return fail(h, RT_ERR_ARG, "hist must be device memory or NULL");
         }
     }
+    if (!h->p.cosmo) return step_chunk(h, nsteps, hist);
+    int worst = RT_OK;
+    for (int done = 0; done < nsteps; done += kCosmoChunk) {
+        const int n = std::min(kCosmoChunk, nsteps - done);
+        const int rc = step_chunk(h, n, hist ? hist + (size_t)done * h->nboxes * RTD_NDIAG : nullptr);
+        if (rc == RT_ERR_ARG || rc == RT_ERR_CUDA || rc == RT_ERR_STATE) return rc;
+        if (rc != RT_OK && worst == RT_OK) worst = rc;
+    }
+    return worst;
+}
+
+// nsteps (<= kCosmoChunk when cosmo) steps in one go
+static int step_chunk(rt_handle *h, int nsteps, double *hist)
+{
     rtd::Ctl *c = h->h_ctl;
     c->hist = hist;
     c->step = -1;
@@ -659,6 +708,14 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
     CU(h, cudaEventRecord(h->ev_in, h->user));
     CU(h, cudaStreamWaitEvent(h->s, h->ev_in, 0));
     CU(h, cudaMemcpyAsync(h->d_ctl, c, sizeof(rtd::Ctl), cudaMemcpyHostToDevice, h->s));
+    if (h->p.cosmo) {                    // a at the start of every step of this chunk
+        const double dt_com = h->bdev[0].dt;
+        h->h_acos[0] = h->a_now;
+        for (int k = 0; k < nsteps; k++)
+            h->h_acos[k + 1] = friedmann_step(h->h_acos[k], h->h_acos[k] * dt_com, h->p);
+        CU(h, cudaMemcpyAsync(h->d_acos, h->h_acos, sizeof(double) * (nsteps + 1),
+                              cudaMemcpyHostToDevice, h->s));
+    }
     if (!h->graph && nsteps >= RT_GRAPH_STEPS) {
         int rc = build_graph(h);
         if (rc) return rc;
@@ -696,6 +753,7 @@ extern "C" int rt_step(rt_handle *h, int nsteps, double *hist)
         }
     }
     h->steps_done += nsteps;
+    if (h->p.cosmo) h->a_now = h->h_acos[nsteps];
     h->nclamp += c->nclamp;
     h->error_bits |= (int)c->err;
     if (c->err & RTD_ERR_SUBCYCLE)
@@ -742,6 +800,7 @@ extern "C" int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, cons
         if (h->nboxes != 1) return fail(h, RT_ERR_ARG, "rt_adjoint needs a single-box handle");
         if (!h->fp64) return fail(h, RT_ERR_ARG, "rt_adjoint needs an FP64 precision form");
         if (h->p.flux != RT_FLUX_GLF) return fail(h, RT_ERR_ARG, "rt_adjoint needs the GLF flux");
+        if (h->p.cosmo) return fail(h, RT_ERR_ARG, "rt_adjoint: no supercomoving units");
         for (int f = 0; f < 6; f++)
             if (h->p.bc[f] != RT_BC_PERIODIC)
                 return fail(h, RT_ERR_ARG, "rt_adjoint needs periodic boundaries");
@@ -933,6 +992,7 @@ extern "C" int rt_query(rt_handle *h, rt_stats *st)
     st->tile_y = rtl::kTileY[v];
     st->transport_grid = h->tgrid;
     st->chem_grid = h->cgrid;
+    st->a = h->p.cosmo ? h->a_now : 1.0;
     return RT_OK;
 }
 

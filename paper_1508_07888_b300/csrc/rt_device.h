@@ -68,6 +68,8 @@ struct Phys {
     const double *hll_d;          // the same in FP64
     int bc[6];                    // -x,+x,-y,+y,-z,+z
     double inflow_c[2][RTD_MAXG]; // inflow faces -x, +x: beam density N per group times nunit
+    int cosmo;                    // supercomoving units: state comoving, chemistry at a(t)
+    const double *acos;           // a at the start of each step of the current call, [nsteps + 1]
 };
 
 // One box (array in device memory, indexed by work items).

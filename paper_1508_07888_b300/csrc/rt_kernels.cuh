@@ -1170,6 +1170,42 @@ template <> __device__ __forceinline__ double flux_nmin<double>() { return 1e-29
 __device__ __forceinline__ double ldn(const float *p, int64_t i) { return f2d(p[i]); }
 __device__ __forceinline__ double ldn(const double *p, int64_t i) { return p[i]; }
 
+// Supercomoving units (Sec. 3): the stored state is the comoving N^, F^
+// (units of nunit) and T~ = a^2 T, the density n0 comoving and dt the
+// comoving step; the chemistry of step k runs in physical units at a_k:
+// N, F, S and n0 scaled by 1/a^3, T = T~/a^2, over a_k dt.  After it, back
+// by a^3 (F^ also by a_k/a_(k+1): F^ follows F~/c~, and c~ grows like a) and
+// T~ = a^2 T.
+template <int G>
+__device__ __forceinline__ void cosmo_in(double a, Cell<G> &s, double *S, double &n0, double &span,
+                                         double dt_com)
+{
+    const double ia3 = 1.0 / (a * a * a);
+#pragma unroll
+    for (int i = 0; i < G; i++) {
+        s.N[i] = s.N[i] * ia3;
+#pragma unroll
+        for (int m = 0; m < 3; m++) s.F[i][m] = s.F[i][m] * ia3;
+        S[i] = S[i] * ia3;
+    }
+    n0 = n0 * ia3;
+    s.T = s.T / (a * a);
+    span = a * dt_com;
+}
+
+template <int G>
+__device__ __forceinline__ void cosmo_out(double a, double a1, Cell<G> &s)
+{
+    const double a3 = a * a * a, fr = a / a1;
+#pragma unroll
+    for (int i = 0; i < G; i++) {
+        s.N[i] = s.N[i] * a3;
+#pragma unroll
+        for (int m = 0; m < 3; m++) s.F[i][m] = s.F[i][m] * a3 * fr;
+    }
+    s.T = s.T * (a * a);
+}
+
 // Diagnostics of a set of cells: two FP64 sums (ionised fraction, photons),
 // the largest |F|/N (bits of a non-negative double, so integer max), two
 // integer counts.
@@ -1328,13 +1364,23 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             }
             int ncyc = 0;
             unsigned int err = 0;
-            if (ph.nsub > 0) {
-                const double h = B.dt / ph.nsub;
-                for (int k = 0; k < ph.nsub; k++)
-                    err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, h, false, ncyc);
-            } else {
-                err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, B.dt, true, ncyc);
+            // supercomoving units: the state is comoving, the chemistry runs
+            // in physical units at this step's a (N, F, S, n0 / a^3, T~ / a^2,
+            // dt = a dt_com)
+            double span = B.dt, n0c = n0, ca = 1.0, ca1 = 1.0;
+            if (ph.cosmo) {
+                ca = ph.acos[ctl->step];
+                ca1 = ph.acos[ctl->step + 1];
+                cosmo_in<G>(ca, s, S, n0c, span, B.dt);
             }
+            if (ph.nsub > 0) {
+                const double h = span / ph.nsub;
+                for (int k = 0; k < ph.nsub; k++)
+                    err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, h, false, ncyc);
+            } else {
+                err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, span, true, ncyc);
+            }
+            if (ph.cosmo) cosmo_out<G>(ca, ca1, s);
             if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
             if (err) atomicOr(&ctl->err, err);
             double ph_tot = 0.0;
@@ -1466,12 +1512,15 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         }
         int ncyc = 0;
         unsigned int err = 0;
+        double span = B.dt, n0c = n0;
+        if (ph.cosmo) cosmo_in<G>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
         if (ph.nsub > 0) {
-            const double h = B.dt / ph.nsub;
-            for (int q = 0; q < ph.nsub; q++) err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, h, false, ncyc);
+            const double h = span / ph.nsub;
+            for (int q = 0; q < ph.nsub; q++) err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, h, false, ncyc);
         } else {
-            err |= chem_span<G, STRICT>(ph, tab, B, n0, S, s, B.dt, true, ncyc);
+            err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, span, true, ncyc);
         }
+        if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
         if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
         if (err) atomicOr(&ctl->err, err);
         F.xHI[f] = s.xHI;

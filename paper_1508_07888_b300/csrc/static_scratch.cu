@@ -74,6 +74,7 @@ extern "C" int rt_transport_static(const rt_params *p, const rt_box *box, int ns
     if (p->precision < RT_PREC_SPLIT || p->precision > RT_PREC_FP64_STRICT)
         return err(RT_ERR_ARG, "rt_transport_static: unknown precision");
     if (p->flux != RT_FLUX_GLF) return err(RT_ERR_ARG, "rt_transport_static: GLF flux only");
+    if (p->cosmo) return err(RT_ERR_ARG, "rt_transport_static: no supercomoving units");
     for (int f = 0; f < 6; f++)
         if (p->bc[f] < RT_BC_PERIODIC || p->bc[f] > RT_BC_REFLECTIVE)
             return err(RT_ERR_ARG, "rt_transport_static: unknown boundary condition");

@@ -16,6 +16,7 @@
 #include <cstdint>
 
 #include <cstring>
+#include <type_traits>
 
 #include "rt_device.h"
 
@@ -935,7 +936,7 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const double *tab, do
     r.aB = tab_poly(a + 1 * RTD_TAB_NC, t);
     r.aA = ph.ots ? r.aB : tab_poly(a, t);
     r.kR = tab_poly(a + 2 * RTD_TAB_NC, t);
-    if (T >= RTD_TAB_TCUT) {
+    if (dbits(T) >= dbits(RTD_TAB_TCUT)) {       // T >= TCUT (both positive)
         const double invT = 1.0 / T;
         r.beta = exp(tab_poly(a + 3 * RTD_TAB_NC, t) - rtd::T_HI * invT);
         const double cce = exp(tab_poly(a + 4 * RTD_TAB_NC, t) - 118348.0 * invT);
@@ -1040,11 +1041,13 @@ struct CellK {
     double n02, K, cvn; // n0^2, n0^2 / nunit, (3/2) kB n0
 };
 
-template <int G>
+// DEFER: F is not carried through the trial (nothing in the chemistry reads
+// it; it only scales by 1/den), the scale of each group goes to rd[] instead
+template <int G, bool DEFER>
 __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B, const CellK<G> &k,
                                                 double n0, const double *S, const Rates &r,
                                                 double alpha, const Cell<G> &s, double e0,
-                                                double dtau, Cell<G> &o, double &e1)
+                                                double dtau, Cell<G> &o, double &e1, double *rdo)
 {
     const double x = 1.0 - s.xHI;
     const double q = s.xHI * n0 * dtau;
@@ -1054,8 +1057,12 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
         const double rd = rcp_nr(fma(ph.csig[i], q, 1.0));
         const double src = (i == 0 && !ph.ots) ? S[i] + rec : S[i];
         o.N[i] = fma(src, dtau, s.N[i]) * rd;
+        if (DEFER) {
+            rdo[i] = rd;
+        } else {
 #pragma unroll
-        for (int m = 0; m < 3; m++) o.F[i][m] = s.F[i][m] * rd;
+            for (int m = 0; m < 3; m++) o.F[i][m] = s.F[i][m] * rd;
+        }
     }
     double gam = B.gN[0] * o.N[0];
 #pragma unroll
@@ -1077,11 +1084,31 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
     o.T = e1 * rcp_nr(k.cvn * (2.0 - o.xHI));
 }
 
+// fac (fast forms without a trace): F is left alone and each group's scale
+// over the accepted trials is multiplied into fac[i] (the caller starts it
+// at 1 and applies it to F); otherwise F is updated in s and fac unused.
+// s <- o; F only when it is carried through the trials
+template <int G, bool F_TOO>
+__device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
+{
+#pragma unroll
+    for (int i = 0; i < G; i++) {
+        s.N[i] = o.N[i];
+        if (F_TOO) {
+#pragma unroll
+            for (int m = 0; m < 3; m++) s.F[i][m] = o.F[i][m];
+        }
+    }
+    s.xHI = o.xHI;
+    s.T = o.T;
+}
+
 template <int G, bool STRICT, class Trace = NoTrace>
 __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,
-                                  int &ncyc, Trace *tr = nullptr)
+                                  int &ncyc, Trace *tr = nullptr, double *fac = nullptr)
 {
+    constexpr bool DEFER = !STRICT && std::is_same<Trace, NoTrace>::value;
     unsigned int err = 0;
     double tau = 0.0;
     CellK<G> k;
@@ -1123,33 +1150,46 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
             // |e| >= rem |rate| (1 + 1e-13) it is >= rem whatever the
             // rounding, and the division is skipped
             const double ar = fabs(rate);
-            if (rate != 0.0 && !(fabs(e) >= rem * ar * 1.0000000000001)) {
+            const double lim = rem * ar * 1.0000000000001;
+            // non-negative doubles order like their bit patterns: the fast
+            // forms compare them on the integer pipe
+            const bool skip = STRICT ? (rate == 0.0 || fabs(e) >= lim)
+                                     : ((dbits(rate) << 1) == 0ull ||
+                                        (long long)dbits(fabs(e)) >= (long long)dbits(lim));
+            if (!skip) {
                 const double est = STRICT ? fabs(e / rate) : fabs(e) * rcp_nr(ar);
                 if (est < rem) { dtau = est; last = false; }
             }
         }
         Cell<G> o;
-        double ep, e1;
+        double ep, e1, rd[G];
         for (int h = 0;; h++) {
             if (STRICT) {
                 chem_trial<G, true>(ph, B.nunit, B.inv_nunit, n0, S, r, alpha, s, dtau, o, ep, e1);
             } else {
                 ep = ep0;
-                chem_trial_fast<G>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1);
+                chem_trial_fast<G, DEFER>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd);
             }
             if (ph.isothermal) break;
-            if (!isfinite(e1)) {            // no amount of halving repairs a NaN/Inf
-                s = o;
+            const bool finite = STRICT ? isfinite(e1)
+                                       : (dbits(e1) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+            if (!finite) {                  // no amount of halving repairs a NaN/Inf
+                take<G, !DEFER>(s, o);
                 ncyc++;
                 return err | RTD_ERR_NONFINITE;
             }
-            if (fabs(e1 - ep) <= 0.1 * ep) break;
+            const double de = fabs(e1 - ep), tol = 0.1 * ep;
+            if (STRICT ? de <= tol : (long long)dbits(de) <= (long long)dbits(tol)) break;
             if (h >= ph.max_halvings) { err |= RTD_ERR_SUBCYCLE; break; }
             dtau = 0.5 * dtau;
             last = false;
         }
         if (tr) tr->push(s, dtau);
-        s = o;
+        if (DEFER) {
+#pragma unroll
+            for (int i = 0; i < G; i++) fac[i] *= rd[i];
+        }
+        take<G, !DEFER>(s, o);
         ncyc++;
         if (last) break;
         tau = tau + dtau;
@@ -1176,7 +1216,9 @@ __device__ __forceinline__ double ldn(const double *p, int64_t i) { return p[i];
 // N, F, S and n0 scaled by 1/a^3, T = T~/a^2, over a_k dt.  After it, back
 // by a^3 (F^ also by a_k/a_(k+1): F^ follows F~/c~, and c~ grows like a) and
 // T~ = a^2 T.
-template <int G>
+// F_TOO: F is carried in the cell (strict form); the fast forms scale F
+// once at the end (the 1/a^3 and a^3 cancel, a_k/a_(k+1) goes into fac)
+template <int G, bool F_TOO>
 __device__ __forceinline__ void cosmo_in(double a, Cell<G> &s, double *S, double &n0, double &span,
                                          double dt_com)
 {
@@ -1184,8 +1226,10 @@ __device__ __forceinline__ void cosmo_in(double a, Cell<G> &s, double *S, double
 #pragma unroll
     for (int i = 0; i < G; i++) {
         s.N[i] = s.N[i] * ia3;
+        if (F_TOO) {
 #pragma unroll
-        for (int m = 0; m < 3; m++) s.F[i][m] = s.F[i][m] * ia3;
+            for (int m = 0; m < 3; m++) s.F[i][m] = s.F[i][m] * ia3;
+        }
         S[i] = S[i] * ia3;
     }
     n0 = n0 * ia3;
@@ -1193,15 +1237,17 @@ __device__ __forceinline__ void cosmo_in(double a, Cell<G> &s, double *S, double
     span = a * dt_com;
 }
 
-template <int G>
+template <int G, bool F_TOO>
 __device__ __forceinline__ void cosmo_out(double a, double a1, Cell<G> &s)
 {
     const double a3 = a * a * a, fr = a / a1;
 #pragma unroll
     for (int i = 0; i < G; i++) {
         s.N[i] = s.N[i] * a3;
+        if (F_TOO) {
 #pragma unroll
-        for (int m = 0; m < 3; m++) s.F[i][m] = s.F[i][m] * a3 * fr;
+            for (int m = 0; m < 3; m++) s.F[i][m] = s.F[i][m] * a3 * fr;
+        }
     }
     s.T = s.T * (a * a);
 }
@@ -1327,11 +1373,18 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             Cell<G> s;
             unsigned long long nclamp = 0;
             bool gross = false;
+            // fast forms: F stays in the stored precision and is scaled once
+            // at the end (read again from U*) by the product of its per-trial
+            // factors (fac)
+            double fac[G];
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
                 s.N[i] = to_d(u.x);
-                s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
+                fac[i] = 1.0;
+                if (STRICT) {
+                    s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
+                }
                 // flux limit after transport, in the state's own precision;
                 // F is scaled by 1/N first so no square underflows
                 if (u.x > flux_nmin<TU>()) {
@@ -1371,24 +1424,38 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (ph.cosmo) {
                 ca = ph.acos[ctl->step];
                 ca1 = ph.acos[ctl->step + 1];
-                cosmo_in<G>(ca, s, S, n0c, span, B.dt);
+                cosmo_in<G, STRICT>(ca, s, S, n0c, span, B.dt);
             }
             if (ph.nsub > 0) {
                 const double h = span / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, h, false, ncyc);
+                    err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
             } else {
-                err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, span, true, ncyc);
+                err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
             }
-            if (ph.cosmo) cosmo_out<G>(ca, ca1, s);
+            if (ph.cosmo) {
+                cosmo_out<G, STRICT>(ca, ca1, s);
+                if (!STRICT) {
+                    const double fr = ca / ca1;
+#pragma unroll
+                    for (int i = 0; i < G; i++) fac[i] = fac[i] * fr;
+                }
+            }
             if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
             if (err) atomicOr(&ctl->err, err);
             double ph_tot = 0.0;
             TU f2max = TU(0);                  // largest |F/N|^2 of the cell's groups
 #pragma unroll
             for (int i = 0; i < G; i++) {
-                const V4<TU> o = {from_d<TU>(s.N[i]), from_d<TU>(s.F[i][0]), from_d<TU>(s.F[i][1]),
-                                  from_d<TU>(s.F[i][2])};
+                V4<TU> o;
+                o.x = from_d<TU>(s.N[i]);
+                if (STRICT) {
+                    o.y = from_d<TU>(s.F[i][0]); o.z = from_d<TU>(s.F[i][1]); o.w = from_d<TU>(s.F[i][2]);
+                } else {
+                    const TU fi = from_d<TU>(fac[i]);
+                    const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
+                    o.y = u.y * fi; o.z = u.z * fi; o.w = u.w * fi;
+                }
                 st4(U + (int64_t)i * B.ncell + c, o);
                 ph_tot += to_d(o.x);
                 if (o.x > flux_nmin<TU>()) {
@@ -1488,11 +1555,15 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         const int64_t c = F.parent[f];
         const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
         Cell<G> s;
+        double fac[G];                 // the refined cell's radiation is not kept
 #pragma unroll
         for (int i = 0; i < G; i++) {
             const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
             s.N[i] = to_d(u.x);
-            s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
+            fac[i] = 1.0;
+            if (STRICT) {
+                s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
+            }
         }
         s.xHI = F.xHI[f];
         s.T = F.T[f];
@@ -1513,12 +1584,13 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         int ncyc = 0;
         unsigned int err = 0;
         double span = B.dt, n0c = n0;
-        if (ph.cosmo) cosmo_in<G>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
+        if (ph.cosmo) cosmo_in<G, STRICT>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
         if (ph.nsub > 0) {
             const double h = span / ph.nsub;
-            for (int q = 0; q < ph.nsub; q++) err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, h, false, ncyc);
+            for (int q = 0; q < ph.nsub; q++)
+                err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
         } else {
-            err |= chem_span<G, STRICT>(ph, tab, B, n0c, S, s, span, true, ncyc);
+            err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
         }
         if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
         if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;

@@ -146,6 +146,35 @@ __device__ __forceinline__ double rcp_nr(double d)
 __device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
 __device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
 
+// reciprocal and square root of the generic kernels: the FP32 fast path
+// (the HLL transport of the split form) takes the MUFU approximations
+// (rcp.approx / sqrt.approx, ~1 ulp), as the FP32 GLF kernel does; FP64 and
+// the strict form take IEEE division and square root
+template <typename R, bool STRICT>
+__device__ __forceinline__ R frcp(R x) { return R(1) / x; }
+template <>
+__device__ __forceinline__ float frcp<float, false>(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <typename R, bool STRICT>
+__device__ __forceinline__ R fdiv(R a, R b) { return a / b; }
+template <>
+__device__ __forceinline__ float fdiv<float, false>(float a, float b) { return a * frcp<float, false>(b); }
+template <typename R, bool STRICT>
+__device__ __forceinline__ R fsqrt(R x) { return rsqrt_(x); }
+template <typename R, bool STRICT>
+__device__ __forceinline__ constexpr bool approx_form() { return !STRICT && sizeof(R) == 4; }
+template <>
+__device__ __forceinline__ float fsqrt<float, false>(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ------------------------------------------------------------- M1 closure
 // Levermore closure, P = Nhat D with D = (1-chi)/2 I + (3chi-1)/2 n n
 // (Sec. 2.2.3; the printed coefficients are swapped, the diffusive limit
@@ -168,29 +197,39 @@ __device__ __forceinline__ void closure(const V4<R> &u, R P[6])
         if (STRICT) {
             ux = u.y / N; uy = u.z / N; uz = u.w / N;
         } else {
-            const R rN = R(1) / N;
+            const R rN = frcp<R, STRICT>(N);
             ux = u.y * rN; uy = u.z * rN; uz = u.w * rN;
         }
         R f2 = ux * ux + uy * uy + uz * uz;
-        if (f2 > R(1)) {                       // rounding guard of |F| <= cN
-            const R f = rsqrt_(f2);
+        // rounding guard of |F| <= cN.  With the approximate reciprocal a
+        // beam (|F| = cN exactly) lands a few ulp either side of f = 1, so
+        // the FP32 fast form takes f^2 >= 1 - 2^-20 as the beam itself and
+        // its closure exactly: chi = 1, a = 0, g = 1, P = N n n
+        constexpr bool AP = approx_form<R, STRICT>();
+        const bool beam = AP ? f2 >= R(1) - R(9.5367431640625e-07) : f2 > R(1);
+        if (beam) {
+            const R f = fsqrt<R, STRICT>(f2);
             if (STRICT) {
                 ux = ux / f; uy = uy / f; uz = uz / f;
             } else {
-                const R rf = R(1) / f;
+                const R rf = frcp<R, STRICT>(f);
                 ux *= rf; uy *= rf; uz *= rf;
             }
             f2 = R(1);
         }
-        const R s = rsqrt_(R(4) - R(3) * f2);
         R a, g;
-        if (STRICT) {
+        if (AP && beam) {
+            a = R(0);
+            g = R(1);
+        } else if (STRICT) {
+            const R s = fsqrt<R, STRICT>(R(4) - R(3) * f2);
             a = ((R(1) + s) - R(2) * f2) / (R(5) + R(2) * s);
             g = (R(6) + R(3) / (R(2) + s)) / (R(5) + R(2) * s);
         } else {
-            const R r5 = R(1) / (R(5) + R(2) * s);
+            const R s = fsqrt<R, STRICT>(R(4) - R(3) * f2);
+            const R r5 = frcp<R, STRICT>(R(5) + R(2) * s);
             a = ((R(1) + s) - R(2) * f2) * r5;
-            g = (R(6) + R(3) / (R(2) + s)) * r5;
+            g = (R(6) + fdiv<R, STRICT>(R(3), R(2) + s)) * r5;
         }
         P[0] = N * (a + g * (ux * ux));
         P[1] = N * (g * (ux * uy));
@@ -253,19 +292,22 @@ __device__ __forceinline__ void hll_fz(const V4<R> &u, R &Fn, R &z)
     R f = R(0);
     Fn = R(0);
     if (u.x > closure_nmin<R>()) {
-        Fn = rsqrt_(u.y * u.y + u.z * u.z + u.w * u.w);
+        Fn = fsqrt<R, STRICT>(u.y * u.y + u.z * u.z + u.w * u.w);
         if (Fn > R(0)) {
-            f = Fn / u.x;
-            if (f > R(1)) f = R(1);
+            f = fdiv<R, STRICT>(Fn, u.x);
+            // clamp to 1; the FP32 fast form also takes f within rounding of
+            // 1 as the beam (z = sqrt(1 - f) would turn one ulp of f into a
+            // transverse speed of 2e-4)
+            if (f >= (approx_form<R, STRICT>() ? R(1) - R(4.76837158203125e-07) : R(1))) f = R(1);
         }
     }
-    z = rsqrt_(R(1) - f);
+    z = fsqrt<R, STRICT>(R(1) - f);
 }
 
-template <typename R, int d>
+template <typename R, bool STRICT, int d>
 __device__ __forceinline__ void hll_speed(const R *tab, const V4<R> &u, R Fn, R z, R &smin, R &smax)
 {
-    const R mu = Fn > R(0) ? comp(u, 1 + d) / Fn : R(0);
+    const R mu = Fn > R(0) ? fdiv<R, STRICT>(comp(u, 1 + d), Fn) : R(0);
     smax = hll_lookup(tab, z, mu);
     smin = -hll_lookup(tab, z, -mu);
 }
@@ -289,7 +331,7 @@ __device__ __forceinline__ void hll(const V4<R> &uL, const R PL[6], R aL, R bL, 
         for (int m = 0; m < 4; m++) Phi[m] = R(0.5) * (GL[m] + GR[m]);
         return;
     }
-    const R den = lp - lm, ll = lp * lm, rden = R(1) / den;
+    const R den = lp - lm, ll = lp * lm, rden = frcp<R, STRICT>(den);
 #pragma unroll
     for (int m = 0; m < 4; m++) {
         const R num = lp * GL[m] - lm * GR[m] + ll * (comp(uR, m) - comp(uL, m));
@@ -510,10 +552,10 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                 if constexpr (HLL) {
                     R Fn, zz, a, b;
                     hll_fz<R, STRICT>(un, Fn, zz);
-                    hll_speed<R, 0>(htab, un, Fn, zz, a, b);
+                    hll_speed<R, STRICT, 0>(htab, un, Fn, zz, a, b);
                     sm.Sp[pslot][0][ty + 1][tx + 1] = a;
                     sm.Sp[pslot][1][ty + 1][tx + 1] = b;
-                    hll_speed<R, 1>(htab, un, Fn, zz, a, b);
+                    hll_speed<R, STRICT, 1>(htab, un, Fn, zz, a, b);
                     sm.Sp[pslot][2][ty + 1][tx + 1] = a;
                     sm.Sp[pslot][3][ty + 1][tx + 1] = b;
                 }
@@ -530,10 +572,10 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                 if constexpr (HLL) {
                     R Fn, zz, a, b;
                     hll_fz<R, STRICT>(h, Fn, zz);
-                    hll_speed<R, 0>(htab, h, Fn, zz, a, b);
+                    hll_speed<R, STRICT, 0>(htab, h, Fn, zz, a, b);
                     sm.Sp[pslot][0][hy][hx] = a;
                     sm.Sp[pslot][1][hy][hx] = b;
-                    hll_speed<R, 1>(htab, h, Fn, zz, a, b);
+                    hll_speed<R, STRICT, 1>(htab, h, Fn, zz, a, b);
                     sm.Sp[pslot][2][hy][hx] = a;
                     sm.Sp[pslot][3][hy][hx] = b;
                 }
@@ -550,8 +592,8 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                 R Fc, zc_, Fq, zq, a0, b0, a1, b1;
                 hll_fz<R, STRICT>(uc, Fc, zc_);
                 hll_fz<R, STRICT>(un, Fq, zq);
-                hll_speed<R, 2>(htab, uc, Fc, zc_, a0, b0);
-                hll_speed<R, 2>(htab, un, Fq, zq, a1, b1);
+                hll_speed<R, STRICT, 2>(htab, uc, Fc, zc_, a0, b0);
+                hll_speed<R, STRICT, 2>(htab, un, Fq, zq, a1, b1);
                 hll<R, STRICT, 2>(uc, Pc, a0, b0, un, Pn, a1, b1, Fzp);
             } else {
                 glf<R, 2>(uc, Pc, un, Pn, Fzp);

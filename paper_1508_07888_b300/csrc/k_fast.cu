@@ -1,6 +1,7 @@
 // k_fast.cu -- instantiations of the hot-path kernels with the compiler's
 // default floating-point contraction (fused multiply-add): the FP32
-// transport + FP64 chemistry form and the all-FP64 form.
+// transport + FP64 chemistry form (GLF and HLL transports) and the all-FP64
+// form.
 #include "launch.h"
 #include "rt_kernels.cuh"
 
@@ -22,7 +23,7 @@ static cudaError_t transport_attr()
     return e;
 }
 
-// the canonical transport kernel (FP64 forms, and the HLL flux in FP32)
+// the canonical transport kernel (the FP64 forms, GLF and HLL)
 template <typename R, int FLUX>
 static cudaError_t transport_generic(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
@@ -62,13 +63,46 @@ static cudaError_t transport_pm(const Launch &L, int zc, const rtd::Phys &ph, rt
 
 template <int TX, int TY>
 static int pm_occupancy();
+template <int TX, int TY>
+static int hll_occupancy();
+
+// the FP32 HLL transport with a TX x TY tile
+template <int TX, int TY>
+static cudaError_t hll_attr()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport_hll<TX, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rtk::transport_hll_smem_bytes<TX, TY>());
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
+template <int TX, int TY>
+static cudaError_t transport_hll(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
+{
+    cudaError_t e = hll_attr<TX, TY>();
+    if (e != cudaSuccess) return e;
+    rtk::k_transport_hll<TX, TY><<<L.grid, dim3(TX, TY), rtk::transport_hll_smem_bytes<TX, TY>(), L.stream>>>(
+        L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
+    return cudaSuccess;
+}
 
 cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
     cudaError_t e = cudaSuccess;
-    if (ph.flux == RTD_FLUX_HLL) {
-        e = fp64 ? transport_generic<double, RTD_FLUX_HLL>(L, zc, ph, ctl)
-                 : transport_generic<float, RTD_FLUX_HLL>(L, zc, ph, ctl);
+    if (ph.flux == RTD_FLUX_HLL && fp64) {
+        e = transport_generic<double, RTD_FLUX_HLL>(L, zc, ph, ctl);
+    } else if (ph.flux == RTD_FLUX_HLL) {
+        switch (L.variant) {
+        case 0: e = transport_hll<kTileX[0], kTileY[0]>(L, zc, ph, ctl); break;
+        case 1: e = transport_hll<kTileX[1], kTileY[1]>(L, zc, ph, ctl); break;
+        case 2: e = transport_hll<kTileX[2], kTileY[2]>(L, zc, ph, ctl); break;
+        default: return cudaErrorInvalidValue;
+        }
     } else if (fp64) {
         e = transport_generic<double, RTD_FLUX_GLF>(L, zc, ph, ctl);
     } else {
@@ -152,14 +186,27 @@ static int generic_occupancy()
 
 int transport_occupancy_fast(bool fp64, int variant, int flux)
 {
-    if (flux == RTD_FLUX_HLL)
-        return fp64 ? generic_occupancy<double, RTD_FLUX_HLL>() : generic_occupancy<float, RTD_FLUX_HLL>();
+    if (flux == RTD_FLUX_HLL && fp64) return generic_occupancy<double, RTD_FLUX_HLL>();
+    if (flux == RTD_FLUX_HLL) {
+        switch (variant) {
+        case 1: return hll_occupancy<kTileX[1], kTileY[1]>();
+        case 2: return hll_occupancy<kTileX[2], kTileY[2]>();
+        default: return hll_occupancy<kTileX[0], kTileY[0]>();
+        }
+    }
     if (fp64) return generic_occupancy<double, RTD_FLUX_GLF>();
     switch (variant) {
     case 1: return pm_occupancy<kTileX[1], kTileY[1]>();
     case 2: return pm_occupancy<kTileX[2], kTileY[2]>();
     default: return pm_occupancy<kTileX[0], kTileY[0]>();
     }
+}
+
+template <int TX, int TY>
+static int hll_occupancy()
+{
+    hll_attr<TX, TY>();
+    return occ((const void *)rtk::k_transport_hll<TX, TY>, TX * TY, rtk::transport_hll_smem_bytes<TX, TY>());
 }
 
 template <int TX, int TY>

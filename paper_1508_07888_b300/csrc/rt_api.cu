@@ -62,6 +62,7 @@ struct rt_handle {
     double *d_rtab = nullptr;                // rate table (null: fits evaluated directly)
     double *d_hll_d = nullptr;               // HLL wave speeds (FP64, FP32 copies)
     float *d_hll_f = nullptr;
+    float4 *d_hll_f4 = nullptr;
     double *d_lastdiag = nullptr;
     rtd::Ctl *d_ctl = nullptr;
     rtd::Ctl *h_ctl = nullptr;               // pinned mirror
@@ -125,6 +126,7 @@ static void release(rt_handle *h)
     cudaFree(h->d_gdone);
     cudaFree(h->d_hll_d);
     cudaFree(h->d_hll_f);
+    cudaFree(h->d_hll_f4);
     cudaFree(h->d_acos);
     cudaFreeHost(h->h_acos);
     cudaFree(h->d_fines);
@@ -229,10 +231,10 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
 {
     std::vector<TuneChoice> cand;
     for (int v = 0; v < rtl::kTileVariants; v++) {
-        const int occ = rtl::transport_occupancy(false, false, v);
+        const int occ = rtl::transport_occupancy(false, false, v, h->p.flux);
         for (int m = 1; m <= occ; m++) cand.push_back({v, m});
     }
-    std::string key = std::to_string(dev) + "/" + std::to_string(h->p.ngroups);
+    std::string key = std::to_string(dev) + "/" + std::to_string(h->p.flux) + "/" + std::to_string(h->p.ngroups);
     for (const auto &D : h->bdev)
         key += "/" + std::to_string(D.nx) + "x" + std::to_string(D.ny) + "x" + std::to_string(D.nz);
     TuneChoice best{0, 1};
@@ -452,6 +454,19 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     if (rt_hll_speeds(RTD_HLL_NF, RTD_HLL_NM, td.data()) != RT_OK)
                         return fail(h, RT_ERR_ARG, "HLL speed table");
                     for (int i = 0; i < nt; i++) tf[i] = (float)td[i];
+                    // FP32 pairs (lambda_min, lambda_max) at (i, j) and
+                    // (i, j + 1), lambda_min(f, mu_j) = -lambda_max(f, mu_{NM - j})
+                    const int n4 = (RTD_HLL_NF + 1) * RTD_HLL_NM;
+                    std::vector<float4> tf4(n4);
+                    for (int i = 0; i <= RTD_HLL_NF; i++) {
+                        const float *row = tf.data() + i * (RTD_HLL_NM + 1);
+                        for (int j = 0; j < RTD_HLL_NM; j++)
+                            tf4[i * RTD_HLL_NM + j] = make_float4(-row[RTD_HLL_NM - j], row[j],
+                                                                  -row[RTD_HLL_NM - j - 1], row[j + 1]);
+                    }
+                    CU(h, cudaMalloc(&h->d_hll_f4, sizeof(float4) * n4));
+                    CU(h, cudaMemcpy(h->d_hll_f4, tf4.data(), sizeof(float4) * n4, cudaMemcpyHostToDevice));
+                    h->ph.hll_f4 = h->d_hll_f4;
                     CU(h, cudaMalloc(&h->d_hll_d, sizeof(double) * nt));
                     CU(h, cudaMalloc(&h->d_hll_f, sizeof(float) * nt));
                     CU(h, cudaMemcpy(h->d_hll_d, td.data(), sizeof(double) * nt, cudaMemcpyHostToDevice));
@@ -483,7 +498,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMalloc(&h->d_fines, sizeof(rtd::FineDev) * nboxes));
                 CU(h, cudaMemcpy(h->d_fines, h->fdev.data(), sizeof(rtd::FineDev) * nboxes,
                                  cudaMemcpyHostToDevice));
-                if (!fp64 && p->flux == RT_FLUX_GLF && p->tune > 0)
+                if (!fp64 && p->tune > 0)
                     return tune_transport(h, p->tune, dev, nsm);
                 return RT_OK;
             }()))
@@ -987,7 +1002,7 @@ extern "C" int rt_query(rt_handle *h, rt_stats *st)
         st->kernel_ms[j] = h->kernel_ms[j];
         st->kernel_launches[j] = h->kernel_launches[j];
     }
-    const int v = (h->fp64 || h->p.flux != RT_FLUX_GLF) ? 0 : h->tvariant;
+    const int v = h->fp64 ? 0 : h->tvariant;
     st->tile_x = rtl::kTileX[v];
     st->tile_y = rtl::kTileY[v];
     st->transport_grid = h->tgrid;

@@ -66,6 +66,7 @@ struct Phys {
     int flux;                     // RTD_FLUX_GLF / RTD_FLUX_HLL
     const float *hll_f;           // HLL wave speeds [RTD_HLL_NF + 1][RTD_HLL_NM + 1], FP32 copy
     const double *hll_d;          // the same in FP64
+    const float4 *hll_f4;         // FP32 (lambda_min, lambda_max) at (i, j) and (i, j+1), [NF + 1][NM] (k_transport_hll)
     int bc[6];                    // -x,+x,-y,+y,-z,+z
     double inflow_c[2][RTD_MAXG]; // inflow faces -x, +x: beam density N per group times nunit
     int cosmo;                    // supercomoving units: state comoving, chemistry at a(t)

@@ -532,6 +532,7 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
         for (int q = 0; q < S - 2; q++) issue(q);
 
         R Fzm[4] = {R(0), R(0), R(0), R(0)};
+        R szc_a = R(0), szc_b = R(0);     // HLL: z speeds of the plane being updated
         for (int q = 0; q < L; q++) {
             cp_async_wait<S - 3>();
             __syncthreads();        // plane q landed everywhere; plane q-1's closures visible;
@@ -542,6 +543,7 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
             src_plane(q, zneg);
             R Pn[6];
             V4<R> un = {};
+            R szn_a = R(0), szn_b = R(0);
             if (act) {
                 V4<R> &uref = sm.U[slot][ty + 1][tx + 1];
                 if (zneg) uref.w = -uref.w;                // reflective z ghost plane
@@ -550,6 +552,8 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
 #pragma unroll
                 for (int k = 0; k < 6; k++) sm.P[pslot][k][ty + 1][tx + 1] = Pn[k];
                 if constexpr (HLL) {
+                    // the cell's speeds along x, y (shared with the neighbours)
+                    // and z (kept for its two z faces)
                     R Fn, zz, a, b;
                     hll_fz<R, STRICT>(un, Fn, zz);
                     hll_speed<R, STRICT, 0>(htab, un, Fn, zz, a, b);
@@ -558,6 +562,7 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                     hll_speed<R, STRICT, 1>(htab, un, Fn, zz, a, b);
                     sm.Sp[pslot][2][ty + 1][tx + 1] = a;
                     sm.Sp[pslot][3][ty + 1][tx + 1] = b;
+                    hll_speed<R, STRICT, 2>(htab, un, Fn, zz, szn_a, szn_b);
                 }
             }
             if (hx >= 0) {
@@ -580,6 +585,9 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
                     sm.Sp[pslot][3][hy][hx] = b;
                 }
             }
+            const R sza = szc_a, szb = szc_b;
+            szc_a = szn_a;
+            szc_b = szn_b;
             if (q == 0 || !act) continue;
             // update plane c = q - 1 (z = z0 + q - 2) unless c is the ghost plane 0
             const int c = q - 1, cs = c % S, cp = c & 1;
@@ -589,12 +597,7 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
             for (int k = 0; k < 6; k++) Pc[k] = sm.P[cp][k][ty + 1][tx + 1];
             R Fzp[4];
             if constexpr (HLL) {
-                R Fc, zc_, Fq, zq, a0, b0, a1, b1;
-                hll_fz<R, STRICT>(uc, Fc, zc_);
-                hll_fz<R, STRICT>(un, Fq, zq);
-                hll_speed<R, STRICT, 2>(htab, uc, Fc, zc_, a0, b0);
-                hll_speed<R, STRICT, 2>(htab, un, Fq, zq, a1, b1);
-                hll<R, STRICT, 2>(uc, Pc, a0, b0, un, Pn, a1, b1, Fzp);
+                hll<R, STRICT, 2>(uc, Pc, sza, szb, un, Pn, szn_a, szn_b, Fzp);
             } else {
                 glf<R, 2>(uc, Pc, un, Pn, Fzp);
             }
@@ -885,6 +888,301 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
             Rz_prev = Rz_c;
             Rz_c = Rz_n;
             uc = un;
+            slot = slot + 1 == S ? 0 : slot + 1;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------- FP32 HLL transport
+// Both signal speeds of a state along one axis from the paired table: entry
+// (i, j), j < NM, holds the pairs (lambda_min, lambda_max) at mu_j and
+// mu_{j+1}, f = 1 - (i/NF)^2, mu_j = -1 + 2j/NM, with lambda_min(f, mu) =
+// -lambda_max(f, -mu) stored beside lambda_max; the bilinear form of
+// hll_lookup on both at once, two 16-byte loads.  The row part (i, tx)
+// depends on f only and is shared by the three axes.
+__device__ __forceinline__ float2 hll_pair(const float4 *__restrict__ tab, int i, float tx, float mu)
+{
+    const float y = (mu + 1.0f) * (0.5f * (float)RTD_HLL_NM);
+    int j = (int)y;
+    j = j > RTD_HLL_NM - 1 ? RTD_HLL_NM - 1 : (j < 0 ? 0 : j);
+    const float ty = y - (float)j;
+    const float4 r0 = __ldg(tab + i * RTD_HLL_NM + j), r1 = __ldg(tab + (i + 1) * RTD_HLL_NM + j);
+    const float2 v00 = lo2(r0), v01 = hi2(r0), v10 = lo2(r1), v11 = hi2(r1);
+    const float2 wx1 = make_float2(tx, tx), wx0 = make_float2(1.0f - tx, 1.0f - tx);
+    const float2 wy1 = make_float2(ty, ty), wy0 = make_float2(1.0f - ty, 1.0f - ty);
+    const float2 a = __ffma2_rn(v10, wx1, __fmul2_rn(v00, wx0));
+    const float2 b = __ffma2_rn(v11, wx1, __fmul2_rn(v01, wx0));
+    return __ffma2_rn(b, wy1, __fmul2_rn(a, wy0));
+}
+
+// a - b on a pair (b * -1 is exact, so the fused form rounds once, as a - b)
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+// HLL flux between (UL, GL) with speeds sL = (min, max) and (UR, GR), sR, as
+// Phi = al G_L + be G_R + ka (U_R - U_L) with al = l+/(l+ - l-), be =
+// -l-/(l+ - l-), ka = l+ l-/(l+ - l-) (the form of hll()); no wave across
+// the face gives al = be = 1/2, ka = 0, the mean of the two fluxes
+__device__ __forceinline__ float4 hll_face(const float4 &UL, const float4 &GL, float2 sL, const float4 &UR,
+                                           const float4 &GR, float2 sR)
+{
+    const float lp = fmaxf(fmaxf(sL.y, sR.y), 0.0f), lm = fminf(fminf(sL.x, sR.x), 0.0f);
+    const float den = lp - lm;
+    float al = 0.5f, be = 0.5f, ka = 0.0f;
+    if (den > 0.0f) {
+        const float r = rcp_approx(den);
+        al = lp * r;
+        be = -lm * r;
+        ka = (lp * lm) * r;
+    }
+    const float2 A = make_float2(al, al), Bv = make_float2(be, be), K = make_float2(ka, ka);
+    const float2 dlo = fsub2(lo2(UR), lo2(UL)), dhi = fsub2(hi2(UR), hi2(UL));
+    const float2 plo = __ffma2_rn(K, dlo, __ffma2_rn(Bv, lo2(GR), __fmul2_rn(A, lo2(GL))));
+    const float2 phi = __ffma2_rn(K, dhi, __ffma2_rn(Bv, hi2(GR), __fmul2_rn(A, hi2(GL))));
+    return f4(plo, phi);
+}
+
+// closure, flux vectors G_d = (F_d, P_d.) and speeds of one cell (the FP32
+// fast forms of closure() and hll_fz(); mu = F_d/|F|, 0 for F = 0).  ALL:
+// the speeds along x, y, z; otherwise along axis ax (0 = x, 1 = y) only,
+// in s[0]
+struct HllCell {
+    float4 G[3];
+    float2 s[3];
+};
+
+template <bool ALL>
+__device__ __forceinline__ void hll_cell(const float4 *__restrict__ tab, const V4<float> &u, int ax, HllCell &c)
+{
+    float P[6];
+    closure<float, false>(u, P);
+    c.G[0] = make_float4(u.y, P[0], P[1], P[2]);
+    c.G[1] = make_float4(u.z, P[1], P[3], P[4]);
+    c.G[2] = make_float4(u.w, P[2], P[4], P[5]);
+    float Fn, z;
+    hll_fz<float, false>(u, Fn, z);
+    const float x = z * (float)RTD_HLL_NF;
+    int i = (int)x;
+    i = i > RTD_HLL_NF - 1 ? RTD_HLL_NF - 1 : (i < 0 ? 0 : i);
+    const float tx = x - (float)i;
+    const float rF = Fn > 0.0f ? rcp_approx(Fn) : 0.0f;
+    if (ALL) {
+        c.s[0] = hll_pair(tab, i, tx, u.y * rF);
+        c.s[1] = hll_pair(tab, i, tx, u.z * rF);
+        c.s[2] = hll_pair(tab, i, tx, u.w * rF);
+    } else {
+        c.s[0] = hll_pair(tab, i, tx, (ax == 0 ? u.y : u.z) * rF);
+    }
+}
+
+template <int TX, int TY>
+struct TransportSmemHLL {
+    V4<float> U[TP_STAGES][TY + 2][TX + 2];
+    float4 Gx[2][TY + 2][TX + 2];      // G_x of two planes
+    float4 Gy[2][TY + 2][TX + 2];      // G_y of two planes
+    float2 Sx[2][TY + 2][TX + 2];      // (min, max) speeds along x of two planes
+    float2 Sy[2][TY + 2][TX + 2];      // along y
+};
+
+template <int TX, int TY>
+constexpr size_t transport_hll_smem_bytes() { return sizeof(TransportSmemHLL<TX, TY>); }
+
+// FP32 transport with the HLL flux.  Pipeline, work split and halos of
+// k_transport_pm; each cell's closure, flux vectors and speeds are evaluated
+// once per plane, the x/y ones shared through shared memory, the z ones kept
+// in registers, and the z-face flux carried from plane to plane.  Halo cells
+// evaluate the one axis their face needs; reflective halos keep their
+// negated state in shared memory (the flux reads U of both sides).  After the
+// update |F| <= N is restored as in k_transport.
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 3)
+k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
+{
+    static_assert(2 * TX + 2 * TY <= TX * TY, "one halo cell per thread at most");
+    constexpr int S = TP_STAGES;
+    extern __shared__ __align__(16) unsigned char tp_smem_raw[];
+    TransportSmemHLL<TX, TY> &sm = *reinterpret_cast<TransportSmemHLL<TX, TY> *>(tp_smem_raw);
+    const float4 *__restrict__ tab = ph.hll_f4;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
+
+    const int64_t ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
+    const int64_t uend = nunits * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    for (int64_t u = ubeg; u < uend;) {
+        const int b = find_box_unit(boxes, nboxes, u);
+        const BoxDev &B = boxes[b];
+        const int nx = B.nx, ny = B.ny, nz = B.nz;
+        const int64_t loc = u - B.titem0;
+        int64_t colid = loc / nz;
+        const int z0 = (int)(loc - colid * nz);
+        const int64_t zlim = (int64_t)z0 + (uend - u);
+        const int z1 = zlim < (int64_t)nz ? (int)zlim : nz;
+        u += z1 - z0;
+        const int ix = (int)(colid % B.tiles_x); colid /= B.tiles_x;
+        const int iy = (int)(colid % B.tiles_y);
+        const int g = (int)(colid / B.tiles_y);
+        const int x0 = ix * TX, y0 = iy * TY;
+        const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
+        const int x = x0 + tx, y = y0 + ty;
+        const bool act = (tx < ntx) && (ty < nty);
+        const int L = (z1 - z0) + 2;
+        const V4<float> *Ug = reinterpret_cast<const V4<float> *>(B.U) + (int64_t)g * B.ncell;
+        V4<float> *Og = reinterpret_cast<V4<float> *>(B.Us) + (int64_t)g * B.ncell;
+        const float lam = (float)B.lam;
+        const int64_t sxy = (int64_t)nx * ny;
+
+        // halo cell of this thread: 0 = left column, 1 = right, 2 = bottom
+        // row, 3 = top (its x or y face only)
+        int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0, hk = 0;
+        float hin = 0.0f;
+        bool hif = false;
+        {
+            int t = tid;
+            if (t < nty) {
+                hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1; hk = 0;
+                if (sx < 0) {
+                    if (ph.bc[0] == 0) sx = nx - 1;
+                    else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; }
+                    if (ph.bc[0] == 3) { hif = true; hin = (float)(ph.inflow_c[0][g] * B.inv_nunit); }
+                }
+            } else if ((t -= nty) < nty) {
+                hx = ntx + 1; hy = t + 1; sy = y0 + t; sx = x0 + ntx; hk = 1;
+                if (sx >= nx) {
+                    if (ph.bc[1] == 0) sx = 0;
+                    else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; }
+                    if (ph.bc[1] == 3) { hif = true; hin = -(float)(ph.inflow_c[1][g] * B.inv_nunit); }
+                }
+            } else if ((t -= nty) < ntx) {
+                hx = t + 1; hy = 0; sx = x0 + t; sy = y0 - 1; hk = 2;
+                if (sy < 0) { if (ph.bc[2] == 0) sy = ny - 1; else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; } }
+            } else if ((t -= ntx) < ntx) {
+                hx = t + 1; hy = nty + 1; sx = x0 + t; sy = y0 + nty; hk = 3;
+                if (sy >= ny) { if (ph.bc[3] == 0) sy = 0; else { sy = ny - 1; hneg = ph.bc[3] == 2 ? 2 : 0; } }
+            }
+        }
+        const V4<float> *gown = Ug + (int64_t)y * nx + x;
+        const V4<float> *ghalo = Ug + (int64_t)sy * nx + sx;
+        const bool zneg_first = z0 == 0 && ph.bc[4] == 2, zneg_last = z1 == nz && ph.bc[5] == 2;
+        int zi = z0 - 1;
+        int slot_i = 0;
+        auto issue = [&]() {
+            if (zi < z1 + 1) {
+                int zz = zi;
+                if (zz < 0) zz = ph.bc[4] == 0 ? nz - 1 : 0;
+                else if (zz >= nz) zz = ph.bc[5] == 0 ? 0 : nz - 1;
+                const int64_t pl = (int64_t)zz * sxy;
+                if (act) cp_async16(&sm.U[slot_i][ty + 1][tx + 1], gown + pl);
+                if (hx >= 0) {
+                    if (hif) sm.U[slot_i][hy][hx] = V4<float>{fabsf(hin), hin, 0.0f, 0.0f};
+                    else cp_async16(&sm.U[slot_i][hy][hx], ghalo + pl);
+                }
+            }
+            cp_async_commit();
+            zi++;
+            slot_i = slot_i + 1 == S ? 0 : slot_i + 1;
+        };
+#pragma unroll
+        for (int q = 0; q < S - 2; q++) issue();
+
+        float4 uc = {}, Gzc = {}, Fzm = {};   // plane q-1: state, G_z; flux of its lower z face
+        float2 szc = {};                      // its z speeds
+        V4<float> *out = Og + (int64_t)z0 * sxy + (int64_t)y * nx + x;
+        int slot = 0, slot_c = S - 1;         // ring slots of planes q and q-1
+        for (int q = 0; q < L; q++) {
+            cp_async_wait<S - 3>();
+            __syncthreads();
+            issue();
+            const int hs = q & 1;
+            const bool zneg = (q == 0 && zneg_first) || (q == L - 1 && zneg_last);
+            float4 un = {}, Gzn = {};
+            float2 szn = {};
+            if (act) {
+                V4<float> v = sm.U[slot][ty + 1][tx + 1];
+                if (zneg) v.w = -v.w;
+                HllCell hc;
+                hll_cell<true>(tab, v, 0, hc);
+                sm.Gx[hs][ty + 1][tx + 1] = hc.G[0];
+                sm.Gy[hs][ty + 1][tx + 1] = hc.G[1];
+                sm.Sx[hs][ty + 1][tx + 1] = hc.s[0];
+                sm.Sy[hs][ty + 1][tx + 1] = hc.s[1];
+                un = make_float4(v.x, v.y, v.z, v.w);
+                Gzn = hc.G[2];
+                szn = hc.s[2];
+            }
+            if (hx >= 0) {
+                V4<float> &hr = sm.U[slot][hy][hx];
+                V4<float> h = hr;
+                if (zneg) h.w = -h.w;
+                if (hneg == 1) h.y = -h.y;
+                else if (hneg == 2) h.z = -h.z;
+                if (hneg) hr = h;
+                const int ax = hk >> 1;
+                HllCell hc;
+                hll_cell<false>(tab, h, ax, hc);
+                if (ax == 0) {
+                    sm.Gx[hs][hy][hx] = hc.G[0];
+                    sm.Sx[hs][hy][hx] = hc.s[0];
+                } else {
+                    sm.Gy[hs][hy][hx] = hc.G[1];
+                    sm.Sy[hs][hy][hx] = hc.s[0];
+                }
+            }
+            if (act && q >= 1) {
+                const float4 Fzp = hll_face(uc, Gzc, szc, un, Gzn, szn);
+                if (q >= 2) {
+                    // update plane c = q - 1 (z = z0 + q - 2)
+                    const int cs = hs ^ 1;
+                    const float4 Gxc = sm.Gx[cs][ty + 1][tx + 1], Gyc = sm.Gy[cs][ty + 1][tx + 1];
+                    const float2 sxc = sm.Sx[cs][ty + 1][tx + 1], syc = sm.Sy[cs][ty + 1][tx + 1];
+                    float4 Fxm, Fxp, Fym, Fyp;
+                    {
+                        const V4<float> v = sm.U[slot_c][ty + 1][tx];
+                        const float2 s = sm.Sx[cs][ty + 1][tx];
+                        Fxm = hll_face(make_float4(v.x, v.y, v.z, v.w), sm.Gx[cs][ty + 1][tx], s, uc, Gxc, sxc);
+                    }
+                    {
+                        const V4<float> v = sm.U[slot_c][ty + 1][tx + 2];
+                        const float2 s = sm.Sx[cs][ty + 1][tx + 2];
+                        Fxp = hll_face(uc, Gxc, sxc, make_float4(v.x, v.y, v.z, v.w), sm.Gx[cs][ty + 1][tx + 2], s);
+                    }
+                    {
+                        const V4<float> v = sm.U[slot_c][ty][tx + 1];
+                        const float2 s = sm.Sy[cs][ty][tx + 1];
+                        Fym = hll_face(make_float4(v.x, v.y, v.z, v.w), sm.Gy[cs][ty][tx + 1], s, uc, Gyc, syc);
+                    }
+                    {
+                        const V4<float> v = sm.U[slot_c][ty + 2][tx + 1];
+                        const float2 s = sm.Sy[cs][ty + 2][tx + 1];
+                        Fyp = hll_face(uc, Gyc, syc, make_float4(v.x, v.y, v.z, v.w), sm.Gy[cs][ty + 2][tx + 1], s);
+                    }
+                    const float2 L2 = make_float2(-lam, -lam);
+                    const float2 dlo = __fadd2_rn(__fadd2_rn(fsub2(lo2(Fxp), lo2(Fxm)), fsub2(lo2(Fyp), lo2(Fym))),
+                                                  fsub2(lo2(Fzp), lo2(Fzm)));
+                    const float2 dhi = __fadd2_rn(__fadd2_rn(fsub2(hi2(Fxp), hi2(Fxm)), fsub2(hi2(Fyp), hi2(Fym))),
+                                                  fsub2(hi2(Fzp), hi2(Fzm)));
+                    const float2 olo = __ffma2_rn(L2, dlo, lo2(uc)), ohi = __ffma2_rn(L2, dhi, hi2(uc));
+                    float o0 = olo.x, o1 = olo.y, o2 = ohi.x, o3 = ohi.y;
+                    const float Fn = fsqrt<float, false>(o1 * o1 + o2 * o2 + o3 * o3);
+                    if (Fn > o0) {
+                        const float r = o0 > 0.0f ? o0 * rcp_approx(Fn) : 0.0f;
+                        o1 *= r;
+                        o2 *= r;
+                        o3 *= r;
+                    }
+                    st4(out, V4<float>{o0, o1, o2, o3});
+                    out += sxy;
+                }
+                Fzm = Fzp;
+            }
+            uc = un;
+            Gzc = Gzn;
+            szc = szn;
+            slot_c = slot;
             slot = slot + 1 == S ? 0 : slot + 1;
         }
         cp_async_wait<0>();

@@ -188,21 +188,22 @@ def test_upload_download_and_argument_errors():
     s.close()
 
 
+@pytest.mark.parametrize("flux", [0, 1])
 @pytest.mark.parametrize("shape,bc", [((33, 9, 40), [1, 1, 0, 0, 2, 2]), ((9, 33, 17), [0] * 6),
                                       ((16, 48, 48), [2, 1, 2, 1, 2, 1])])
-def test_transport_launch_shapes_are_bitwise_equal(shape, bc):
-    """Every launch shape of the FP32 transport (tile x resident blocks per
-    SM, rt_params.tune = 2 + k) gives the same bits as the default; the
-    tuner (tune = 1) picks one of them and reports it."""
+def test_transport_launch_shapes_are_bitwise_equal(shape, bc, flux):
+    """Every launch shape of the FP32 transport, GLF and HLL (tile x
+    resident blocks per SM, rt_params.tune = 2 + k) gives the same bits as
+    the default; the tuner (tune = 1) picks one of them and reports it."""
     G = 3
     w, st = _empty_workload(shape, G, bc, seed=sum(shape) + 5)
-    ref = run_gpu(w, 3, "split", None, st)[0][0]
+    ref = run_gpu(w, 3, "split", None, st, flux=flux)[0][0]
     assert ref[4] == B.RT_OK
     shapes = set()
     k = 0
     while True:
         try:
-            (out,), stats = run_gpu(w, 3, "split", None, st, tune=2 + k)
+            (out,), stats = run_gpu(w, 3, "split", None, st, tune=2 + k, flux=flux)
         except B.RTError as e:
             assert e.code == B.RT_ERR_ARG and k >= 3, (k, e)
             break
@@ -211,7 +212,7 @@ def test_transport_launch_shapes_are_bitwise_equal(shape, bc):
             np.testing.assert_array_equal(a, b)
         k += 1
     assert len({s[:2] for s in shapes}) == 3            # three tile shapes were run
-    (out,), stats = run_gpu(w, 3, "split", None, st, tune=1)
+    (out,), stats = run_gpu(w, 3, "split", None, st, tune=1, flux=flux)
     assert (stats.tile_x, stats.tile_y, stats.transport_grid) in shapes
     for a, b in zip(out[:3], ref[:3]):
         np.testing.assert_array_equal(a, b)

@@ -536,10 +536,12 @@ def peaks():
         return None
 
 
-def chem_flops_per_subcycle(G: int, ots: bool) -> float:
+def chem_flops_per_subcycle(G: int, ots: bool, split: bool = True) -> float:
     """Algorithmic FP64 flops of one accepted chemistry sub-cycle (a5-a8 and
-    the rate fits), counted from the formulas as written."""
-    return 22.0 * G + 111.0 - (14.0 if ots else 0.0)
+    the rate fits), counted from the formulas as written.  The split form
+    runs the photon update of each group (1 + c sigma x_HI n0 dtau: 4, (N + S
+    dtau)/den: 3, F/den: 3) in FP32, 10 G flops that are not FP64 work."""
+    return (12.0 if split else 22.0) * G + 111.0 - (14.0 if ots else 0.0)
 
 
 def main():
@@ -643,8 +645,10 @@ def main():
     # (lambda 1, alpha_A 7, alpha_B 7, recombination + free-free cooling 11,
     # beta 11, excitation cooling 6, k_C 2; OTS needs no alpha_A), the dtau
     # estimate 4 G + 19, the trial 18 G + 47 (7 of them the recombination
-    # photons of group 1 without OTS) -> 22 G + 111, against the FP64 pipe
-    # peak: 148 SMs x 2 DFMA/clock x 2 flop x 2032 MHz
+    # photons of group 1 without OTS) -> 22 G + 111; the split form's photon
+    # update (10 G of the trial's flops) runs in FP32 -> 12 G + 111 FP64
+    # flops, against the FP64 pipe peak: 148 SMs x 2 DFMA/clock x 2 flop x
+    # 2032 MHz
     fp64_peak = 148 * 2 * 2 * 2032e6 / 1e12
     c_flops = chem_flops_per_subcycle(G, w.ots) * box.ncell * mean_sub
     c_ach = c_flops / (per_launch["chemistry"] * 1e-3) / 1e12

@@ -361,6 +361,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
         ph.c = p->c_red;
         for (int i = 0; i < p->ngroups; i++) {
             ph.csig[i] = p->c_red * p->sigN[i];
+            ph.csig_f[i] = (float)ph.csig[i];
             ph.SigE[i] = p->sigE[i] * p->Eavg[i] - p->sigN[i] * (13.6 * rtd::EV);
         }
         ph.alphaA = p->alphaA;

@@ -58,6 +58,7 @@ struct Phys {
     int ots, isothermal, nsub, rates_const, max_halvings;
     double c;                     // reduced speed of light, cm/s
     double csig[RTD_MAXG];        // c * sigma_N,i
+    float csig_f[RTD_MAXG];       // the same rounded to FP32 (the split form's photon update)
     double SigE[RTD_MAXG];        // Sigma_E,i = sigma_E,i <E>_i - sigma_N,i E_13.6 (Sec. 2.2.4)
     double alphaA, alphaB, beta;  // rates_const values
     double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250

@@ -1307,6 +1307,7 @@ template <int G>
 struct Cell {
     double N[G], F[G][3];
     double xHI, T;
+    float n32[G];       // N in FP32 where the photon update runs in FP32 (N == n32 then)
 };
 
 // one trial of length dtau from s into o, in the paper's order
@@ -1379,29 +1380,49 @@ template <int G>
 struct CellK {
     double h[G];        // c nunit Sigma_E,i n0      (heating per stored N and neutral fraction)
     double n02, K, cvn; // n0^2, n0^2 / nunit, (3/2) kB n0
+    float n0f, S32[G];  // n0 and the source terms in FP32 (FP32 photon update)
 };
 
 // DEFER: F is not carried through the trial (nothing in the chemistry reads
-// it; it only scales by 1/den), the scale of each group goes to rd[] instead
-template <int G, bool DEFER>
+// it; it only scales by 1/den), the scale of each group goes to rd[] instead.
+// N32 (split form): the photon update of a5, N <- (N + S dtau)/(1 + c
+// sigma_N,i x_HI n0 dtau) and the scale of F, runs in FP32, the precision
+// N and F are stored in; x_HI, T, the rates and the photoionisation,
+// heating and cooling sums stay FP64
+template <int G, bool DEFER, bool N32, typename FT>
 __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B, const CellK<G> &k,
                                                 double n0, const double *S, const Rates &r,
                                                 double alpha, const Cell<G> &s, double e0,
-                                                double dtau, Cell<G> &o, double &e1, double *rdo)
+                                                double dtau, Cell<G> &o, double &e1, FT *rdo)
 {
     const double x = 1.0 - s.xHI;
-    const double q = s.xHI * n0 * dtau;
-    const double rec = ph.ots ? 0.0 : (r.aA - r.aB) * x * x * k.K;
+    if constexpr (N32) {
+        const float dt32 = d2f(dtau);
+        const float q32 = (d2f(s.xHI) * k.n0f) * dt32;
+        const float rec32 = ph.ots ? 0.0f : d2f((r.aA - r.aB) * x * x * k.K);
 #pragma unroll
-    for (int i = 0; i < G; i++) {
-        const double rd = rcp_nr(fma(ph.csig[i], q, 1.0));
-        const double src = (i == 0 && !ph.ots) ? S[i] + rec : S[i];
-        o.N[i] = fma(src, dtau, s.N[i]) * rd;
-        if (DEFER) {
+        for (int i = 0; i < G; i++) {
+            const float rd = __frcp_rn(fmaf(ph.csig_f[i], q32, 1.0f));
+            const float src = (i == 0 && !ph.ots) ? k.S32[i] + rec32 : k.S32[i];
+            const float n = fmaf(src, dt32, s.n32[i]) * rd;
+            o.n32[i] = n;
+            o.N[i] = f2d(n);
             rdo[i] = rd;
-        } else {
+        }
+    } else {
+        const double q = s.xHI * n0 * dtau;
+        const double rec = ph.ots ? 0.0 : (r.aA - r.aB) * x * x * k.K;
 #pragma unroll
-            for (int m = 0; m < 3; m++) o.F[i][m] = s.F[i][m] * rd;
+        for (int i = 0; i < G; i++) {
+            const double rd = rcp_nr(fma(ph.csig[i], q, 1.0));
+            const double src = (i == 0 && !ph.ots) ? S[i] + rec : S[i];
+            o.N[i] = fma(src, dtau, s.N[i]) * rd;
+            if (DEFER) {
+                rdo[i] = rd;
+            } else {
+#pragma unroll
+                for (int m = 0; m < 3; m++) o.F[i][m] = s.F[i][m] * rd;
+            }
         }
     }
     double gam = B.gN[0] * o.N[0];
@@ -1428,12 +1449,13 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
 // over the accepted trials is multiplied into fac[i] (the caller starts it
 // at 1 and applies it to F); otherwise F is updated in s and fac unused.
 // s <- o; F only when it is carried through the trials
-template <int G, bool F_TOO>
+template <int G, bool F_TOO, bool N32 = false>
 __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
 {
 #pragma unroll
     for (int i = 0; i < G; i++) {
         s.N[i] = o.N[i];
+        if (N32) s.n32[i] = o.n32[i];
         if (F_TOO) {
 #pragma unroll
             for (int m = 0; m < 3; m++) s.F[i][m] = o.F[i][m];
@@ -1443,12 +1465,13 @@ __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
     s.T = o.T;
 }
 
-template <int G, bool STRICT, class Trace = NoTrace>
+template <int G, bool STRICT, class Trace = NoTrace, typename FT = double>
 __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,
-                                  int &ncyc, Trace *tr = nullptr, double *fac = nullptr)
+                                  int &ncyc, Trace *tr = nullptr, FT *fac = nullptr)
 {
     constexpr bool DEFER = !STRICT && std::is_same<Trace, NoTrace>::value;
+    constexpr bool N32 = DEFER && std::is_same<FT, float>::value;
     unsigned int err = 0;
     double tau = 0.0;
     CellK<G> k;
@@ -1460,6 +1483,15 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         k.n02 = n0 * n0;
         k.K = k.n02 * B.inv_nunit;
         k.cvn = (1.5 * rtd::KB) * n0;
+    }
+    if (N32) {
+        k.n0f = d2f(n0);
+#pragma unroll
+        for (int i = 0; i < G; i++) {
+            k.S32[i] = d2f(S[i]);
+            s.n32[i] = d2f(s.N[i]);
+            s.N[i] = f2d(s.n32[i]);
+        }
     }
     for (;;) {
         const double rem = span - tau;
@@ -1502,19 +1534,20 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
             }
         }
         Cell<G> o;
-        double ep, e1, rd[G];
+        double ep, e1;
+        FT rd[G];
         for (int h = 0;; h++) {
             if (STRICT) {
                 chem_trial<G, true>(ph, B.nunit, B.inv_nunit, n0, S, r, alpha, s, dtau, o, ep, e1);
             } else {
                 ep = ep0;
-                chem_trial_fast<G, DEFER>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd);
+                chem_trial_fast<G, DEFER, N32, FT>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd);
             }
             if (ph.isothermal) break;
             const bool finite = STRICT ? isfinite(e1)
                                        : (dbits(e1) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
             if (!finite) {                  // no amount of halving repairs a NaN/Inf
-                take<G, !DEFER>(s, o);
+                take<G, !DEFER, N32>(s, o);
                 ncyc++;
                 return err | RTD_ERR_NONFINITE;
             }
@@ -1529,7 +1562,7 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
 #pragma unroll
             for (int i = 0; i < G; i++) fac[i] *= rd[i];
         }
-        take<G, !DEFER>(s, o);
+        take<G, !DEFER, N32>(s, o);
         ncyc++;
         if (last) break;
         tau = tau + dtau;
@@ -1715,13 +1748,16 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             bool gross = false;
             // fast forms: F stays in the stored precision and is scaled once
             // at the end (read again from U*) by the product of its per-trial
-            // factors (fac)
-            double fac[G];
+            // factors (fac), formed in that precision (FP32 photon update of
+            // the split form)
+            using FT = typename std::conditional<!STRICT && std::is_same<TU, float>::value, float,
+                                                 double>::type;
+            FT fac[G];
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
                 s.N[i] = to_d(u.x);
-                fac[i] = 1.0;
+                fac[i] = FT(1);
                 if (STRICT) {
                     s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
                 }
@@ -1769,14 +1805,14 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (ph.nsub > 0) {
                 const double h = span / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
+                    err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
             } else {
-                err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
+                err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
             }
             if (ph.cosmo) {
                 cosmo_out<G, STRICT>(ca, ca1, s);
                 if (!STRICT) {
-                    const double fr = ca / ca1;
+                    const FT fr = from_d<FT>(ca / ca1);
 #pragma unroll
                     for (int i = 0; i < G; i++) fac[i] = fac[i] * fr;
                 }
@@ -1792,7 +1828,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 if (STRICT) {
                     o.y = from_d<TU>(s.F[i][0]); o.z = from_d<TU>(s.F[i][1]); o.w = from_d<TU>(s.F[i][2]);
                 } else {
-                    const TU fi = from_d<TU>(fac[i]);
+                    const TU fi = (TU)fac[i];          // FT is TU in the fast forms
                     const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
                     o.y = u.y * fi; o.z = u.z * fi; o.w = u.w * fi;
                 }
@@ -1895,12 +1931,14 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         const int64_t c = F.parent[f];
         const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
         Cell<G> s;
-        double fac[G];                 // the refined cell's radiation is not kept
+        // the refined cell's radiation is not kept (fac only as in k_chem)
+        using FT = typename std::conditional<!STRICT && std::is_same<TU, float>::value, float, double>::type;
+        FT fac[G];
 #pragma unroll
         for (int i = 0; i < G; i++) {
             const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
             s.N[i] = to_d(u.x);
-            fac[i] = 1.0;
+            fac[i] = FT(1);
             if (STRICT) {
                 s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
             }
@@ -1928,9 +1966,9 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         if (ph.nsub > 0) {
             const double h = span / ph.nsub;
             for (int q = 0; q < ph.nsub; q++)
-                err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
+                err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
         } else {
-            err |= chem_span<G, STRICT, NoTrace>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
+            err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
         }
         if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
         if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;

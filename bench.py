@@ -427,6 +427,7 @@ def hll_run(K=3):
     return {"value": w.cells * w.steps * K / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms / K,
             "transport_ms_per_launch": t_ms,
             "transport_gbs": 32.0 * w.ngroups * w.cells / (t_ms * 1e-3) / 1e9,
+            "transport_traffic": profiled_traffic().get("transport_hll"),
             "chemistry_ms_per_launch": st.kernel_ms[1] / max(st.kernel_launches[1], 1)}
 
 

@@ -56,6 +56,7 @@ struct rt_handle {
     std::vector<std::vector<int>> src_uidx;  // per box: unique-table index of each given source
     std::vector<double *> d_src_S;
     rtd::DiagPart *d_partials = nullptr;
+    double *d_lanes = nullptr;               // per-item lane values of the FP64 diagnostics
     unsigned *d_done = nullptr;              // per-box group counters of the fused reduction
     rtd::DiagPart *d_gpart = nullptr;        // per-group partials
     unsigned *d_gdone = nullptr;             // per-group item counters
@@ -121,6 +122,7 @@ static void release(rt_handle *h)
     for (auto *p : h->d_src_S) cudaFree(p);
     cudaFree(h->d_boxes);
     cudaFree(h->d_partials);
+    cudaFree(h->d_lanes);
     cudaFree(h->d_done);
     cudaFree(h->d_gpart);
     cudaFree(h->d_gdone);
@@ -423,6 +425,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * nboxes,
                                  cudaMemcpyHostToDevice));
                 CU(h, cudaMalloc(&h->d_partials, sizeof(rtd::DiagPart) * citem));
+                CU(h, cudaMalloc(&h->d_lanes, sizeof(double) * 2 * RTD_CHEM_ITEM * citem));
                 CU(h, cudaMalloc(&h->d_gpart, sizeof(rtd::DiagPart) * cgroup));
                 CU(h, cudaMalloc(&h->d_gdone, sizeof(unsigned) * cgroup));
                 CU(h, cudaMemset(h->d_gdone, 0, sizeof(unsigned) * cgroup));
@@ -579,7 +582,7 @@ static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = 
 {
     rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s, h->tvariant};
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
-    const rtd::DiagBuf db{h->d_partials, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
+    const rtd::DiagBuf db{h->d_partials, h->d_lanes, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     e = h->strict ? rtl::transport_strict(Lt, h->zc, h->ph, h->d_ctl)

@@ -103,7 +103,8 @@ struct DiagPart {
     unsigned long long count, ncyc;   // cells with xHI < 0.5, chemistry sub-cycles
 };
 struct DiagBuf {
-    DiagPart *part;                   // one per chemistry work item
+    DiagPart *part;                   // one per chemistry work item (X, ph unused)
+    double *lane;                     // per work item: its 32 lanes' (1 - xHI), then their photons
     DiagPart *gpart;                  // one per group of RTD_CHEM_GROUP items
     unsigned *gdone;                  // per group: items finished in this step
     unsigned *done;                   // per box: groups finished in this step

@@ -1687,6 +1687,39 @@ __device__ __forceinline__ DiagAcc warp_sum_parts(const DiagPart *p, int64_t n)
     return warp_reduce_diag(a);
 }
 
+// the integer fields of a work item (max, counts) across the warp, result in
+// lane 0; the FP64 sums of an item are not reduced here (lane values)
+__device__ __forceinline__ DiagAcc warp_reduce_ints(DiagAcc a)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long f = __shfl_down_sync(0xffffffffu, a.fbits, off);
+        a.fbits = f > a.fbits ? f : a.fbits;
+        a.count += __shfl_down_sync(0xffffffffu, a.count, off);
+        a.ncyc += __shfl_down_sync(0xffffffffu, a.ncyc, off);
+    }
+    return a;
+}
+
+// Sum of a group of n work items by one warp: the integer fields from the
+// items' partials, the FP64 sums from their lane values (lane l adds slot l
+// of every item in item order), then the fixed tree; result in lane 0.  The
+// per-item FP64 sums thus cost n adds per lane instead of a tree per item.
+__device__ __forceinline__ DiagAcc group_sum(const DiagPart *p, const double *lanev, int64_t n)
+{
+    const int l = threadIdx.x & 31;
+    DiagAcc a = {0.0, 0.0, 0ull, 0ull, 0ull};
+    for (int64_t i = l; i < n; i += 32) diag_add(a, load_part(p + i));
+    double x = 0.0, ph = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        x += __ldcg(lanev + j * (2 * RTD_CHEM_ITEM) + l);
+        ph += __ldcg(lanev + j * (2 * RTD_CHEM_ITEM) + RTD_CHEM_ITEM + l);
+    }
+    a.X = x;
+    a.ph = ph;
+    return warp_reduce_diag(a);
+}
+
 // All groups of box b are reduced: sum the group partials in a fixed order
 // and write the step's diagnostics (ionised fraction, photons, max f,
 // n(xHI < 0.5), mean sub-cycles) into lastdiag and the caller's history.
@@ -1846,10 +1879,17 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             v.X = 1.0 - s.xHI;
             v.ph = ph_tot;
             v.fbits = (unsigned long long)__double_as_longlong(to_d(sqrt(f2max)));
-            v.count = s.xHI < 0.5 ? 1ull : 0ull;
+            // xHI < 0.5 on the integer pipe: doubles order like their bits
+            // as signed integers (negative values below every positive one)
+            v.count = (long long)dbits(s.xHI) < (long long)dbits(0.5) ? 1ull : 0ull;
             v.ncyc = (unsigned long long)ncyc;
         }
-        v = warp_reduce_diag(v);
+        // FP64 sums: each lane's values go to the item's fixed slots (summed
+        // per group); the integer fields are reduced across the warp
+        db.lane[it * (2 * RTD_CHEM_ITEM) + lane] = v.X;
+        db.lane[it * (2 * RTD_CHEM_ITEM) + RTD_CHEM_ITEM + lane] = v.ph;
+        __threadfence();
+        v = warp_reduce_ints(v);
         const int64_t gl = li / RTD_CHEM_GROUP;           // group within the box
         int last_group = 0;
         if (lane == 0) {
@@ -1864,7 +1904,8 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             __threadfence();
             const int64_t first = B.citem0 + gl * RTD_CHEM_GROUP;
             const int64_t left = B.ncitems - gl * RTD_CHEM_GROUP;
-            const DiagAcc g = warp_sum_parts(db.part + first, left < RTD_CHEM_GROUP ? left : RTD_CHEM_GROUP);
+            const DiagAcc g = group_sum(db.part + first, db.lane + first * (2 * RTD_CHEM_ITEM),
+                                        left < RTD_CHEM_GROUP ? left : RTD_CHEM_GROUP);
             int last_box = 0;
             if (lane == 0) {
                 store_part(db.gpart + B.cgroup0 + gl, g);

@@ -120,6 +120,12 @@ __host__ __device__ __forceinline__ float d2f(double d)
     return (float)d;
 }
 
+// finite (not NaN or Inf) from the exponent bits, on the integer pipe
+__host__ __device__ __forceinline__ bool finite_bits(double d)
+{
+    return (dbits(d) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
 template <typename R> __device__ __forceinline__ double to_d(R v);
 template <> __device__ __forceinline__ double to_d<float>(float v) { return f2d(v); }
 template <> __device__ __forceinline__ double to_d<double>(double v) { return v; }
@@ -1266,6 +1272,7 @@ __device__ __forceinline__ double tab_poly(const double *c, double t)
 // exact, and below RTD_TAB_TCUT, where both factors are exactly zero in
 // double, they are not evaluated.  Outside 1 K .. 2^30 K the fits are
 // evaluated directly.
+template <bool STRICT>
 __device__ __forceinline__ Rates rates_tab(const Phys &ph, const double *tab, double T)
 {
     int j;
@@ -1277,7 +1284,7 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const double *tab, do
     r.aA = ph.ots ? r.aB : tab_poly(a, t);
     r.kR = tab_poly(a + 2 * RTD_TAB_NC, t);
     if (dbits(T) >= dbits(RTD_TAB_TCUT)) {       // T >= TCUT (both positive)
-        const double invT = 1.0 / T;
+        const double invT = STRICT ? 1.0 / T : rcp_nr(T);
         r.beta = exp(tab_poly(a + 3 * RTD_TAB_NC, t) - rtd::T_HI * invT);
         const double cce = exp(tab_poly(a + 4 * RTD_TAB_NC, t) - 118348.0 * invT);
         r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
@@ -1495,7 +1502,7 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
     }
     for (;;) {
         const double rem = span - tau;
-        const Rates r = tab ? rates_tab(ph, tab, s.T) : rates_at(ph, s.T);
+        const Rates r = tab ? rates_tab<STRICT>(ph, tab, s.T) : rates_at(ph, s.T);
         const double alpha = ph.ots ? r.aB : r.aA;
         double dtau = rem;
         bool last = true;
@@ -1544,8 +1551,7 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
                 chem_trial_fast<G, DEFER, N32, FT>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd);
             }
             if (ph.isothermal) break;
-            const bool finite = STRICT ? isfinite(e1)
-                                       : (dbits(e1) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+            const bool finite = STRICT ? isfinite(e1) : finite_bits(e1);
             if (!finite) {                  // no amount of halving repairs a NaN/Inf
                 take<G, !DEFER, N32>(s, o);
                 ncyc++;
@@ -1850,7 +1856,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                     for (int i = 0; i < G; i++) fac[i] = fac[i] * fr;
                 }
             }
-            if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
+            if (!finite_bits(s.xHI) || !finite_bits(s.T)) err |= RTD_ERR_NONFINITE;
             if (err) atomicOr(&ctl->err, err);
             double ph_tot = 0.0;
             TU f2max = TU(0);                  // largest |F/N|^2 of the cell's groups
@@ -2012,7 +2018,7 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
             err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
         }
         if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
-        if (!isfinite(s.xHI) || !isfinite(s.T)) err |= RTD_ERR_NONFINITE;
+        if (!finite_bits(s.xHI) || !finite_bits(s.T)) err |= RTD_ERR_NONFINITE;
         if (err) atomicOr(&ctl->err, err);
         F.xHI[f] = s.xHI;
         F.T[f] = s.T;

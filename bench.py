@@ -680,7 +680,7 @@ def main():
             "config": {"workload": w.name + " (lognormal sigma=1, P~k^-2, 64 sources, 3 groups "
                                             "5e4 K BB, c/10, T evolving, adaptive chemistry)",
                        "cells": box.ncell, "rt_steps_per_bench_step": nsteps,
-                       "form": "split: FP32 transport + FP64 chemistry",
+                       "form": "split: FP32 transport + FP64 chemistry (x_HI, T, rates, sums; photon update in FP32)",
                        "l2": f"inputs larger than L2 (resident state {state_bytes / 1e6:.0f} MB)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "roofline_transport": roof_t,

@@ -748,7 +748,7 @@ constexpr size_t transport_pm_smem_bytes() { return sizeof(TransportSmemPM<TX, T
 // one thread each) is a template parameter so the launch shape can be tuned
 // per box set; every shape computes each cell with the same arithmetic.
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
+__global__ void __launch_bounds__(TX *TY, 3)
 k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
 {
     static_assert(2 * TX + 2 * TY <= TX * TY, "one halo cell per thread at most");
@@ -822,12 +822,14 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         const bool zneg_first = z0 == 0 && ph.bc[4] == 2, zneg_last = z1 == nz && ph.bc[5] == 2;
         int zi = z0 - 1;                          // plane of the next issue
         int slot_i = 0;                           // its ring slot
+        // offset of plane zi inside the box (advanced by one plane per
+        // issue) and of the two ghost planes
+        int64_t pl_in = (int64_t)zi * sxy;
+        const int64_t pl_lo = ph.bc[4] == 0 ? (int64_t)(nz - 1) * sxy : 0;
+        const int64_t pl_hi = ph.bc[5] == 0 ? 0 : (int64_t)(nz - 1) * sxy;
         auto issue = [&]() {
             if (zi < z1 + 1) {
-                int zz = zi;
-                if (zz < 0) zz = ph.bc[4] == 0 ? nz - 1 : 0;
-                else if (zz >= nz) zz = ph.bc[5] == 0 ? 0 : nz - 1;
-                const int64_t pl = (int64_t)zz * sxy;
+                const int64_t pl = zi < 0 ? pl_lo : (zi >= nz ? pl_hi : pl_in);
                 if (act) cp_async16(&sm.U[slot_i][ty + 1][tx + 1], gown + pl);
                 if (hx >= 0) {
                     if (hif) sm.U[slot_i][hy][hx] = V4<float>{fabsf(hin), hin, 0.0f, 0.0f};
@@ -836,6 +838,7 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
             }
             cp_async_commit();
             zi++;
+            pl_in += sxy;
             slot_i = slot_i + 1 == S ? 0 : slot_i + 1;
         };
 #pragma unroll
@@ -845,6 +848,7 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         float4 Rz_prev = {}, Rz_c = {};     // right-going z halves of planes q-2 and q-1
         V4<float> *out = Og + (int64_t)z0 * sxy + (int64_t)y * nx + x;
         int slot = 0;                       // ring slot of plane q
+#pragma unroll 3
         for (int q = 0; q < L; q++) {
             cp_async_wait<S - 3>();
             __syncthreads();

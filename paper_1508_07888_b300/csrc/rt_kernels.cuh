@@ -1080,12 +1080,12 @@ k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, in
         const bool zneg_first = z0 == 0 && ph.bc[4] == 2, zneg_last = z1 == nz && ph.bc[5] == 2;
         int zi = z0 - 1;
         int slot_i = 0;
+        int64_t pl_in = (int64_t)zi * sxy;       // plane zi's offset, and the ghost planes'
+        const int64_t pl_lo = ph.bc[4] == 0 ? (int64_t)(nz - 1) * sxy : 0;
+        const int64_t pl_hi = ph.bc[5] == 0 ? 0 : (int64_t)(nz - 1) * sxy;
         auto issue = [&]() {
             if (zi < z1 + 1) {
-                int zz = zi;
-                if (zz < 0) zz = ph.bc[4] == 0 ? nz - 1 : 0;
-                else if (zz >= nz) zz = ph.bc[5] == 0 ? 0 : nz - 1;
-                const int64_t pl = (int64_t)zz * sxy;
+                const int64_t pl = zi < 0 ? pl_lo : (zi >= nz ? pl_hi : pl_in);
                 if (act) cp_async16(&sm.U[slot_i][ty + 1][tx + 1], gown + pl);
                 if (hx >= 0) {
                     if (hif) sm.U[slot_i][hy][hx] = V4<float>{fabsf(hin), hin, 0.0f, 0.0f};
@@ -1094,6 +1094,7 @@ k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, in
             }
             cp_async_commit();
             zi++;
+            pl_in += sxy;
             slot_i = slot_i + 1 == S ? 0 : slot_i + 1;
         };
 #pragma unroll
@@ -1103,6 +1104,7 @@ k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, in
         float2 szc = {};                      // its z speeds
         V4<float> *out = Og + (int64_t)z0 * sxy + (int64_t)y * nx + x;
         int slot = 0, slot_c = S - 1;         // ring slots of planes q and q-1
+#pragma unroll 2
         for (int q = 0; q < L; q++) {
             cp_async_wait<S - 3>();
             __syncthreads();

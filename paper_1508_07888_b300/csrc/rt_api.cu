@@ -365,6 +365,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
             ph.csig[i] = p->c_red * p->sigN[i];
             ph.csig_f[i] = (float)ph.csig[i];
             ph.SigE[i] = p->sigE[i] * p->Eavg[i] - p->sigN[i] * (13.6 * rtd::EV);
+            ph.hK[i] = (float)std::fabs(p->c_red * ph.SigE[i] / (1.5 * rtd::KB));
         }
         ph.alphaA = p->alphaA;
         ph.alphaB = p->alphaB;
@@ -397,6 +398,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     D.dx = B.dx;
                     D.nunit = B.nunit;
                     D.inv_nunit = 1.0 / B.nunit;
+                    D.nunit_f = (float)B.nunit;
                     for (int i = 0; i < RTD_MAXG; i++) {
                         D.gN[i] = i < G ? h->ph.csig[i] * B.nunit : 0.0;
                         D.hN[i] = i < G ? h->ph.c * B.nunit * h->ph.SigE[i] : 0.0;

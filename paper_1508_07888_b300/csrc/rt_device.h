@@ -59,6 +59,7 @@ struct Phys {
     double c;                     // reduced speed of light, cm/s
     double csig[RTD_MAXG];        // c * sigma_N,i
     float csig_f[RTD_MAXG];       // the same rounded to FP32 (the split form's photon update)
+    float hK[RTD_MAXG];           // |c Sigma_E,i| / (1.5 kB) in FP32 (the chemistry's FP32 pre-test)
     double SigE[RTD_MAXG];        // Sigma_E,i = sigma_E,i <E>_i - sigma_N,i E_13.6 (Sec. 2.2.4)
     double alphaA, alphaB, beta;  // rates_const values
     double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250
@@ -90,6 +91,7 @@ struct BoxDev {
     const int64_t *src_cell;          // sorted unique source cells (nsrc)
     const double *src_S;              // [nsrc][G] source term, stored units per second
     int nsrc;
+    float nunit_f;                    // nunit in FP32 (the chemistry's FP32 pre-test)
     int64_t titem0, ntitems;          // transport plane units of this box (prefix, count)
     int64_t citem0, ncitems;          // chemistry work items (32 cells) of this box
     int64_t cgroup0, ncgroups;        // diagnostics groups (64 items) of this box

@@ -1497,8 +1497,8 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         k.K = k.n02 * B.inv_nunit;
         k.cvn = (1.5 * rtd::KB) * n0;
     }
+    if (!STRICT) k.n0f = d2f(n0);
     if (N32) {
-        k.n0f = d2f(n0);
 #pragma unroll
         for (int i = 0; i < G; i++) {
             k.S32[i] = d2f(S[i]);
@@ -1514,7 +1514,28 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         bool last = true;
         // e^p (the fast forms reuse it in every trial of this sub-cycle)
         const double ep0 = STRICT ? 0.0 : k.cvn * (2.0 - s.xHI) * s.T;
-        if (!ph.isothermal && use_est) {
+        // FP32 pre-test of the estimate's skip (fast forms).  heat and
+        // cooling are >= 0, so |rate| <= heat + cool, and q = rem (heat +
+        // cool) / e is a sum of products of non-negative FP32 numbers in which
+        // n0 and kB cancel (each a few ulp; an underflowed term is below any
+        // part of q that matters); 1 - x_HI comes from its FP64 value.  q <=
+        // 0.999 therefore implies |e| >= rem |rate| (1 + 1e-13), the skip the
+        // FP64 test below takes, which is then not evaluated: the decisions,
+        // and the results, are those of the FP64 test
+        bool pre_skip = false;
+        if (!STRICT && !ph.isothermal && use_est) {
+            const float xh = fabsf(d2f(s.xHI)), xl = fabsf(d2f(1.0 - s.xHI));
+            float hsum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < G; i++) hsum = fmaf(ph.hK[i], fabsf(d2f(s.N[i])), hsum);
+            constexpr float KB15I = (float)(1.0 / (1.5 * rtd::KB));
+            const float kr = fabsf(d2f(r.kR)) * KB15I, kc = fabsf(d2f(r.kC)) * KB15I;
+            const float cool = (k.n0f * xl) * fmaf(xl, kr, xh * kc);
+            const float q = (d2f(rem) * fmaf(xh * B.nunit_f, hsum, cool)) *
+                            __frcp_rn((2.0f - xh) * d2f(s.T));
+            pre_skip = q >= 0.0f && q <= 0.999f;
+        }
+        if (!ph.isothermal && use_est && !pre_skip) {
             double rate, e;
             if (STRICT) {
                 double heat = 0.0;

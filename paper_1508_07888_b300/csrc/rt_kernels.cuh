@@ -1391,8 +1391,7 @@ struct NoTrace {
 // chem_trial to a few ulp.
 template <int G>
 struct CellK {
-    double h[G];        // c nunit Sigma_E,i n0      (heating per stored N and neutral fraction)
-    double n02, K, cvn; // n0^2, n0^2 / nunit, (3/2) kB n0
+    double n02, K, cvn; // n0^2, n0^2 / nunit (without OTS), (3/2) kB n0
     float n0f, S32[G];  // n0 and the source terms in FP32 (FP32 photon update)
 };
 
@@ -1449,12 +1448,12 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
         e1 = e0;
         return;
     }
-    double hs = k.h[0] * o.N[0];
+    double hs = B.hN[0] * o.N[0];            // heating per neutral atom / n0
 #pragma unroll
-    for (int i = 1; i < G; i++) hs = fma(k.h[i], o.N[i], hs);
+    for (int i = 1; i < G; i++) hs = fma(B.hN[i], o.N[i], hs);
     const double x1 = 1.0 - o.xHI;
     const double cool = k.n02 * x1 * fma(x1, r.kR, o.xHI * r.kC);   // Lambda(n0, x^{p+1}, T^p)
-    e1 = fma(dtau, fma(o.xHI, hs, -cool), e0);
+    e1 = fma(dtau, fma(o.xHI * n0, hs, -cool), e0);
     o.T = e1 * rcp_nr(k.cvn * (2.0 - o.xHI));
 }
 
@@ -1489,12 +1488,8 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
     double tau = 0.0;
     CellK<G> k;
     if (!STRICT) {
-#pragma unroll
-        for (int i = 0; i < G; i++) {
-            k.h[i] = B.hN[i] * n0;
-        }
         k.n02 = n0 * n0;
-        k.K = k.n02 * B.inv_nunit;
+        k.K = ph.ots ? 0.0 : k.n02 * B.inv_nunit;
         k.cvn = (1.5 * rtd::KB) * n0;
     }
     if (!STRICT) k.n0f = d2f(n0);
@@ -1506,8 +1501,8 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
             s.N[i] = f2d(s.n32[i]);
         }
     }
+    double rem = span;                          // span - tau, tau = 0 in the first sub-cycle
     for (;;) {
-        const double rem = span - tau;
         const Rates r = tab ? rates_tab<STRICT>(ph, tab, s.T) : rates_at(ph, s.T);
         const double alpha = ph.ots ? r.aB : r.aA;
         double dtau = rem;
@@ -1545,9 +1540,10 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
                 rate = heat - cooling(r, n0, s.xHI);
                 e = eint(s.xHI, n0, s.T);
             } else {
-                double hs = k.h[0] * s.N[0];
+                double hs = B.hN[0] * s.N[0];
 #pragma unroll
-                for (int i = 1; i < G; i++) hs = fma(k.h[i], s.N[i], hs);
+                for (int i = 1; i < G; i++) hs = fma(B.hN[i], s.N[i], hs);
+                hs = hs * n0;
                 const double x = 1.0 - s.xHI;
                 rate = fma(s.xHI, hs, -(k.n02 * x * fma(x, r.kR, s.xHI * r.kC)));
                 e = ep0;
@@ -1599,6 +1595,7 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         ncyc++;
         if (last) break;
         tau = tau + dtau;
+        rem = span - tau;
         if (ncyc >= RTD_MAXCYC) { err |= RTD_ERR_SUBCYCLE; break; }
     }
     return err;
@@ -1899,7 +1896,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                     o.y = u.y * fi; o.z = u.z * fi; o.w = u.w * fi;
                 }
                 st4(U + (int64_t)i * B.ncell + c, o);
-                ph_tot += to_d(o.x);
+                ph_tot = i == 0 ? to_d(o.x) : ph_tot + to_d(o.x);
                 if (o.x > flux_nmin<TU>()) {
                     const TU rn = TU(1) / o.x;
                     const TU ux = o.y * rn, uy = o.z * rn, uz = o.w * rn;

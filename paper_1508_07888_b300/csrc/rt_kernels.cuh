@@ -715,15 +715,13 @@ __device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
         P0 = gx * ux + Na; P3 = gy * uy + Na; P5 = gz * uz + Na;
         P1 = gx * uy; P2 = gx * uz; P4 = gy * uz;
     }
-    const float2 ulo = make_float2(u.x, u.y), uhi = make_float2(u.z, u.w);
-    const float2 m1 = make_float2(-1.0f, -1.0f);
-    const float2 G[3][2] = {{make_float2(u.y, P0), make_float2(P1, P2)},
-                            {make_float2(u.z, P1), make_float2(P3, P4)},
-                            {make_float2(u.w, P2), make_float2(P4, P5)}};
+    // scalar adds: the flux vectors' components are not aligned register
+    // pairs, so packed adds would need moves to assemble them (same rounding)
+    const float G[3][4] = {{u.y, P0, P1, P2}, {u.z, P1, P3, P4}, {u.w, P2, P4, P5}};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        h.R[d] = f4(__fadd2_rn(ulo, G[d][0]), __fadd2_rn(uhi, G[d][1]));
-        h.L[d] = f4(__ffma2_rn(G[d][0], m1, ulo), __ffma2_rn(G[d][1], m1, uhi));
+        h.R[d] = make_float4(u.x + G[d][0], u.y + G[d][1], u.z + G[d][2], u.w + G[d][3]);
+        h.L[d] = make_float4(u.x - G[d][0], u.y - G[d][1], u.z - G[d][2], u.w - G[d][3]);
     }
 }
 

@@ -728,9 +728,13 @@ __device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
+// the FP32 GLF kernel streams one plane deeper than the others (4 planes
+// ahead): it is the one bound by DRAM latency
+constexpr int TP_STAGES_PM = 6;
+
 template <int TX, int TY>
 struct TransportSmemPM {
-    V4<float> U[TP_STAGES][TY + 2][TX + 2];
+    V4<float> U[TP_STAGES_PM][TY + 2][TX + 2];
     float4 H[2][4][TY + 2][TX + 2];    // per cell: Rx, Lx, Ry, Ly of two planes
 };
 
@@ -750,7 +754,7 @@ __global__ void __launch_bounds__(TX *TY, 3)
 k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
 {
     static_assert(2 * TX + 2 * TY <= TX * TY, "one halo cell per thread at most");
-    constexpr int S = TP_STAGES;
+    constexpr int S = TP_STAGES_PM;
     extern __shared__ __align__(16) unsigned char tp_smem_raw[];
     TransportSmemPM<TX, TY> &sm = *reinterpret_cast<TransportSmemPM<TX, TY> *>(tp_smem_raw);
 

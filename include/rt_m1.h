@@ -105,13 +105,17 @@ typedef struct rt_params {
     int    bc[6];                        /* faces -x,+x,-y,+y,-z,+z, rt_bc values */
     int    max_halvings;                 /* cap of the 10% rule (e.g. 30) */
     int    precision;                    /* rt_precision */
-    int    tune;                         /* launch shape of the SPLIT form's transport (tile and
-                                            resident blocks per SM; the results do not depend
-                                            on it): 0 = default, 1 = time every shape at
-                                            rt_create on a synthetic state in scratch and keep
-                                            the fastest (cached per device and box set for the
-                                            process), 2 + k = shape k; ignored by the FP64 forms
-                                            and by the HLL flux */
+    int    tune;                         /* launch shape of the SPLIT form's transport, GLF or
+                                            HLL (tile and grid; the results do not depend on
+                                            it): 0 = default, 1 = time every shape at rt_create
+                                            on a synthetic state in scratch and keep the
+                                            fastest (cached per device, flux and box set for
+                                            the process), 2 + k = shape k: k = 3 t + (b - 1)
+                                            for tile t (32x8, 16x16, 64x4) at b = 1..3 resident
+                                            blocks per SM (capped by what fits), k = 9 + 2 t +
+                                            (j - 1) for tile t at j = 1, 2 blocks per tile
+                                            column; k >= 15 is RT_ERR_ARG.  Ignored by the
+                                            FP64 forms */
     int    flux;                         /* rt_flux; rt_adjoint and rt_transport_static need GLF */
     double inflow[6];                    /* photons/cm^2/s entering through each RT_BC_INFLOW face */
     int    cosmo;                        /* 1: supercomoving units (Sec. 3).  U holds the comoving

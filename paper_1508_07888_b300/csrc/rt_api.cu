@@ -200,18 +200,24 @@ extern "C" double rt_timestep(const rt_params *p, double dx)
 }
 
 // ------------------------------------------------------------------ tuner
-// Launch shape of the FP32 transport: tile (rtl::kTileX/Y) x resident blocks
-// per SM.  Every candidate computes each cell with the same arithmetic, so
-// the choice changes the time only.  tune = 1 times every candidate on the
-// handle's boxes (on a synthetic realizable state in scratch, so the
-// caller's state is not touched) and keeps the fastest; the choice is cached
-// per device, group count and box set for later handles.  tune = 2 + k
-// selects candidate k without timing.
+// Launch shape of the FP32 transport: tile (rtl::kTileX/Y) and grid.  Every
+// candidate computes each cell with the same arithmetic, so the choice
+// changes the time only.  Candidate k:
+//   k = 3 t + (b - 1), k < 9: tile t at b = 1..3 resident blocks per SM
+//     (capped by what fits), the grid b x SMs;
+//   k = 9 + 2 t + (j - 1): tile t with j = 1, 2 blocks per tile column, so
+//     the runs of neighbouring columns start at the same planes and each
+//     reads its x/y halo while the neighbour's plane is still in L2.
+// tune = 1 times every candidate on the handle's boxes (on a synthetic
+// realizable state in scratch, so the caller's state is not touched) and
+// keeps the fastest; the choice is cached per device, flux, group count and
+// box set for later handles.  tune = 2 + k selects candidate k without timing.
 struct TuneChoice {
-    int variant, blocks_per_sm;
+    int variant, grid;
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune_cache;
+constexpr int kTuneCandidates = 5 * rtl::kTileVariants;
 
 static void apply_layout(rt_handle *h, std::vector<rtd::BoxDev> &bd, int variant)
 {
@@ -229,12 +235,32 @@ static int tgrid_of(int64_t ntitems, int blocks_per_sm, int nsm)
     return (int)std::max<int64_t>(1, std::min<int64_t>((ntitems + 3) / 4, (int64_t)blocks_per_sm * nsm));
 }
 
+static TuneChoice tune_candidate(rt_handle *h, int k, int nsm)
+{
+    constexpr int V = rtl::kTileVariants;
+    const int v = k < 3 * V ? k / 3 : (k - 3 * V) / 2;
+    const int occ = rtl::transport_occupancy(false, false, v, h->p.flux);
+    std::vector<rtd::BoxDev> bd = h->bdev;
+    apply_layout(h, bd, v);
+    int64_t nt = 0, ncol = 0;
+    for (const auto &D : bd) {
+        nt += D.ntitems;
+        ncol += D.ntitems / D.nz;
+    }
+    if (k < 3 * V) return {v, tgrid_of(nt, std::min(k % 3 + 1, occ), nsm)};
+    const int64_t j = (k - 3 * V) % 2 + 1;
+    const int64_t g = std::min<int64_t>(j * ncol, (int64_t)occ * nsm);
+    return {v, (int)std::max<int64_t>(1, std::min<int64_t>(g, (nt + 3) / 4))};
+}
+
 static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
 {
     std::vector<TuneChoice> cand;
-    for (int v = 0; v < rtl::kTileVariants; v++) {
-        const int occ = rtl::transport_occupancy(false, false, v, h->p.flux);
-        for (int m = 1; m <= occ; m++) cand.push_back({v, m});
+    for (int k = 0; k < kTuneCandidates; k++) {
+        const TuneChoice c = tune_candidate(h, k, nsm);
+        bool dup = false;
+        for (const auto &o : cand) dup |= o.variant == c.variant && o.grid == c.grid;
+        if (!dup) cand.push_back(c);
     }
     std::string key = std::to_string(dev) + "/" + std::to_string(h->p.flux) + "/" + std::to_string(h->p.ngroups);
     for (const auto &D : h->bdev)
@@ -242,9 +268,9 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
     TuneChoice best{0, 1};
     bool have = false;
     if (tune >= 2) {
-        if ((size_t)(tune - 2) >= cand.size())
-            return fail(h, RT_ERR_ARG, "tune %d: only %d launch shapes", tune, (int)cand.size());
-        best = cand[tune - 2];
+        if (tune - 2 >= kTuneCandidates)
+            return fail(h, RT_ERR_ARG, "tune %d: only %d launch shapes", tune, kTuneCandidates);
+        best = tune_candidate(h, tune - 2, nsm);
         have = true;
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -283,7 +309,7 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
                 for (const auto &D : bd) nt += D.ntitems;
                 CU(h, cudaMemcpyAsync(tbox, bd.data(), sizeof(rtd::BoxDev) * h->nboxes,
                                       cudaMemcpyHostToDevice, h->s));
-                rtl::Launch L{tbox, h->nboxes, nt, tgrid_of(nt, c.blocks_per_sm, nsm), h->s, c.variant};
+                rtl::Launch L{tbox, h->nboxes, nt, c.grid, h->s, c.variant};
                 CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));      // warm-up
                 CU(h, cudaEventRecord(e0, h->s));
                 for (int r = 0; r < 5; r++) CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));
@@ -304,7 +330,7 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
     h->ntitems = 0;
     for (const auto &D : h->bdev) h->ntitems += D.ntitems;
     h->tvariant = best.variant;
-    h->tgrid = tgrid_of(h->ntitems, best.blocks_per_sm, nsm);
+    h->tgrid = best.grid;
     CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * h->nboxes, cudaMemcpyHostToDevice));
     return RT_OK;
 }

@@ -1,10 +1,11 @@
 // Host-side checks of the chemistry kernel's numerical helpers, compiled by
 // tests/test_host_numerics.py with nvcc and run on the CPU:
-//   1. f2d (float -> double by integer operations) against the conversion
+//   1. f2d (float -> double by integer operations, the conversion
+//      instruction for subnormals, Inf and NaN) against the conversion
 //      instruction, for every float;
 //   2. d2f (double -> float, round to nearest even) against the conversion,
 //      on exponents around the float range with exact ties, near-ties and
-//      carries into the exponent;
+//      carries into the exponent, in the normal and the subnormal results;
 //   3. the rate table (rate_table.cu) evaluated the kernel's way (interval
 //      and local variable from T's bits) against the rate fits in long
 //      double at random temperatures.
@@ -60,6 +61,21 @@ int main()
         case 4: m = 0xfffffffffffffull - (g() & 0x3fffffffull); break;
         }
         chk(rtk::dfrom(((r >> 63) << 63) | (ex << 52) | m));
+    }
+    // ties, near-ties and carries at the rounding position of subnormal
+    // results (exponents 873..896: the dropped bits are the low 926 - ex
+    // bits of the 53-bit significand)
+    for (unsigned long long ex = 870; ex <= 897; ex++) {
+        const unsigned sft = ex <= 896 ? 926u - (unsigned)ex : 29u;
+        for (int k = 0; k < 4000; k++) {
+            const unsigned long long full = (g() & 0xfffffffffffffull) | (1ull << 52);
+            const unsigned long long keep = sft < 53 ? full & ~((1ull << sft) - 1ull) : 0ull;
+            const unsigned long long half = sft <= 53 ? 1ull << (sft - 1u) : 0ull;
+            for (unsigned long long low : {half, half - 1ull, half + 1ull, 0ull, (half << 1) - 1ull}) {
+                const unsigned long long m = ((keep | (sft <= 53 ? low : 0ull)) & 0xfffffffffffffull);
+                chk(rtk::dfrom(((unsigned long long)(k & 1) << 63) | (ex << 52) | m));
+            }
+        }
     }
     for (unsigned long long ex = 0; ex < 2048; ex++)
         for (int s = 0; s < 2; s++)

@@ -1921,13 +1921,12 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
         // per group); the integer fields are reduced across the warp
         db.lane[it * (2 * RTD_CHEM_ITEM) + lane] = v.X;
         db.lane[it * (2 * RTD_CHEM_ITEM) + RTD_CHEM_ITEM + lane] = v.ph;
-        __threadfence();
         v = warp_reduce_ints(v);
+        if (lane == 0) store_part(db.part + it, v);
+        __threadfence();                  // every lane's stores before the arrival count
         const int64_t gl = li / RTD_CHEM_GROUP;           // group within the box
         int last_group = 0;
         if (lane == 0) {
-            store_part(db.part + it, v);
-            __threadfence();
             const int64_t left = B.ncitems - gl * RTD_CHEM_GROUP;
             const unsigned n_in = (unsigned)(left < RTD_CHEM_GROUP ? left : RTD_CHEM_GROUP);
             last_group = atomicAdd(&db.gdone[B.cgroup0 + gl], 1u) == n_in - 1u;

@@ -1675,6 +1675,12 @@ __device__ __forceinline__ void diag_add(DiagAcc &a, const DiagAcc &b)
     a.ncyc += b.ncyc;
 }
 
+// acquire-release fence at GPU scope: with a relaxed atomic after it, a
+// release of the thread's (and, through a barrier, its warp's) earlier
+// stores; after an atomic, an acquire (lighter than the sequentially
+// consistent __threadfence)
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // warp reduction in a fixed order (shuffle-down tree), result in lane 0
 __device__ __forceinline__ DiagAcc warp_reduce_diag(DiagAcc a)
 {
@@ -1923,17 +1929,22 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
         db.lane[it * (2 * RTD_CHEM_ITEM) + RTD_CHEM_ITEM + lane] = v.ph;
         v = warp_reduce_ints(v);
         if (lane == 0) store_part(db.part + it, v);
-        __threadfence();                  // every lane's stores before the arrival count
+        // the warp barrier orders every lane's stores before lane 0's release
+        // (an acquire-release fence, then the arrival count); the warp that
+        // completes the group acquires after its count and shares it
+        __syncwarp();
         const int64_t gl = li / RTD_CHEM_GROUP;           // group within the box
         int last_group = 0;
         if (lane == 0) {
             const int64_t left = B.ncitems - gl * RTD_CHEM_GROUP;
             const unsigned n_in = (unsigned)(left < RTD_CHEM_GROUP ? left : RTD_CHEM_GROUP);
+            fence_acq_rel_gpu();
             last_group = atomicAdd(&db.gdone[B.cgroup0 + gl], 1u) == n_in - 1u;
+            if (last_group) fence_acq_rel_gpu();
         }
         last_group = __shfl_sync(0xffffffffu, last_group, 0);
         if (last_group) {
-            __threadfence();
+            __syncwarp();
             const int64_t first = B.citem0 + gl * RTD_CHEM_GROUP;
             const int64_t left = B.ncitems - gl * RTD_CHEM_GROUP;
             const DiagAcc g = group_sum(db.part + first, db.lane + first * (2 * RTD_CHEM_ITEM),

@@ -441,7 +441,8 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                     D.titem0 = titem;
                     titem += D.ntitems;
                     D.citem0 = citem;
-                    D.ncitems = (D.ncell + RTD_CHEM_ITEM - 1) / RTD_CHEM_ITEM;
+                    D.ncitems = (D.ncell + RTD_CHEM_ITEM * RTD_CHEM_LANE_CELLS - 1) /
+                                (RTD_CHEM_ITEM * RTD_CHEM_LANE_CELLS);
                     citem += D.ncitems;
                     D.cgroup0 = cgroup;
                     D.ncgroups = (D.ncitems + RTD_CHEM_GROUP - 1) / RTD_CHEM_GROUP;

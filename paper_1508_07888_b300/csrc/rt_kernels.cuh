@@ -1783,8 +1783,9 @@ __device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf
     }
 }
 
-// One work item = RTD_CHEM_ITEM (32) consecutive cells of one box, one warp,
-// one thread per cell; warps draw items independently (no block barrier).
+// One work item = RTD_CHEM_LANE_CELLS x RTD_CHEM_ITEM (2 x 32) consecutive
+// cells of one box and one warp, each lane taking one cell of every row of
+// 32 in turn; warps draw items independently (no block barrier).
 // Reads the post-transport state, runs the sub-cycled chemistry over the
 // box's dt, writes the new radiation state into the caller's U and the
 // item's diagnostic partial.  The warp that completes a group of
@@ -1810,8 +1811,11 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
         const int b = find_box(boxes, nboxes, it, true);
         const BoxDev &B = boxes[b];
         const int64_t li = it - B.citem0;                 // item within the box
-        const int64_t c = li * RTD_CHEM_ITEM + lane;
         DiagAcc v = {0.0, 0.0, 0ull, 0ull, 0ull};
+        // the item's cells: RTD_CHEM_LANE_CELLS rows of 32, one cell of each
+        // per lane, in order (the lane's diagnostics summed in that order)
+        for (int hrow = 0; hrow < RTD_CHEM_LANE_CELLS; hrow++) {
+        const int64_t c = (li * RTD_CHEM_LANE_CELLS + hrow) * RTD_CHEM_ITEM + lane;
         if (c < B.ncell) {
             const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
             V4<TU> *U = reinterpret_cast<V4<TU> *>(B.U);
@@ -1915,13 +1919,17 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             }
             B.xHI[c] = s.xHI;
             B.T[c] = s.T;
-            v.X = 1.0 - s.xHI;
-            v.ph = ph_tot;
-            v.fbits = (unsigned long long)__double_as_longlong(to_d(sqrt(f2max)));
+            DiagAcc vc;
+            vc.X = 1.0 - s.xHI;
+            vc.ph = ph_tot;
+            vc.fbits = (unsigned long long)__double_as_longlong(to_d(sqrt(f2max)));
             // xHI < 0.5 on the integer pipe: doubles order like their bits
             // as signed integers (negative values below every positive one)
-            v.count = (long long)dbits(s.xHI) < (long long)dbits(0.5) ? 1ull : 0ull;
-            v.ncyc = (unsigned long long)ncyc;
+            vc.count = (long long)dbits(s.xHI) < (long long)dbits(0.5) ? 1ull : 0ull;
+            vc.ncyc = (unsigned long long)ncyc;
+            if (hrow == 0) v = vc;
+            else diag_add(v, vc);
+        }
         }
         // FP64 sums: each lane's values go to the item's fixed slots (summed
         // per group); the integer fields are reduced across the warp

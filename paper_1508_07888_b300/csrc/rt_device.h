@@ -16,7 +16,7 @@
 // cells per work item (one warp), work items per diagnostics group
 #define RTD_CHEM_BLOCK 256
 #define RTD_CHEM_ITEM 32
-#define RTD_CHEM_LANE_CELLS 2            // cells per lane in a chemistry work item
+#define RTD_CHEM_LANE_CELLS 4            // cells per lane in a chemistry work item
 #define RTD_CHEM_GROUP 64
 
 // device error bits (OR-ed into Ctl::err)

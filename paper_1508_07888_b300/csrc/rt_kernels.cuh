@@ -1783,7 +1783,7 @@ __device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf
     }
 }
 
-// One work item = RTD_CHEM_LANE_CELLS x RTD_CHEM_ITEM (2 x 32) consecutive
+// One work item = RTD_CHEM_LANE_CELLS x RTD_CHEM_ITEM (4 x 32) consecutive
 // cells of one box and one warp, each lane taking one cell of every row of
 // 32 in turn; warps draw items independently (no block barrier).
 // Reads the post-transport state, runs the sub-cycled chemistry over the

@@ -379,6 +379,16 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -1799,6 +1809,19 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
 {
     const int lane = threadIdx.x & 31;
     const double *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
+    // split form: each row of 32 cells' inputs (U* of every group, x_HI, T,
+    // n0) is staged into the warp's shared-memory buffers by cp.async while
+    // the lanes work on the previous row, so the DRAM latency of a cell's
+    // loads is hidden without registers; a lane reads back only what it
+    // copied itself
+    constexpr bool STAGE = !STRICT && sizeof(TU) == 4 && sizeof(TN) == 4;
+    struct Row {
+        V4<TU> U[G][RTD_CHEM_ITEM];
+        double xHI[RTD_CHEM_ITEM], T[RTD_CHEM_ITEM];
+        TN n0[RTD_CHEM_ITEM];
+    };
+    __shared__ __align__(16) Row rows[STAGE ? RTD_CHEM_BLOCK / 32 : 1][STAGE ? 2 : 1];
+    Row *wrow = rows[STAGE ? (threadIdx.x >> 5) : 0];
     // items are handed out one at a time from a counter, so warps that draw
     // cheap cells (cold gas) take more of them; the order of the work does
     // not enter any result
@@ -1812,12 +1835,31 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
         const BoxDev &B = boxes[b];
         const int64_t li = it - B.citem0;                 // item within the box
         DiagAcc v = {0.0, 0.0, 0ull, 0ull, 0ull};
+        const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
+        // copies of row hr into buffer hr & 1 (an empty group past the item)
+        auto stage = [&](int hr) {
+            const int64_t cs = (li * RTD_CHEM_LANE_CELLS + hr) * RTD_CHEM_ITEM + lane;
+            if (hr < RTD_CHEM_LANE_CELLS && cs < B.ncell) {
+                Row &r = wrow[hr & 1];
+#pragma unroll
+                for (int i = 0; i < G; i++) cp_async16(&r.U[i][lane], Us + (int64_t)i * B.ncell + cs);
+                cp_async8(&r.xHI[lane], B.xHI + cs);
+                cp_async8(&r.T[lane], B.T + cs);
+                cp_async4(&r.n0[lane], reinterpret_cast<const TN *>(B.n0) + cs);
+            }
+            cp_async_commit();
+        };
+        if constexpr (STAGE) stage(0);
         // the item's cells: RTD_CHEM_LANE_CELLS rows of 32, one cell of each
         // per lane, in order (the lane's diagnostics summed in that order)
         for (int hrow = 0; hrow < RTD_CHEM_LANE_CELLS; hrow++) {
         const int64_t c = (li * RTD_CHEM_LANE_CELLS + hrow) * RTD_CHEM_ITEM + lane;
+        if constexpr (STAGE) {
+            stage(hrow + 1);
+            cp_async_wait<1>();                          // row hrow has landed
+        }
+        const Row &rw = wrow[STAGE ? (hrow & 1) : 0];
         if (c < B.ncell) {
-            const V4<TU> *Us = reinterpret_cast<const V4<TU> *>(B.Us);
             V4<TU> *U = reinterpret_cast<V4<TU> *>(B.U);
             Cell<G> s;
             unsigned long long nclamp = 0;
@@ -1831,7 +1873,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             FT fac[G];
 #pragma unroll
             for (int i = 0; i < G; i++) {
-                const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
+                const V4<TU> u = STAGE ? rw.U[i][lane] : ld4(Us + (int64_t)i * B.ncell + c);
                 s.N[i] = to_d(u.x);
                 fac[i] = FT(1);
                 if (STRICT) {
@@ -1850,9 +1892,9 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             }
             if (gross) atomicOr(&ctl->err, RTD_ERR_REALIZ);
             if (nclamp) atomicAdd(&ctl->nclamp, nclamp);
-            s.xHI = B.xHI[c];
-            s.T = B.T[c];
-            const double n0 = ldn(reinterpret_cast<const TN *>(B.n0), c);
+            s.xHI = STAGE ? rw.xHI[lane] : B.xHI[c];
+            s.T = STAGE ? rw.T[lane] : B.T[c];
+            const double n0 = STAGE ? to_d(rw.n0[lane]) : ldn(reinterpret_cast<const TN *>(B.n0), c);
             // source term of this cell: sorted unique cells, binary search
             double S[G];
 #pragma unroll
@@ -1905,7 +1947,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                     o.y = from_d<TU>(s.F[i][0]); o.z = from_d<TU>(s.F[i][1]); o.w = from_d<TU>(s.F[i][2]);
                 } else {
                     const TU fi = (TU)fac[i];          // FT is TU in the fast forms
-                    const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
+                    const V4<TU> u = STAGE ? rw.U[i][lane] : ld4(Us + (int64_t)i * B.ncell + c);
                     o.y = u.y * fi; o.z = u.z * fi; o.w = u.w * fi;
                 }
                 st4(U + (int64_t)i * B.ncell + c, o);

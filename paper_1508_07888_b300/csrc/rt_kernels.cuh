@@ -1850,6 +1850,18 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             cp_async_commit();
         };
         if constexpr (STAGE) stage(0);
+        // does the item hold a source cell?  (one search per item; the
+        // sources are sparse, so most items skip the per-cell search)
+        bool item_src = false;
+        if (B.nsrc > 0) {
+            const int64_t c0 = li * (RTD_CHEM_LANE_CELLS * RTD_CHEM_ITEM);
+            int lo = 0, hi = B.nsrc;                     // first source cell >= c0
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (B.src_cell[mid] < c0) lo = mid + 1; else hi = mid;
+            }
+            item_src = lo < B.nsrc && B.src_cell[lo] < c0 + RTD_CHEM_LANE_CELLS * RTD_CHEM_ITEM;
+        }
         // the item's cells: RTD_CHEM_LANE_CELLS rows of 32, one cell of each
         // per lane, in order (the lane's diagnostics summed in that order)
         for (int hrow = 0; hrow < RTD_CHEM_LANE_CELLS; hrow++) {
@@ -1899,7 +1911,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             double S[G];
 #pragma unroll
             for (int i = 0; i < G; i++) S[i] = 0.0;
-            if (B.nsrc > 0) {
+            if (item_src) {
                 int lo = 0, hi = B.nsrc - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;

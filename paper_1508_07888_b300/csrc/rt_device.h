@@ -12,11 +12,12 @@
 // transport tile: TX x TY threads, one (x, y) column each, marching in z
 #define RTD_TX 32
 #define RTD_TY 8
-// chemistry: threads per block (independent warps, one thread per cell),
-// cells per work item (one warp), work items per diagnostics group
+// chemistry: threads per block (independent warps, one cell per thread at a
+// time), lanes of a work item (one warp), cells per lane in a coarse work
+// item (the fine level's items have one), work items per diagnostics group
 #define RTD_CHEM_BLOCK 256
 #define RTD_CHEM_ITEM 32
-#define RTD_CHEM_LANE_CELLS 4            // cells per lane in a chemistry work item
+#define RTD_CHEM_LANE_CELLS 4
 #define RTD_CHEM_GROUP 64
 
 // device error bits (OR-ed into Ctl::err)

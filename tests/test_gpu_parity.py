@@ -190,13 +190,17 @@ def test_upload_download_and_argument_errors():
 
 @pytest.mark.parametrize("flux", [0, 1])
 @pytest.mark.parametrize("shape,bc", [((33, 9, 40), [1, 1, 0, 0, 2, 2]), ((9, 33, 17), [0] * 6),
-                                      ((16, 48, 48), [2, 1, 2, 1, 2, 1])])
+                                      ((16, 48, 48), [2, 1, 2, 1, 2, 1]),
+                                      ((12, 20, 37), [3, 1, 0, 0, 2, 2])])
 def test_transport_launch_shapes_are_bitwise_equal(shape, bc, flux):
-    """Every launch shape of the FP32 transport, GLF and HLL (tile x
-    resident blocks per SM, rt_params.tune = 2 + k) gives the same bits as
-    the default; the tuner (tune = 1) picks one of them and reports it."""
+    """Every launch shape of the FP32 transport, GLF and HLL (tile x grid,
+    rt_params.tune = 2 + k) gives the same bits as the default; the tuner
+    (tune = 1) picks one of them and reports it.  The last case has an
+    inflow face (its ghost beam written into the halo by both kernels)."""
     G = 3
     w, st = _empty_workload(shape, G, bc, seed=sum(shape) + 5)
+    if bc[0] == I.BC_INFLOW:
+        w.inflow = [2e6, 0, 0, 0, 0, 0]
     ref = run_gpu(w, 3, "split", None, st, flux=flux)[0][0]
     assert ref[4] == B.RT_OK
     shapes = set()
@@ -227,6 +231,19 @@ def test_tuned_full_step_matches_default():
     for a, b in zip(out[:4], ref[:4]):
         np.testing.assert_array_equal(a, b)
     assert st.tile_x * st.tile_y == 256 and st.chem_grid > 0
+
+
+def test_ensemble_launch_shapes_are_bitwise_equal():
+    """Uneven boxes in one launch: every transport launch shape, the
+    column-aligned grids included (their runs then straddle boxes of other
+    depths), gives the same bits, state and history, as the default."""
+    w = I.ensemble(nboxes=5, steps=6, sides=(8, 12, 16, 20), seed=11)
+    ref, _ = run_gpu(w, 6, "split")
+    for k in (0, 5, 7, 9, 12, 14):
+        out, _ = run_gpu(w, 6, "split", tune=2 + k)
+        for b in range(5):
+            for x, y in zip(out[b][:4], ref[b][:4]):
+                np.testing.assert_array_equal(x, y)
 
 
 @pytest.mark.parametrize("shape", [(7, 5, 3), (9, 33, 17), (33, 9, 40)])

@@ -5,7 +5,7 @@
 // recombination cooling; exp(-118348/T)/(1 + sqrt(T/1e5)) excitation cooling;
 // 1.42e-27 x 1.3 sqrt(T) bremsstrahlung) are evaluated here in long double and
 // interpolated on 2^RTD_TAB_SUB equal intervals of T per binade, 1 K <= T <
-// 2^30 K, each by a degree-6 Chebyshev polynomial rewritten in the monomial
+// 2^30 K, each by a degree-5 Chebyshev polynomial rewritten in the monomial
 // basis of the local variable t = 2 (T - T_a)/(T_b - T_a) - 1 in [-1, 1).
 // Tabulated functions (layout [interval][function][coefficient]):
 //   0: alpha_A   1: alpha_B   2: recombination (case A or B) + free-free cooling

@@ -40,9 +40,9 @@
 #define RTD_TAB_NF 5         // aA, aB, kR, ln(beta) + T_HI/T, ln(cce) + 118348/T
 #define RTD_TAB_E0 0         // 1 K
 #define RTD_TAB_E1 30        // 2^30 K = 1.07e9 K
-#define RTD_TAB_SUB 5
+#define RTD_TAB_SUB 6        // 64 intervals per binade
 #define RTD_TAB_NINT ((RTD_TAB_E1 - RTD_TAB_E0) << RTD_TAB_SUB)
-#define RTD_TAB_NC 7         // degree 6 in t
+#define RTD_TAB_NC 6         // degree 5 in t
 // below this temperature both exp(-T_HI/T) and exp(-118348/T) factors of the
 // fits are exactly zero in double precision (checked when the table is built)
 #define RTD_TAB_TCUT 155.0

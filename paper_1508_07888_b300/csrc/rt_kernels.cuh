@@ -1285,8 +1285,8 @@ __device__ __forceinline__ double tab_poly(const double *c, double t)
     return p;
 }
 
-// The same rates from the tables built at set-up (rate_table.cu): degree-6
-// Chebyshev interpolants on 32 intervals of T per binade, accurate to ~1e-14
+// The same rates from the tables built at set-up (rate_table.cu): degree-5
+// Chebyshev interpolants on 64 intervals of T per binade, accurate to ~2e-14
 // relative; beta and the excitation cooling keep their exp(-c/T) factor
 // exact, and below RTD_TAB_TCUT, where both factors are exactly zero in
 // double, they are not evaluated.  Outside 1 K .. 2^30 K the fits are

@@ -71,8 +71,9 @@ __device__ RatesD rates_d_exact(const Phys &ph, double T)
 }
 
 // the tabulated rates of the forward pass (rates_tab), differentiated
-// through the interpolating polynomials: d/dT = (dt/dT) d/dt, with
-// dt/dT = 2 / (interval width) = 2^(SUB + 1 - e)
+// through the interpolating polynomials in their variable y (y = 1 at the
+// interval's start, 2 at its end): d/dT = (dy/dT) d/dy, with
+// dy/dT = 1 / (interval width) = 2^(SUB - e)
 __device__ RatesD rates_d(const Phys &ph, const double *tab, double T)
 {
     if (!tab || ph.rates_const) return rates_d_exact(ph, T);
@@ -80,7 +81,7 @@ __device__ RatesD rates_d(const Phys &ph, const double *tab, double T)
     double t;
     if (!tab_pos(T, j, t)) return rates_d_exact(ph, T);
     const int e = (int)(__double_as_longlong(T) >> 52) - 1023;
-    const double dtdT = ldexp(1.0, RTD_TAB_SUB + 1 - e);
+    const double dtdT = ldexp(1.0, RTD_TAB_SUB - e);    // dy/dT of the tables' variable y
     const double *a = tab + (size_t)j * (RTD_TAB_NF * RTD_TAB_NC);
     double g[RTD_TAB_NF], dg[RTD_TAB_NF];
     for (int f = 0; f < RTD_TAB_NF; f++) {

@@ -5,8 +5,9 @@
 // recombination cooling; exp(-118348/T)/(1 + sqrt(T/1e5)) excitation cooling;
 // 1.42e-27 x 1.3 sqrt(T) bremsstrahlung) are evaluated here in long double and
 // interpolated on 2^RTD_TAB_SUB equal intervals of T per binade, 1 K <= T <
-// 2^30 K, each by a degree-5 Chebyshev polynomial rewritten in the monomial
-// basis of the local variable t = 2 (T - T_a)/(T_b - T_a) - 1 in [-1, 1).
+// 2^30 K, each by a degree-5 Chebyshev polynomial in the local variable
+// t = 2 (T - T_a)/(T_b - T_a) - 1 in [-1, 1), stored as monomial coefficients
+// in y = (t + 3)/2 in [1, 2), the value the kernel reads off T's bits.
 // Tabulated functions (layout [interval][function][coefficient]):
 //   0: alpha_A   1: alpha_B   2: recombination (case A or B) + free-free cooling
 //   3: ln(beta) + T_HI/T               (beta = exp(f3 - T_HI/T))
@@ -95,17 +96,26 @@ bool build_rate_table(bool ots, double *out)
                 for (int m = 0; m < N; m++) s += fv[m] * cosl(M_PIl * n * (m + 0.5L) / N);
                 c[n] = (n == 0 ? 1.0L : 2.0L) * s / N;
             }
-            double *o = out + ((size_t)j * RTD_TAB_NF + f) * N;
+            // monomial coefficients in t, then in y = (t + 3)/2 in [1, 2),
+            // the kernel's variable (t = 2y - 3 composed in long double)
+            LD mt[RTD_TAB_NC], my[RTD_TAB_NC] = {};
             for (int i = 0; i < N; i++) {
                 LD s = 0;
                 for (int n = 0; n < N; n++) s += c[n] * cheb[n][i];
-                o[i] = (double)s;
+                mt[i] = s;
             }
-            for (int k = 0; k <= 16; k++) {           // check, in double Horner
-                const double t = -1.0 + 2.0 * k / 16.0;
+            my[0] = mt[N - 1];
+            for (int i = N - 2; i >= 0; i--) {          // my <- my (2y - 3) + mt[i]
+                for (int k = N - 1; k >= 1; k--) my[k] = 2 * my[k - 1] - 3 * my[k];
+                my[0] = -3 * my[0] + mt[i];
+            }
+            double *o = out + ((size_t)j * RTD_TAB_NF + f) * N;
+            for (int i = 0; i < N; i++) o[i] = (double)my[i];
+            for (int k = 0; k <= 16; k++) {           // check, in double Horner in y
+                const double y = 1.0 + k / 16.0;
                 double p = o[N - 1];
-                for (int i = N - 2; i >= 0; i--) p = p * t + o[i];
-                const LD ex = fit(f, lo + ((LD)t + 1) * 0.5L * (hi - lo), ots);
+                for (int i = N - 2; i >= 0; i--) p = p * y + o[i];
+                const LD ex = fit(f, lo + ((LD)y - 1) * (hi - lo), ots);
                 const LD err = f <= 2 ? fabsl((p - ex) / ex) : fabsl(p - ex);
                 if (!(err <= 1e-13L)) return false;
             }

@@ -1260,8 +1260,9 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
 }
 
 // Position of T in the rate tables (rate_table.cu): interval j and local
-// variable t in [-1, 1), both from T's bits.  For T = 2^e (1 + m), m in [0, 1),
-// j = 2^SUB (e - E0) + floor(2^SUB m) and t = 2 frac(2^SUB m) - 1, exactly.
+// variable y in [1, 2), both from T's bits.  For T = 2^e (1 + m), m in [0, 1),
+// j = 2^SUB (e - E0) + floor(2^SUB m) and y = 1 + frac(2^SUB m), exactly (the
+// tables hold their polynomials in y, so no arithmetic forms it).
 // Returns false outside [2^E0, 2^E1) (and for T <= 0, NaN, Inf).
 __device__ __forceinline__ bool tab_pos(double T, int &j, double &t)
 {
@@ -1271,9 +1272,7 @@ __device__ __forceinline__ bool tab_pos(double T, int &j, double &t)
     constexpr int low = 52 - RTD_TAB_SUB;
     j = ((e - RTD_TAB_E0) << RTD_TAB_SUB) + (int)((bits >> low) & ((1 << RTD_TAB_SUB) - 1));
     // 1 + frac in [1, 2): the mantissa bits below the top SUB, moved up
-    const double y = __longlong_as_double(0x3FF0000000000000ll |
-                                          ((bits & ((1ll << low) - 1)) << RTD_TAB_SUB));
-    t = fma(y, 2.0, -3.0);
+    t = __longlong_as_double(0x3FF0000000000000ll | ((bits & ((1ll << low) - 1)) << RTD_TAB_SUB));
     return true;
 }
 
@@ -1405,6 +1404,7 @@ struct NoTrace {
 template <int G>
 struct CellK {
     double n02, K, cvn; // n0^2, n0^2 / nunit (without OTS), (3/2) kB n0
+    double cvn2;        // 3 kB n0
     float n0f, S32[G];  // n0 and the source terms in FP32 (FP32 photon update)
 };
 
@@ -1467,7 +1467,7 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
     const double x1 = 1.0 - o.xHI;
     const double cool = k.n02 * x1 * fma(x1, r.kR, o.xHI * r.kC);   // Lambda(n0, x^{p+1}, T^p)
     e1 = fma(dtau, fma(o.xHI * n0, hs, -cool), e0);
-    o.T = e1 * rcp_nr(k.cvn * (2.0 - o.xHI));
+    o.T = e1 * rcp_nr(fma(-k.cvn, o.xHI, k.cvn2));    // (3/2) kB n0 (2 - x_HI)
 }
 
 // fac (fast forms without a trace): F is left alone and each group's scale
@@ -1504,6 +1504,7 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         k.n02 = n0 * n0;
         k.K = ph.ots ? 0.0 : k.n02 * B.inv_nunit;
         k.cvn = (1.5 * rtd::KB) * n0;
+        k.cvn2 = 2.0 * k.cvn;
     }
     if (!STRICT) k.n0f = d2f(n0);
     if (N32) {
@@ -1521,7 +1522,7 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         double dtau = rem;
         bool last = true;
         // e^p (the fast forms reuse it in every trial of this sub-cycle)
-        const double ep0 = STRICT ? 0.0 : k.cvn * (2.0 - s.xHI) * s.T;
+        const double ep0 = STRICT ? 0.0 : fma(-k.cvn, s.xHI, k.cvn2) * s.T;
         // FP32 pre-test of the estimate's skip (fast forms).  heat and
         // cooling are >= 0, so |rate| <= heat + cool, and q = rem (heat +
         // cool) / e is a sum of products of non-negative FP32 numbers in which

@@ -98,7 +98,7 @@ int main()
             const int low = 52 - RTD_TAB_SUB;
             const int j = ((e - RTD_TAB_E0) << RTD_TAB_SUB) + (int)((bits >> low) & ((1 << RTD_TAB_SUB) - 1));
             const double y = rtk::dfrom(0x3FF0000000000000ull | ((bits & ((1ull << low) - 1)) << RTD_TAB_SUB));
-            const double t = std::fma(y, 2.0, -3.0);
+            const double t = y;                  // the tables' variable
             const double *a = tab.data() + (size_t)j * RTD_TAB_NF * RTD_TAB_NC;
             double gv[RTD_TAB_NF];
             for (int f = 0; f < RTD_TAB_NF; f++) {

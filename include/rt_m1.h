@@ -236,8 +236,8 @@ RT_API int rt_set_profiling(rt_handle *h, int on);
 /* Counters and the last diagnostics; never launches work. */
 RT_API int rt_query(rt_handle *h, rt_stats *st);
 
-/* Message of the last failing call on h (or of the last failing rt_create
- * when h is NULL).  Never NULL. */
+/* Message of the last failing call on h; when h is NULL, of the last failing
+ * rt_create or rt_transport_static on the calling thread.  Never NULL. */
 RT_API const char *rt_last_error(rt_handle *h);
 
 /* Free the scratch and the handle (h may be NULL). */
@@ -284,18 +284,22 @@ RT_API int rt_group_table(int ngroups, const double *edges_eV, double T_bb,
  * The post-transport state lives in a static device array of
  * RT_STATIC_SCRATCH_BYTES bytes, so the box must satisfy
  *     ngroups * nx * ny * nz * 4 * element size <= RT_STATIC_SCRATCH_BYTES - 768
- * (e.g. 2,097,088 cells for one FP32 group); a larger box is rejected with
- * RT_ERR_TOO_LARGE before any work is queued.
+ * (2,097,104 cells for one FP32 group); a larger box is rejected with
+ * RT_ERR_TOO_LARGE before any work is queued.  Unlike rt_step, no flux-limit
+ * check (|F| <= cN, the realizability count of rt_stats) is applied to the
+ * result.
  *
  * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
- * and the call returns after that stream has drained.  The first call made
- * while a given device is current looks up the array's device address on that
- * device (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  Every call shares the one array and it keeps the last
- * call's contents (each call rewrites what it reads before reading it), so
- * calls that overlap on the GPU -- from several threads or streams at once --
- * race and must be serialised by the caller.
- * Returns RT_OK, RT_ERR_ARG (bad argument), RT_ERR_TOO_LARGE or RT_ERR_CUDA. */
+ * and the call returns after that stream has drained, so it may not be called
+ * while the stream is being captured into a CUDA graph.  The first call made
+ * while a given device is current looks up the array's device address on
+ * that device (cudaGetSymbolAddress) and caches it.  Every call shares the one
+ * array and it keeps the last call's contents (each call rewrites what it
+ * reads before reading it), so calls that overlap on the GPU -- from several
+ * threads or streams at once -- race and must be serialised by the caller.
+ * Returns RT_OK, RT_ERR_ARG (bad argument), RT_ERR_TOO_LARGE or RT_ERR_CUDA,
+ * with the message in rt_last_error(NULL).  After RT_ERR_CUDA the stream has
+ * drained, but box->U holds an undefined number of the requested steps. */
 RT_API int rt_transport_static(const rt_params *p, const rt_box *box, int nsteps, void *stream);
 
 #ifdef __cplusplus

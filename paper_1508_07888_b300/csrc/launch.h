@@ -67,6 +67,10 @@ cudaError_t chem_adj(int G, const rtd::BoxDev *boxes, const rtd::Phys &ph, const
 cudaError_t transport_adj(int G, const rtd::BoxDev *boxes, const double *U, const double *lamS,
                           double *lamU, int64_t ncell, cudaStream_t s);
 
+// message that rt_last_error(NULL) returns on the calling thread (rt_api.cu);
+// entry points without a handle record their failures here
+void set_thread_error(const char *msg);
+
 // resident blocks per SM of each kernel (for persistent grid sizing)
 int transport_occupancy(bool fp64, bool strict, int variant = 0, int flux = RTD_FLUX_GLF);
 int chem_occupancy(bool fp64, bool strict, int G);

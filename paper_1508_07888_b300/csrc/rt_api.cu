@@ -95,6 +95,8 @@ struct rt_handle {
 
 static thread_local std::string g_create_err;
 
+void rtl::set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
+
 static int fail(rt_handle *h, int code, const char *fmt, ...)
 {
     char buf[512];

@@ -38,8 +38,12 @@ constexpr int kMaxDevices = 64;
 unsigned char *g_dev_addr[kMaxDevices] = {nullptr};
 std::mutex g_setup_mutex;
 
-// every failure returns a status only: the messages below document the cause
-inline int err(int code, const char *) { return code; }
+// a failure returns its status and leaves its message for rt_last_error(NULL)
+inline int err(int code, const char *msg)
+{
+    rtl::set_thread_error(msg);
+    return code;
+}
 
 // device address of the scratch on the current device (set-up on first use)
 int scratch_address(unsigned char **out)
@@ -88,12 +92,17 @@ extern "C" int rt_transport_static(const rt_params *p, const rt_box *box, int ns
     if (nsteps < 0) return err(RT_ERR_ARG, "rt_transport_static: nsteps must be >= 0");
     const bool fp64 = p->precision != RT_PREC_SPLIT;
     const bool strict = p->precision == RT_PREC_FP64_STRICT;
-    const int64_t ncell = (int64_t)box->nx * box->ny * box->nz;
-    const size_t need = (size_t)p->ngroups * (size_t)ncell * 4 * (fp64 ? 8 : 4);
-    if (need > RT_STATIC_SCRATCH_BYTES - kStateOff)
+    // capacity in cells, then the box against it one factor at a time, so that
+    // no product of the sizes can overflow before it is compared
+    const uint64_t cell_bytes = (uint64_t)p->ngroups * 4 * (fp64 ? 8 : 4);
+    const uint64_t cap = (RT_STATIC_SCRATCH_BYTES - kStateOff) / cell_bytes;
+    const uint64_t nxy_cap = cap / (uint64_t)box->nx;
+    if ((uint64_t)box->ny > nxy_cap || (uint64_t)box->nz > nxy_cap / (uint64_t)box->ny)
         return err(RT_ERR_TOO_LARGE, "rt_transport_static: the box's radiation state does not fit the "
                                "static scratch (G*nx*ny*nz*4*element size must be at most "
                                "RT_STATIC_SCRATCH_BYTES - 768 bytes)");
+    const int64_t ncell = (int64_t)box->nx * box->ny * box->nz;
+    const size_t need = (size_t)cell_bytes * (size_t)ncell;
     if (nsteps == 0) return RT_OK;
 
     unsigned char *base = nullptr;
@@ -147,13 +156,21 @@ extern "C" int rt_transport_static(const rt_params *p, const rt_box *box, int ns
         rtl::Launch L{dd, 1, D[0].ntitems, grid, s};
         cudaError_t e = strict ? rtl::transport_strict(L, 32, ph, dctl)
                                : rtl::transport_fast(fp64, L, 32, ph, dctl);
-        if (e != cudaSuccess) return err(RT_ERR_CUDA, "rt_transport_static: kernel launch failed");
+        if (e != cudaSuccess) {
+            // drain what was queued before the failure, so that no step of this
+            // call is still running on box->U when the caller gets the status
+            cudaStreamSynchronize(s);
+            return err(RT_ERR_CUDA, "rt_transport_static: kernel launch failed");
+        }
     }
     if (nsteps & 1) {
-        if (cudaMemcpyAsync(box->U, base + kStateOff, need, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(box->U, base + kStateOff, need, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            cudaStreamSynchronize(s);
             return err(RT_ERR_CUDA, "rt_transport_static: copy of the result failed");
+        }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return err(RT_ERR_CUDA, "rt_transport_static: stream synchronisation failed");
+    rtl::set_thread_error("");
     return RT_OK;
 }

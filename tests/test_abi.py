@@ -123,3 +123,25 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == C.sizeof(cls), name
         for f, _ in cls._fields_:
             assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+@pytest.mark.parametrize("side", [256, 1 << 20, (1 << 31) - 1])
+def test_static_transport_size_check_cannot_overflow(side):
+    """rt_transport_static checks the box against its fixed scratch before any
+    CUDA call, one factor at a time: a box whose byte count overflows 64 bits
+    (2^20 or 2^31 - 1 cells per axis) is rejected, not wrapped under the limit.
+    U is a dummy aligned address that is never dereferenced."""
+    f = B.lib().rt_transport_static
+    f.restype = C.c_int
+    f.argtypes = [C.POINTER(B.rt_params), C.POINTER(B.rt_box), C.c_int, C.c_void_p]
+    t = {"sigN": [0.0], "sigE": [0.0], "Eavg": [0.0], "frac": [1.0]}
+    p = B.make_params(1, t, 3e9, isothermal=True, rates_const=True)
+    box = B.rt_box()
+    box.nx = box.ny = box.nz = side
+    box.dx, box.nunit = 3e20, 1.0
+    box.U = 1 << 20
+    assert f(C.byref(p), C.byref(box), 1, None) == B.RT_ERR_TOO_LARGE
+    assert "does not fit" in B.rt_last_error(None)
+    box.nx = box.ny = box.nz = 0
+    assert f(C.byref(p), C.byref(box), 1, None) == B.RT_ERR_ARG
+    assert "positive" in B.rt_last_error(None)

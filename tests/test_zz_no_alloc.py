@@ -81,13 +81,19 @@ def test_static_transport_matches_allocating_path_two_calls_in_a_row(prec, tol, 
     assert not np.array_equal(first, second)
 
 
-def test_static_transport_rejects_a_box_beyond_its_scratch():
+@pytest.mark.parametrize("side", [256, 1 << 20])
+def test_static_transport_rejects_a_box_beyond_its_scratch(side):
+    """256^3 x 16 B = 256 MiB is over the 32 MiB scratch; at 2^20 cells per
+    axis the byte count of the box overflows 64 bits, which the check must not
+    let wrap past the limit.  Both return before any work is queued."""
     import torch
     Ut = torch.zeros(16, dtype=torch.float32, device="cuda")
     box = B.rt_box()
-    box.nx = box.ny = box.nz = 256           # 256^3 x 16 B = 256 MiB > 32 MiB
+    box.nx = box.ny = box.nz = side
     box.dx, box.nunit = 3e20, 1.0
     box.U = Ut.data_ptr()
     p = params(1, B.RT_PREC_SPLIT, [0] * 6)
     assert entry()(C.byref(p), C.byref(box), 1, None) == B.RT_ERR_TOO_LARGE
+    assert "does not fit" in B.rt_last_error(None)
+    torch.cuda.synchronize()
     assert torch.count_nonzero(Ut).item() == 0

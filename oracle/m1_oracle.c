@@ -53,7 +53,13 @@
  *      recombination, collisional ionisation and recombination cooling;
  *      collisional-excitation cooling exp(-118348/T) form of Cen (1992);
  *      bremsstrahlung 1.42e-27 g_ff sqrt(T) with g_ff = 1.3; no Compton term.
- *      parity unpinned beyond alpha_A/alpha_B at 5e3, 1e4, 2e4 K (textbook).
+ *      Pinned, independently of the fits: alpha_A/alpha_B against the
+ *      textbook values at 5e3-2e4 K; the case A - B split of the rate and
+ *      of the cooling against recombination to 1s (Milne relation with the
+ *      exact 1s cross-section); case B against Kramers sums over n >= 2;
+ *      beta against Lotz's cross-section and Voronov's fit; the thresholds
+ *      of beta and of the excitation cooling; the ionisation energy of the
+ *      collisional-ionisation cooling; the classical free-free emissivity.
  *   R9 photo-ionisation cross-section: the exact hydrogenic form
  *      sigma = A0 (E1/E)^4 exp(4 - 4 atan(eps)/eps)/(1 - exp(-2 pi/eps)),
  *      eps = sqrt(E/E1 - 1), A0 = 6.30e-18 cm^2, E1 = 13.6 eV.

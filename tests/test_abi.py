@@ -45,7 +45,7 @@ def test_group_table_matches_oracle(edges, T):
 def test_timestep_matches_paper_reading():
     t = {"sigN": [1.0], "sigE": [1.0], "Eavg": [1.0], "frac": [1.0]}
     p = B.make_params(1, t, 3e9, cfl=0.9)
-    assert B.rt_timestep(p, 6e20) == pytest.approx(0.9 * 6e20 / (3 * 3e9), rel=1e-15)
+    assert B.rt_timestep(p, 6e20) == pytest.approx(0.9 * 6e20 / (3 * 3e9), rel=1e-15, abs=0)
     p.cfl = 0.0
     assert B.rt_timestep(p, 6e20) < 0
 

@@ -109,7 +109,7 @@ def test_config5_gradients_match_finite_differences():
             v = torch.as_tensor(rng.standard_normal(n00.shape), device="cuda") * n00
             fd = (loss(Q0, n00 + h * v) - loss(Q0, n00 - h * v)).item() / (2 * h)
             ad = torch.sum(gn * v).item()
-            assert ad == pytest.approx(fd, rel=1e-3), (ad, fd)
+            assert ad == pytest.approx(fd, rel=1e-3, abs=0), (ad, fd)
         flat = gn.reshape(-1).cpu().numpy()
         top = np.argsort(-np.abs(flat))[:2000]
         for c in rng.choice(top, size=32, replace=False):

@@ -97,7 +97,7 @@ def test_transport_adjoint_dot_product():
     h = 1e-6
     lhs = np.sum(w * (O.transport(p, U + h * v, lam) - O.transport(p, U - h * v, lam))) / (2 * h)
     rhs = np.sum(O.transport_adj(p, U, w, lam) * v)
-    assert rhs == pytest.approx(lhs, rel=1e-7)
+    assert rhs == pytest.approx(lhs, rel=1e-7, abs=0)
 
 
 def test_full_adjoint_against_run_differences():
@@ -133,9 +133,9 @@ def test_full_adjoint_against_run_differences():
         Qp[k] += h
         Qm[k] -= h
         fd = (loss(Qp, n0) - loss(Qm, n0)) / (2 * h)
-        assert dQ[k] == pytest.approx(fd, rel=1e-5), (k, dQ[k], fd)
+        assert dQ[k] == pytest.approx(fd, rel=1e-5, abs=0), (k, dQ[k], fd)
     for seed in range(2):
         v = np.random.default_rng(100 + seed).standard_normal(shape) * n0
         h = 1e-6
         fd = (loss(Q, n0 + h * v) - loss(Q, n0 - h * v)) / (2 * h)
-        assert np.sum(dn0 * v.reshape(-1)) == pytest.approx(fd, rel=1e-5)
+        assert np.sum(dn0 * v.reshape(-1)) == pytest.approx(fd, rel=1e-5, abs=0)

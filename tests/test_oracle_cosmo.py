@@ -62,7 +62,7 @@ def test_einstein_de_sitter_expansion():
         a = O.advance_a(a, dt, H_FAST, 1.0, 0.0)
         t += dt
     exact = (0.1 ** 1.5 + 1.5 * H_FAST * t) ** (2.0 / 3.0)
-    assert a == pytest.approx(exact, rel=1e-10)
+    assert a == pytest.approx(exact, rel=1e-10, abs=0)
     assert a > 0.3
 
 

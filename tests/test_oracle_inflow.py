@@ -40,7 +40,7 @@ def test_photons_enter_at_the_given_rate(flux):
             tot = U[..., 0].sum(axis=(1, 2, 3))
             np.testing.assert_allclose(tot, rho * lam * k * shape[0] * shape[1], rtol=1e-12)
     # photon number flux of the incoming beam: c N nunit = 3e6 /cm^2/s in total
-    assert rho.sum() * 0.1 * C * nunit == pytest.approx(3.0e6, rel=1e-15)
+    assert rho.sum() * 0.1 * C * nunit == pytest.approx(3.0e6, rel=1e-15, abs=0)
     np.testing.assert_allclose(rho / rho.sum(), [0.7, 0.3], rtol=1e-15)
 
 

@@ -49,12 +49,14 @@ def parse():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the all-FP64 comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample-steps", type=int, default=3,
+                    help="oracle steps timed at each of the CPU baseline's sample points")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-crta", action="store_true")
     ap.add_argument("--no-hll", action="store_true")
     ap.add_argument("--no-cosmo", action="store_true")
+    ap.add_argument("--no-256", action="store_true", help="skip the 256^3 workload's row")
     ap.add_argument("--tune", type=int, default=1,
                     help="rt_params.tune of the split form: 1 = time the transport's launch "
                          "shapes at create, 2 + k = shape k (profiling runs fix the shape)")
@@ -308,11 +310,12 @@ def e2e_host(w, precision, K, W, nsteps):
     return sec, h2d, d2h
 
 
-def cpu_baseline(w, steps):
-    """The FP64 oracle, single-threaded, on the first `steps` radiative steps
-    of the same workload."""
+def cpu_baseline(w, steps, points=(0, 100, 250)):
+    """The FP64 oracle, single-threaded, timed on `steps` radiative steps at
+    each of `points` (step indices spread over the run, so that the sample
+    carries the later steps' chemistry work too); between the points the
+    oracle advances its own state on every host core, untimed."""
     import oracle as O
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
     box = w.boxes[0]
     t = O.group_table(w.edges_eV, w.T_bb)
     from paper_1508_07888_b300 import inputs as I
@@ -322,15 +325,65 @@ def cpu_baseline(w, steps):
     nunit = w.nunit(box)
     S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)
     U, xHI, T = box.initial_state(w.ngroups)
+    at, sec, timed = 0, 0.0, 0
+    for k in points:
+        if k > at:
+            O.set_threads(os.cpu_count() or 1)
+            r = O.run(p, U, xHI, T, box.n0, box.dx, nunit, k - at, S)
+            U, xHI, T, at = r.U, r.xHI, r.T, k
+        O.set_threads(1)
+        t0 = time.perf_counter()
+        r = O.run(p, U, xHI, T, box.n0, box.dx, nunit, steps, S)
+        sec += time.perf_counter() - t0
+        U, xHI, T, at = r.U, r.xHI, r.T, at + steps
+        timed += steps
     O.set_threads(1)
-    t0 = time.perf_counter()
-    O.run(p, U, xHI, T, box.n0, box.dx, nunit, steps, S)
-    sec = time.perf_counter() - t0
-    return {"value": box.ncell * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"radiative steps 1-{steps} of the same 128^3 3-group workload "
-                      f"({sec:.1f} s, FP64 C oracle, 1 thread; early steps carry fewer "
-                      f"chemistry sub-cycles than the 500-step average)",
+    where = ", ".join(f"{k + 1}-{k + steps}" for k in points)
+    return {"value": box.ncell * timed / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"radiative steps {where} of the same 128^3 3-group workload "
+                      f"({sec:.1f} s timed, FP64 C oracle, 1 thread; the oracle advances its "
+                      f"own state between the sampled steps on all host cores, untimed)",
             "cpu": cpu_model(), "host_cpu_count": os.cpu_count()}
+
+
+def reion256_run(B, ws, K=3, nsteps=20):
+    """The 256^3 workload (sigma = 1.5, P ~ k^-2.5, 1024 sources with
+    Q ~ n0^1.5, 3 groups, c/20, 8 fixed chemistry intervals per step), split
+    form, 20 radiative steps per run (of its 200): its state (805 MB of FP32
+    radiation) is far beyond the 126 MB L2, so the transport's HBM rate is
+    clean of cache reuse.  Per-kernel times by CUDA events."""
+    import torch
+    from paper_1508_07888_b300 import inputs as I
+    w = I.reion_large()
+    r = DeviceRun(w, B.RT_PREC_SPLIT)
+    r.reset()
+    r.run(nsteps)
+    B.rt_set_profiling(r.solver.h, 1)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        r.reset()
+        r.run(nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    val, sec = replica_value(ws, w.cells * nsteps * K, e0.elapsed_time(e1) / 1e3)
+    st = B.rt_query(r.solver.h)
+    r.close()
+    t_ms = st.kernel_ms[0] / max(st.kernel_launches[0], 1)
+    c_ms = st.kernel_ms[1] / max(st.kernel_launches[1], 1)
+    pk = peaks()
+    hbm = pk["hbm_gbs"] if pk else 6400.0
+    gbs = 32.0 * w.ngroups * w.cells / (t_ms * 1e-3) / 1e9
+    return {"workload": w.name + " (sigma=1.5, P~k^-2.5, 1024 sources, 3 groups, c/20, nsub=8)",
+            "value": val, "unit": UNIT, "cells": w.cells, "rt_steps_per_run": nsteps,
+            "ms_per_run": sec * 1e3 / K,
+            "transport_ms_per_launch": t_ms, "transport_gbs": gbs,
+            "transport_frac": gbs / hbm,
+            "transport_traffic": profiled_traffic().get("transport_256"),
+            "chemistry_ms_per_launch": c_ms,
+            "peak_note": "of measured" if pk else "of fallback"}
 
 
 def ensemble_run(B, ws, K=3):
@@ -667,6 +720,7 @@ def main():
     crta = None if args.no_crta else crta_run()
     hll = None if args.no_hll else hll_run()
     cosmo = None if args.no_cosmo else cosmo_run()
+    r256 = None if args.no_256 else reion256_run(B, ws)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -689,6 +743,7 @@ def main():
             "launch": launch,
             "fp64_form": fp64, "e2e": e2e, "cpu_baseline": cpu,
             "ensemble": ens, "adjoint": adj, "crta": crta, "hll": hll, "cosmo": cosmo,
+            "reion256": r256,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "final_diag": dict(zip(B.DIAG_NAMES, diag)),
         }

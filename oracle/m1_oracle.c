@@ -764,7 +764,9 @@ int orc_run_crta(const orc_params *p, int nx, int ny, int nz, double dx, double 
     int64_t nclamp = 0;
     for (int step = 0; step < nsteps; step++) {
         orc_transport(p, nx, ny, nz, lam, U, Us);
-        /* realizability after transport: |F| <= cN (1 + 1e-12) */
+        /* realizability after transport: |F| <= cN (1 + 1e-12); a count, so
+         * the order in which threads add it up does not matter */
+#pragma omp parallel for num_threads(orc_threads) schedule(static) reduction(+:nclamp)
         for (size_t k = 0; k < ncell * G; k++) {
             double N = Us[4 * k];
             if (N > 0.0) {
@@ -799,14 +801,18 @@ int orc_run_crta(const orc_params *p, int nx, int ny, int nz, double dx, double 
             err |= orc_chem_cell(p, dt, nunit, n0f[f], Sc, Uc, &xHIf[f], &Tf[f], &ncyc);
         }
         if (hist) {
-            double X = 0.0, ph = 0.0, fmax = 0.0, nion = 0.0;
-            for (size_t id = 0; id < ncell; id++) {
-                X += 1.0 - xHI[id];
-                if (xHI[id] < 0.5) nion += 1.0;
-            }
+            /* the two sums in index order; the count and the maximum are exact
+             * in any order, so threads share them */
+            double X = 0.0, ph = 0.0, fmax = 0.0;
+            int64_t nion = 0;
+            for (size_t id = 0; id < ncell; id++) X += 1.0 - xHI[id];
+            for (size_t k = 0; k < ncell * G; k++) ph += U[4 * k];
+#pragma omp parallel for num_threads(orc_threads) schedule(static) reduction(+:nion)
+            for (size_t id = 0; id < ncell; id++)
+                if (xHI[id] < 0.5) nion++;
+#pragma omp parallel for num_threads(orc_threads) schedule(static) reduction(max:fmax)
             for (size_t k = 0; k < ncell * G; k++) {
                 double N = U[4 * k];
-                ph += N;
                 if (N > 0.0) {
                     double ux = U[4 * k + 1] / N, uy = U[4 * k + 2] / N, uz = U[4 * k + 3] / N;
                     double f = sqrt(ux * ux + uy * uy + uz * uz);
@@ -817,7 +823,7 @@ int orc_run_crta(const orc_params *p, int nx, int ny, int nz, double dx, double 
             h[0] = X / (double)ncell;
             h[1] = ph * nunit * (dx * dx * dx);
             h[2] = fmax;
-            h[3] = nion;
+            h[3] = (double)nion;
             h[4] = cyc_sum / (double)ncell;
         }
     }

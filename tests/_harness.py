@@ -54,20 +54,36 @@ def gpu_params(w: I.Workload, table: dict, precision: str, **over) -> B.rt_param
     return B.make_params(w.ngroups, table, c_red, **kw)
 
 
-def run_oracle(w: I.Workload, steps: int, table=None, states=None, threads=None, **over):
-    """Returns per box: (U, xHI, T, hist, err, nclamp)."""
+def run_oracle(w: I.Workload, steps: int, table=None, states=None, threads=None,
+               box_parallel=False, **over):
+    """Returns per box: (U, xHI, T, hist, err, nclamp).
+
+    box_parallel: run the boxes side by side, one single-threaded oracle call
+    per host core (the calls release the GIL and share no state; the results
+    are the same bits as one after the other).  Otherwise each box runs on
+    `threads` OpenMP threads (default: the host's cores, at most 8)."""
     table = table if table is not None else tables(w)[0]
     if threads is None:
         threads = min(8, os.cpu_count() or 1)
-    O.set_threads(threads)
-    out = []
-    for bi, box in enumerate(w.boxes):
+
+    def one(bi):
+        box = w.boxes[bi]
         p = oracle_params(w, table, box=box, **over)
         nunit = w.nunit(box)
         U, xHI, T = states[bi] if states is not None else box.initial_state(w.ngroups)
         S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)
         r = O.run(p, U, xHI, T, box.n0, box.dx, nunit, steps, S)
-        out.append((r.U, r.xHI, r.T, r.hist, r.err, r.nclamp))
+        return (r.U, r.xHI, r.T, r.hist, r.err, r.nclamp)
+
+    if box_parallel:
+        from concurrent.futures import ThreadPoolExecutor
+        O.set_threads(1)
+        order = sorted(range(len(w.boxes)), key=lambda b: -w.boxes[b].ncell)   # largest first
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+            res = dict(zip(order, ex.map(one, order)))
+        return [res[b] for b in range(len(w.boxes))]
+    O.set_threads(threads)
+    out = [one(bi) for bi in range(len(w.boxes))]
     O.set_threads(1)
     return out
 

@@ -53,6 +53,8 @@ def test_cosmo_parity(prec):
     if prec == "split":
         ex, eT = linf_rel(x, r.run.xHI), linf_rel(T, r.run.T)
         assert ex <= 1e-3 and eT <= 1e-3, (ex, eT)
+        err = field_errors((U, x, T), (r.run.U, r.run.xHI, r.run.T), 3)
+        assert max(err[k] for k in err if k[0] in "NF") <= 1e-4, err
     else:
         err = field_errors((U, x, T), (r.run.U, r.run.xHI, r.run.T), 3)
         assert max(err.values()) <= 1e-9, err

@@ -111,21 +111,21 @@ def test_set_fine_arguments():
     s.close()
 
 
-def test_reion_128_fine_level_sampled_step():
+def test_reion_128_fine_level_sampled_step(reion128_oracle):
     """The 128^3 workload with its densest eighth refined into 8 children
-    (2,097,152 refined cells): after 60 steps, one more step of sampled
-    refined cells against the oracle's chemistry from the oracle's own
-    transport of the coarse state."""
+    (2,097,152 refined cells), refined after the oracle's 100 steps: each child
+    starts in its parent's state at that time.  One GPU step from that
+    oracle-made state, against the oracle's chemistry of sampled refined
+    cells from the oracle's own transport of the same coarse state."""
     import torch
-    w = I.reion()
+    w, to, tp, ora = reion128_oracle
     box = w.boxes[0]
-    to, tp = tables(w)
+    U, xHI, T = ora[:3]
     fine = I.refine_densest(box, frac=0.125, seed=7)
-    s = make_solver(w, "fp64", tp)
-    xf, Tf = s.set_fine(0, fine.parent, fine.n0, fine.xHI, fine.T)
-    assert s.step(60) == B.RT_OK
-    U, xHI, T = s.numpy_state(0)
-    x0, T0 = xf.cpu().numpy().copy(), Tf.cpu().numpy().copy()
+    x0 = xHI.reshape(-1)[fine.parent].copy()
+    T0 = T.reshape(-1)[fine.parent].copy()
+    s = make_solver(w, "fp64", tp, [(U, xHI, T)])
+    xf, Tf = s.set_fine(0, fine.parent, fine.n0, x0, T0)
     assert s.step(1) == B.RT_OK
     x1, T1 = xf.cpu().numpy(), Tf.cpu().numpy()
     s.close()
@@ -136,7 +136,11 @@ def test_reion_128_fine_level_sampled_step():
     S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)
     rng = np.random.default_rng(128)
     near_src = np.flatnonzero(np.isin(fine.parent, box.src_cells))
-    idx = np.unique(np.concatenate([rng.choice(fine.parent.size, 3000, replace=False), near_src]))
+    front = np.flatnonzero((x0 > 0.02) & (x0 < 0.98))
+    if front.size > 2000:
+        front = rng.choice(front, 2000, replace=False)
+    idx = np.unique(np.concatenate([rng.choice(fine.parent.size, 3000, replace=False), near_src,
+                                    front]))
     G = w.ngroups
     Usf = Us.reshape(G, -1, 4)
     worst = 0.0

@@ -1,16 +1,17 @@
 """GPU parity at the full sizes of the workloads, in the launch configuration
-the benchmark times (one handle over the whole box, graph replay).
+the benchmark times (one handle over the whole box or ensemble, graph
+replay), on sampled cells.
 
-The oracle cannot afford hundreds of steps of a 128^3 or 256^3 box, so each
-check runs the GPU to step k, takes its state, lets the GPU make one more
-step, and compares that step on sampled cells -- random cells, every source
-cell and every cell of the ionisation front -- with the oracle's one-step
-evaluation of the same cells from the same state.  Properties that hold at
-any size (bounds of xHI and T, the flux limit, photon totals) are checked on
-the whole box.
+Each check loads a state the oracle produced -- the initial state, or the
+oracle's own state after its multi-step run of the workload -- into the
+library, lets the GPU make one step, and compares that step on sampled cells
+(random cells, every source cell and every cell of the ionisation front)
+with the oracle's one-step evaluation of the same cells from the same state.
+No oracle input comes from the GPU.  Properties that hold at any size
+(bounds of xHI and T, the flux limit) are checked on the whole box.  The
+element-wise comparison of whole runs is in test_gpu_multistep.py.
 """
 import math
-import os
 
 import numpy as np
 import pytest
@@ -37,79 +38,74 @@ def sample(box, xHI, rng, nrand=4096, nfront=2048):
     return np.array(sorted(cells), dtype=np.int64)
 
 
-def one_step_check(w, solver, box_index, prec, to, rng):
-    """Compare the solver's next step of box `box_index` with the oracle on samples."""
-    box = w.boxes[box_index]
-    U, xHI, T = solver.numpy_state(box_index)
-    assert solver.step(1) == B.RT_OK
-    U1, x1, T1 = solver.numpy_state(box_index)
+def one_step_check(w, states, boxes, prec, to, tp, rng):
+    """Load the oracle-made `states` (one (U, xHI, T) per box) into one
+    handle, make one GPU step, and compare boxes `boxes` on sampled cells with
+    the oracle's step of the same cells from the same state.  The split form
+    starts both sides from U rounded to float32, the precision it stores."""
+    if prec == "split":
+        states = [(I.f32(U).astype(np.float64), x, T) for U, x, T in states]
+    s = make_solver(w, prec, tp, states)
+    assert s.step(1) == B.RT_OK
     p = oracle_params(w, to)
-    nunit = w.nunit(box)
-    S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)
-    cells = sample(box, xHI, rng)
-    Uo, xo, To_, err = O.step_cells(p, U, xHI, T, box.n0, box.dx, nunit, cells, S)
-    assert err == 0
     G = w.ngroups
-    Ug = U1.reshape(G, -1, 4)[:, cells, :].transpose(1, 0, 2)       # [k, G, 4]
     tol = TOL[prec]
-    for g in range(G):
-        Nscale = max(np.max(np.abs(U1[g, ..., 0])), 1e-300)
-        den = np.maximum(np.abs(Uo[:, g, 0]), 1e-6 * Nscale)
-        eN = np.max(np.abs(Ug[:, g, 0] - Uo[:, g, 0]) / den)
-        eF = np.max(np.linalg.norm(Ug[:, g, 1:] - Uo[:, g, 1:], axis=-1) / den)
-        assert eN <= tol and eF <= tol, (prec, g, eN, eF)
-    ex = np.max(np.abs(x1.reshape(-1)[cells] - xo) / np.maximum(np.abs(xo), 1e-6))
-    eT = np.max(np.abs(T1.reshape(-1)[cells] - To_) / To_)
-    assert ex <= tol and eT <= tol, (prec, ex, eT)
-    # whole-box properties
-    assert np.all((x1 >= 0.0) & (x1 <= 1.0)) and np.all(T1 > 0.0)
-    N, F = U1[..., 0], np.linalg.norm(U1[..., 1:], axis=-1)
-    assert np.all(F <= N * (1.0 + (1e-5 if prec == "split" else 1e-12)) + 1e-300)
-    return len(cells)
-
-
-@pytest.mark.parametrize("prec", ["split", "fp64"])
-def test_reion_128_sampled_steps(prec):
-    """The benchmark workload: 128^3, 3 groups, 64 sources, adaptive chemistry."""
-    w = I.reion()
-    to, tp = tables(w)
-    s = make_solver(w, prec, tp)
-    rng = np.random.default_rng(128)
-    done = 0
-    for k in (0, 120, 499):
-        assert s.step(k - done) == B.RT_OK
-        one_step_check(w, s, 0, prec, to, rng)
-        done = k + 1
+    for b in boxes:
+        box = w.boxes[b]
+        U, xHI, T = states[b]
+        U1, x1, T1 = s.numpy_state(b)
+        nunit = w.nunit(box)
+        S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)
+        cells = sample(box, xHI, rng)
+        Uo, xo, To_, err = O.step_cells(p, U, xHI, T, box.n0, box.dx, nunit, cells, S)
+        assert err == 0
+        Ug = U1.reshape(G, -1, 4)[:, cells, :].transpose(1, 0, 2)       # [k, G, 4]
+        for g in range(G):
+            Nscale = max(np.max(np.abs(U1[g, ..., 0])), 1e-300)
+            den = np.maximum(np.abs(Uo[:, g, 0]), 1e-6 * Nscale)
+            eN = np.max(np.abs(Ug[:, g, 0] - Uo[:, g, 0]) / den)
+            eF = np.max(np.linalg.norm(Ug[:, g, 1:] - Uo[:, g, 1:], axis=-1) / den)
+            assert eN <= tol and eF <= tol, (prec, b, g, eN, eF)
+        ex = np.max(np.abs(x1.reshape(-1)[cells] - xo) / np.maximum(np.abs(xo), 1e-6))
+        eT = np.max(np.abs(T1.reshape(-1)[cells] - To_) / To_)
+        assert ex <= tol and eT <= tol, (prec, b, ex, eT)
+        # whole-box properties
+        assert np.all((x1 >= 0.0) & (x1 <= 1.0)) and np.all(T1 > 0.0)
+        N, F = U1[..., 0], np.linalg.norm(U1[..., 1:], axis=-1)
+        assert np.all(F <= N * (1.0 + (1e-5 if prec == "split" else 1e-12)) + 1e-300)
     st = s.stats()
     s.close()
     assert st.error_bits == 0
 
 
-def test_reion_256_nsub8_sampled_steps():
-    """256^3, sigma = 1.5, 1024 sources, c/20, 8 fixed chemistry intervals."""
-    w = I.reion_large()
-    to, tp = tables(w)
-    s = make_solver(w, "split", tp)
+@pytest.mark.parametrize("prec", ["split", "fp64"])
+def test_reion_128_sampled_steps(prec, reion128_oracle):
+    """The benchmark workload (128^3, 3 groups, 64 sources, adaptive
+    chemistry): its first step and its step after the oracle's 100 steps."""
+    w, to, tp, ora = reion128_oracle
+    rng = np.random.default_rng(128)
+    box = w.boxes[0]
+    one_step_check(w, [box.initial_state(w.ngroups)], [0], prec, to, tp, rng)
+    one_step_check(w, [ora[:3]], [0], prec, to, tp, rng)
+
+
+@pytest.mark.parametrize("prec", ["split", "fp64"])
+def test_reion_256_nsub8_sampled_steps(prec, reion256_oracle):
+    """256^3, sigma = 1.5, 1024 sources, c/20, 8 fixed chemistry intervals:
+    the first step and the step after the oracle's 20 steps."""
+    w, to, tp, ora = reion256_oracle
     rng = np.random.default_rng(256)
-    done = 0
-    for k in (0, 60, 199):
-        assert s.step(k - done) == B.RT_OK
-        one_step_check(w, s, 0, "split", to, rng)
-        done = k + 1
-    s.close()
+    box = w.boxes[0]
+    one_step_check(w, [box.initial_state(w.ngroups)], [0], prec, to, tp, rng)
+    one_step_check(w, [ora[:3]], [0], prec, to, tp, rng)
 
 
-def test_ensemble_64_boxes_sampled_steps():
-    """64 periodic boxes of side 32-96 in one handle (one launch per kernel)."""
-    w = I.ensemble()
-    to, tp = tables(w)
-    s = make_solver(w, "split", tp)
-    assert s.step(99) == B.RT_OK
+def test_ensemble_64_boxes_sampled_steps(ensemble64_oracle):
+    """64 periodic boxes of side 32-96 in one handle (one launch per kernel),
+    one step from the oracle's states after 100 steps."""
+    w, to, tp, ora = ensemble64_oracle
     rng = np.random.default_rng(64)
-    for b in range(0, 64, 7):
-        one_step_check(w, s, b, "split", to, rng)
-        # one_step_check advanced every box by one step: keep them in step
-    s.close()
+    one_step_check(w, [o[:3] for o in ora], list(range(0, 64, 7)), "split", to, tp, rng)
 
 
 QS, N0, ALPHA = 5e48, 1e-3, I.ALPHA_B_1E4

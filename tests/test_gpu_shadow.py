@@ -37,6 +37,19 @@ def test_small_clump_parity(flux, prec):
         # HLL carries the FP32 transport's 1e-7 through its amplification
         tol_x, tol_T = (1e-3, 1e-3) if flux == 0 else (1e-3, 1e-2)
         assert ex <= tol_x and eT <= tol_T, (ex, eT)
+        if flux == 0:
+            # the FP32 transport's radiation, element-wise (floored relative)
+            err = field_errors(gpu, ora, 3)
+            assert max(err[k] for k in err if k[0] in "NF") <= 1e-4, err
+        else:
+            # HLL, normwise: the flux amplifies the FP32 transport's rounding
+            # in the faint cells ahead of the front (the oracle against itself
+            # takes a 1e-15 perturbation to ~1e-3 there), so the radiation
+            # bar is the conditioning's, not 1e-4 (measured 3.7e-4)
+            for g in range(3):
+                scale = np.max(np.abs(ora[0][g, ..., 0]))
+                eN = np.max(np.abs(gpu[0][g] - ora[0][g])) / scale
+                assert eN <= 1e-3, (g, eN)
     elif flux == 0:
         err = field_errors(gpu, ora, 3)
         assert max(err.values()) <= 1e-9, err

@@ -7,6 +7,7 @@ the oracle (a dropped term, a wrong sign or index, a transposed operand)
 fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -553,3 +554,19 @@ def test_step_cells_is_the_full_step_on_those_cells():
     np.testing.assert_array_equal(Uo, full.U.reshape(3, -1, 4)[:, cells, :].transpose(1, 0, 2))
     np.testing.assert_array_equal(xo, full.xHI.reshape(-1)[cells])
     np.testing.assert_array_equal(To, full.T.reshape(-1)[cells])
+
+
+def test_box_parallel_oracle_runs_are_the_same_bits():
+    """The test harness may run an ensemble's boxes side by side (one
+    single-threaded oracle call per core); the results must be the bits of
+    the sequential multi-threaded runs."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from _harness import run_oracle
+    w = I.ensemble(nboxes=4, steps=3, sides=(8, 12), seed=5)
+    a = run_oracle(w, 3, threads=3)
+    b = run_oracle(w, 3, box_parallel=True)
+    for x, y in zip(a, b):
+        for u, v in zip(x[:4], y[:4]):
+            np.testing.assert_array_equal(u, v)
+        assert x[4:] == y[4:]

@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-hll", action="store_true")
     ap.add_argument("--no-cosmo", action="store_true")
     ap.add_argument("--no-256", action="store_true", help="skip the 256^3 workload's row")
+    ap.add_argument("--config-table", action="store_true",
+                    help="instead of the bench line: one JSON line per workload x form")
     ap.add_argument("--tune", type=int, default=1,
                     help="rt_params.tune of the split form: 1 = time the transport's launch "
                          "shapes at create, 2 + k = shape k (profiling runs fix the shape)")
@@ -183,7 +185,8 @@ def make_params(w, precision, tune=None):
     from paper_1508_07888_b300 import binding as B
     return B.make_params(w.ngroups, group_table(w), w.c_red, cfl=w.cfl, ots=w.ots,
                          isothermal=w.isothermal, nsub=w.nsub, bc=w.bc, precision=precision,
-                         tune=tune)
+                         tune=tune, rates_const=w.rates_const, alphaA=w.alphaA,
+                         alphaB=w.alphaB, beta=w.beta)
 
 
 class DeviceRun:
@@ -598,10 +601,104 @@ def chem_flops_per_subcycle(G: int, ots: bool, split: bool = True) -> float:
     return (12.0 if split else 22.0) * G + 111.0 - (14.0 if ots else 0.0)
 
 
+# FP64 flops of one GLF transport cell-group, counted from the formulas as
+# written (+ - x / sqrt each 1): closure 42 (F/N 3, f^2 5, s 3, a 6, g 4,
+# P 21), three faces of 16 (each face shared by two cells), update 28
+TRANSPORT_FP64_FLOPS = 118.0
+
+
+def fp64_peak_tflops():
+    """FP64 pipe: 148 SMs x 2 DFMA/clock x 2 flop x 2032 MHz (a DFMA loop
+    measured 1.97 DFMA/clock/SM at the clock it ran at)."""
+    return 148 * 2 * 2 * 2032e6 / 1e12
+
+
+def oracle_sample(w, steps, boxes=None):
+    """1-thread oracle rate (cell-updates/s) on the first `steps` steps of
+    the given boxes (all by default): a bounded sample of the workload."""
+    import oracle as O
+    from paper_1508_07888_b300 import inputs as I
+    t = O.group_table(w.edges_eV, w.T_bb)
+    t = {k: I.f32(v) for k, v in t.items()}
+    p = O.Params(sigN=t["sigN"], sigE=t["sigE"], Eavg=t["Eavg"], frac=t["frac"], c=w.c_red,
+                 cfl=w.cfl, ots=w.ots, isothermal=w.isothermal, nsub=w.nsub, bc=list(w.bc),
+                 rates_const=w.rates_const, alphaA=w.alphaA, alphaB=w.alphaB, beta=w.beta)
+    O.set_threads(1)
+    cells, sec = 0, 0.0
+    for b in (boxes if boxes is not None else range(len(w.boxes))):
+        box = w.boxes[b]
+        nunit = w.nunit(box)
+        S = O.source_field(p, box.shape, box.src_cells, box.src_Q, box.dx, nunit)
+        U, xHI, T = box.initial_state(w.ngroups)
+        t0 = time.perf_counter()
+        O.run(p, U, xHI, T, box.n0, box.dx, nunit, steps, S)
+        sec += time.perf_counter() - t0
+        cells += box.ncell * steps
+    return cells / sec, sec
+
+
+def config_table():
+    """One JSON line per workload x precision form: throughput, per-kernel
+    times, the transport's HBM fraction (split: 32 G B, FP64: 64 G B per
+    cell; or FP64 flops for the FP64 form's transport) and the chemistry's
+    FP64 fraction, and a bounded 1-thread oracle sample of the same
+    workload.  Not part of the default run."""
+    import torch
+    from paper_1508_07888_b300 import binding as B
+    from paper_1508_07888_b300 import inputs as I
+    torch.cuda.set_device(0)
+    pk = peaks()
+    hbm = pk["hbm_gbs"] if pk else 6400.0
+    f64 = fp64_peak_tflops()
+    cfgs = [("1: Stromgren 32^3, 1 group, FP64 constant rates", I.stromgren(32), 100, 20, None),
+            ("2: reionisation 128^3, 3 groups, adaptive chemistry", I.reion(), 500, 3, None),
+            ("3: reionisation 256^3, 3 groups, c/20, nsub 8 (20 of its 200 steps)",
+             I.reion_large(), 20, 1, None),
+            ("4: ensemble of 64 boxes 32-96^3, 2 groups", I.ensemble(), 100, 2, [0, 1, 2, 3])]
+    for name, w, nsteps, osteps, oboxes in cfgs:
+        orate, osec = oracle_sample(w, osteps, oboxes)
+        for prec, pname in ((B.RT_PREC_SPLIT, "split"), (B.RT_PREC_FP64, "fp64")):
+            ms, kern, diag, nbytes, mean_sub, launch = time_device(w, prec, 2, 1, nsteps, 1,
+                                                                   profile=True)
+            cells = w.cells
+            per = {k: v["ms_total"] / max(v["launches"], 1) for k, v in kern.items()}
+            G = w.ngroups
+            row = {"config": name, "form": pname, "value": cells * nsteps * 2 / (ms * 1e-3),
+                   "unit": UNIT, "rt_steps": nsteps, "kernels_ms_per_launch": per,
+                   "mean_subcycles": mean_sub,
+                   "oracle_1thread": {"value": orate, "sample": f"{osteps} steps, "
+                                      + (f"boxes {oboxes}" if oboxes else "whole workload"),
+                                      "seconds": osec}}
+            t = per.get("transport")
+            if t:
+                if prec == B.RT_PREC_SPLIT:
+                    gbs = 32.0 * G * cells / (t * 1e-3) / 1e9
+                    row["transport_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm,
+                                                 "unit": "GB/s", "frac": gbs / hbm}
+                else:
+                    tf = TRANSPORT_FP64_FLOPS * G * cells / (t * 1e-3) / 1e12
+                    gbs = 64.0 * G * cells / (t * 1e-3) / 1e9
+                    row["transport_roofline"] = {"bound": "alu", "achieved": tf, "peak": f64,
+                                                 "unit": "TFLOP/s", "frac": tf / f64,
+                                                 "hbm_frac": gbs / hbm}
+            c = per.get("chemistry")
+            if c and not w.rates_const:
+                fl = chem_flops_per_subcycle(G, w.ots, prec == B.RT_PREC_SPLIT) * cells * mean_sub
+                tf = fl / (c * 1e-3) / 1e12
+                row["chemistry_roofline"] = {"bound": "alu", "achieved": tf, "peak": f64,
+                                             "unit": "TFLOP/s", "frac": tf / f64}
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"config": "5: adjoint 64^3, 1 group, 200 steps", "form": "fp64",
+                      **adjoint_run()}), flush=True)
+
+
 def main():
     global TUNE
     args = parse()
     TUNE = args.tune
+    if args.config_table:
+        config_table()
+        return
     ws, rank, local = dist_setup(args)
     w = workload()
     box = w.boxes[0]
@@ -703,7 +800,7 @@ def main():
     # update (10 G of the trial's flops) runs in FP32 -> 12 G + 111 FP64
     # flops, against the FP64 pipe peak: 148 SMs x 2 DFMA/clock x 2 flop x
     # 2032 MHz
-    fp64_peak = 148 * 2 * 2 * 2032e6 / 1e12
+    fp64_peak = fp64_peak_tflops()
     c_flops = chem_flops_per_subcycle(G, w.ots) * box.ncell * mean_sub
     c_ach = c_flops / (per_launch["chemistry"] * 1e-3) / 1e12
     roof_c = {"kernel": "chemistry", "bound": "alu", "achieved": c_ach, "peak": fp64_peak,

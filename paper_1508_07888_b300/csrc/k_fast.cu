@@ -56,7 +56,8 @@ static cudaError_t transport_pm(const Launch &L, int zc, const rtd::Phys &ph, rt
 {
     cudaError_t e = pm_attr<TX, TY>();
     if (e != cudaSuccess) return e;
-    rtk::k_transport_pm<TX, TY><<<L.grid, dim3(TX, TY), rtk::transport_pm_smem_bytes<TX, TY>(), L.stream>>>(
+    rtk::k_transport_pm<TX, TY><<<L.grid, rtk::transport_pm_threads<TX, TY>(),
+                                  rtk::transport_pm_smem_bytes<TX, TY>(), L.stream>>>(
         L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
     return cudaSuccess;
 }
@@ -213,7 +214,8 @@ template <int TX, int TY>
 static int pm_occupancy()
 {
     pm_attr<TX, TY>();
-    return occ((const void *)rtk::k_transport_pm<TX, TY>, TX * TY, rtk::transport_pm_smem_bytes<TX, TY>());
+    return occ((const void *)rtk::k_transport_pm<TX, TY>, rtk::transport_pm_threads<TX, TY>(),
+               rtk::transport_pm_smem_bytes<TX, TY>());
 }
 
 __global__ void k_fill_tune(float4 *U, int64_t n)

@@ -170,6 +170,19 @@ template <typename R, bool STRICT>
 __device__ __forceinline__ R fdiv(R a, R b) { return a / b; }
 template <>
 __device__ __forceinline__ float fdiv<float, false>(float a, float b) { return a * frcp<float, false>(b); }
+// reciprocal of the closure: the FP64 fast form (RT_PREC_FP64) takes the
+// Newton reciprocal of rcp_nr (one ulp at most from IEEE 1/d) where the
+// strict form divides.  The HLL speeds keep IEEE division in FP64: there a
+// beam's f = |F|/N must come out exactly 1 (a 1-ulp f gives a beam along a
+// face a transverse speed of ~1e-8 and moves the face off the mean flux)
+template <typename R, bool STRICT>
+__device__ __forceinline__ R crcp(R x) { return frcp<R, STRICT>(x); }
+template <>
+__device__ __forceinline__ double crcp<double, false>(double x) { return rcp_nr(x); }
+template <typename R, bool STRICT>
+__device__ __forceinline__ R cdiv(R a, R b) { return fdiv<R, STRICT>(a, b); }
+template <>
+__device__ __forceinline__ double cdiv<double, false>(double a, double b) { return a * rcp_nr(b); }
 template <typename R, bool STRICT>
 __device__ __forceinline__ R fsqrt(R x) { return rsqrt_(x); }
 template <typename R, bool STRICT>
@@ -204,7 +217,7 @@ __device__ __forceinline__ void closure(const V4<R> &u, R P[6])
         if (STRICT) {
             ux = u.y / N; uy = u.z / N; uz = u.w / N;
         } else {
-            const R rN = frcp<R, STRICT>(N);
+            const R rN = crcp<R, STRICT>(N);
             ux = u.y * rN; uy = u.z * rN; uz = u.w * rN;
         }
         R f2 = ux * ux + uy * uy + uz * uz;
@@ -219,7 +232,7 @@ __device__ __forceinline__ void closure(const V4<R> &u, R P[6])
             if (STRICT) {
                 ux = ux / f; uy = uy / f; uz = uz / f;
             } else {
-                const R rf = frcp<R, STRICT>(f);
+                const R rf = crcp<R, STRICT>(f);
                 ux *= rf; uy *= rf; uz *= rf;
             }
             f2 = R(1);
@@ -234,9 +247,9 @@ __device__ __forceinline__ void closure(const V4<R> &u, R P[6])
             g = (R(6) + R(3) / (R(2) + s)) / (R(5) + R(2) * s);
         } else {
             const R s = fsqrt<R, STRICT>(R(4) - R(3) * f2);
-            const R r5 = frcp<R, STRICT>(R(5) + R(2) * s);
+            const R r5 = crcp<R, STRICT>(R(5) + R(2) * s);
             a = ((R(1) + s) - R(2) * f2) * r5;
-            g = (R(6) + fdiv<R, STRICT>(R(3), R(2) + s)) * r5;
+            g = (R(6) + cdiv<R, STRICT>(R(3), R(2) + s)) * r5;
         }
         P[0] = N * (a + g * (ux * ux));
         P[1] = N * (g * (ux * uy));
@@ -550,6 +563,11 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
 
         R Fzm[4] = {R(0), R(0), R(0), R(0)};
         R szc_a = R(0), szc_b = R(0);     // HLL: z speeds of the plane being updated
+        // FP64 fast form, GLF: the convex form of the update (as the FP32
+        // kernel), from the cell below's U and G_z carried in registers
+        constexpr bool CVX = !STRICT && !HLL;
+        V4<R> ub = {};
+        R gzb[4] = {R(0), R(0), R(0), R(0)};
         for (int q = 0; q < L; q++) {
             cp_async_wait<S - 3>();
             __syncthreads();        // plane q landed everywhere; plane q-1's closures visible;
@@ -612,6 +630,46 @@ k_transport(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int /*
             R Pc[6];
 #pragma unroll
             for (int k = 0; k < 6; k++) Pc[k] = sm.P[cp][k][ty + 1][tx + 1];
+            if constexpr (CVX) {
+                // U* = (1 - 3 lam) U + (lam/2) sum_d [(U + G_d)(left_d) + (U - G_d)(right_d)],
+                // G_x = (Fx, Pxx, Pxy, Pxz), G_y = (Fy, Pxy, Pyy, Pyz), G_z = (Fz, Pxz, Pyz, Pzz):
+                // equal to U - lam sum_d (Phi_{d,+} - Phi_{d,-}) with Phi of Eq. e:glf,
+                // each face's terms formed once
+                if (c >= 1) {
+                    R Pl[6], Pr[6], Pd[6], Pu[6];
+#pragma unroll
+                    for (int k = 0; k < 6; k++) {
+                        Pl[k] = sm.P[cp][k][ty + 1][tx];
+                        Pr[k] = sm.P[cp][k][ty + 1][tx + 2];
+                        Pd[k] = sm.P[cp][k][ty][tx + 1];
+                        Pu[k] = sm.P[cp][k][ty + 2][tx + 1];
+                    }
+                    const V4<R> ul = sm.U[cs][ty + 1][tx], ur = sm.U[cs][ty + 1][tx + 2];
+                    const V4<R> ud = sm.U[cs][ty][tx + 1], uu = sm.U[cs][ty + 2][tx + 1];
+                    const R c0 = R(1) - R(3) * lam, c1 = R(0.5) * lam;
+                    R o[4];
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const R gxl = m == 0 ? ul.y : Pl[pidx(0, m - 1)];
+                        const R gxr = m == 0 ? ur.y : Pr[pidx(0, m - 1)];
+                        const R gyd = m == 0 ? ud.z : Pd[pidx(1, m - 1)];
+                        const R gyu = m == 0 ? uu.z : Pu[pidx(1, m - 1)];
+                        const R gzu = m == 0 ? un.w : Pn[pidx(2, m - 1)];
+                        const R sx = (comp(ul, m) + gxl) + (comp(ur, m) - gxr);
+                        const R sy = (comp(ud, m) + gyd) + (comp(uu, m) - gyu);
+                        const R sz = (comp(ub, m) + gzb[m]) + (comp(un, m) - gzu);
+                        o[m] = c0 * comp(uc, m) + c1 * ((sx + sy) + sz);
+                    }
+                    const int z = z0 + c - 1;
+                    st4(Og + (int64_t)z * sxy + own_col, V4<R>{o[0], o[1], o[2], o[3]});
+                }
+                ub = uc;
+                gzb[0] = uc.w;
+                gzb[1] = Pc[2];
+                gzb[2] = Pc[4];
+                gzb[3] = Pc[5];
+                continue;
+            }
             R Fzp[4];
             if constexpr (HLL) {
                 hll<R, STRICT, 2>(uc, Pc, sza, szb, un, Pn, szn_a, szn_b, Fzp);
@@ -743,33 +801,45 @@ __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z,
 // ahead): it is the one bound by DRAM latency
 constexpr int TP_STAGES_PM = 6;
 
+// rows padded by one cell: the halo columns' threads, one row apart, then
+// fall on distinct banks (a row of TX + 3 cells is 4 (TX + 3) words)
 template <int TX, int TY>
 struct TransportSmemPM {
-    V4<float> U[TP_STAGES_PM][TY + 2][TX + 2];
-    float4 H[2][4][TY + 2][TX + 2];    // per cell: Rx, Lx, Ry, Ly of two planes
+    V4<float> U[TP_STAGES_PM][TY + 2][TX + 3];
+    float4 H[2][4][TY + 2][TX + 3];    // per cell: Rx, Lx, Ry, Ly of two planes
 };
 
 template <int TX, int TY>
 constexpr size_t transport_pm_smem_bytes() { return sizeof(TransportSmemPM<TX, TY>); }
+
+// threads of the FP32 GLF kernel's block: TX x TY interior cells and the
+// 2 (TX + TY) halo cells of the tile, one cell each, rounded up to warps
+template <int TX, int TY>
+constexpr int transport_pm_threads() { return (TX * TY + 2 * (TX + TY) + 31) / 32 * 32; }
 
 // FP32 transport of the split form.  Same pipeline and work split as
 // k_transport; the unsplit GLF update is evaluated in its convex form
 //   U* = (1 - 3 lam) U + (lam/2) sum_d [ (U + G_d)(left_d) + (U - G_d)(right_d) ],
 // which equals U - lam sum_d (Phi_{d,+} - Phi_{d,-}) with Phi of Eq. e:glf.
 // Each cell computes its halves once per plane; x/y neighbours read them from
-// shared memory, the z halves stay in registers.  The tile (TX x TY columns,
-// one thread each) is a template parameter so the launch shape can be tuned
-// per box set; every shape computes each cell with the same arithmetic.
+// shared memory, the z halves stay in registers.  The tile (TX x TY columns)
+// is a template parameter so the launch shape can be tuned per box set;
+// every shape computes each cell with the same arithmetic.  The block holds
+// one thread per interior column and one per halo column (x: left and
+// right, y: bottom and top), so every thread evaluates exactly one closure
+// per plane and no warp waits at the plane's barrier for another's second
+// closure; the halo threads take no part in the update.
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 3)
+__global__ void __launch_bounds__(transport_pm_threads<TX, TY>(), 2)
 k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
 {
-    static_assert(2 * TX + 2 * TY <= TX * TY, "one halo cell per thread at most");
     constexpr int S = TP_STAGES_PM;
     extern __shared__ __align__(16) unsigned char tp_smem_raw[];
     TransportSmemPM<TX, TY> &sm = *reinterpret_cast<TransportSmemPM<TX, TY> *>(tp_smem_raw);
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int tid = threadIdx.x;
+    const bool interior = tid < TX * TY;
+    const int tx = interior ? tid % TX : 0, ty = interior ? tid / TX : 0;
     if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
 
     const int64_t ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
@@ -790,7 +860,7 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         const int x0 = ix * TX, y0 = iy * TY;
         const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
         const int x = x0 + tx, y = y0 + ty;
-        const bool act = (tx < ntx) && (ty < nty);
+        const bool act = interior && (tx < ntx) && (ty < nty);
         const int L = (z1 - z0) + 2;
         const V4<float> *Ug = reinterpret_cast<const V4<float> *>(B.U) + (int64_t)g * B.ncell;
         V4<float> *Og = reinterpret_cast<V4<float> *>(B.Us) + (int64_t)g * B.ncell;
@@ -798,13 +868,13 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         const float c0 = 1.0f - 3.0f * lam, c1 = 0.5f * lam;
         const int64_t sxy = (int64_t)nx * ny;
 
-        // halo cell of this thread and which half of it the tile needs:
+        // halo cell of a halo thread and which half of it the tile needs:
         // 0 = Rx (left column), 1 = Lx (right), 2 = Ry (bottom), 3 = Ly (top)
         int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0, hk = 0;
         float hin = 0.0f;                 // inflow ghost: beam density, sign = direction
         bool hif = false;                 // the halo cell is an inflow ghost
-        {
-            int t = tid;
+        if (!interior) {
+            int t = tid - TX * TY;
             if (t < nty) {
                 hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1; hk = 0;
                 if (sx < 0) {

@@ -71,27 +71,25 @@ __device__ RatesD rates_d_exact(const Phys &ph, double T)
 }
 
 // the tabulated rates of the forward pass (rates_tab), differentiated
-// through the interpolating polynomials in their variable y (y = 1 at the
-// interval's start, 2 at its end): d/dT = (dy/dT) d/dy, with
-// dy/dT = 1 / (interval width) = 2^(SUB - e)
-__device__ RatesD rates_d(const Phys &ph, const double *tab, double T)
+// through the interpolating polynomials in their variable t (t = -1 at the
+// interval's start, 1 at its end): d/dT = (dt/dT) d/dt, with
+// dt/dT = 2 / (interval width) = 2^(SUB + 1 - e)
+__device__ RatesD rates_d(const Phys &ph, const RateCoef *tab, double T)
 {
     if (!tab || ph.rates_const) return rates_d_exact(ph, T);
     int j;
     double t;
-    if (!tab_pos(T, j, t)) return rates_d_exact(ph, T);
+    float t32;
+    if (!tab_pos(T, j, t, t32)) return rates_d_exact(ph, T);
     const int e = (int)(__double_as_longlong(T) >> 52) - 1023;
-    const double dtdT = ldexp(1.0, RTD_TAB_SUB - e);    // dy/dT of the tables' variable y
-    const double *a = tab + (size_t)j * (RTD_TAB_NF * RTD_TAB_NC);
+    const double dtdT = ldexp(1.0, RTD_TAB_SUB + 1 - e);
+    const RateCoef *a = tab + (size_t)j * RTD_TAB_NF;
     double g[RTD_TAB_NF], dg[RTD_TAB_NF];
     for (int f = 0; f < RTD_TAB_NF; f++) {
-        const double *c = a + f * RTD_TAB_NC;
-        double p = c[RTD_TAB_NC - 1], dp = 0.0;
-        for (int i = RTD_TAB_NC - 2; i >= 0; i--) {
-            dp = dp * t + p;
-            p = p * t + c[i];
-        }
-        g[f] = p;
+        const RateCoef &c = a[f];
+        g[f] = tab_eval(&c, t, t32);
+        const double dp = fma(fma(fma(fma(5.0 * (double)c.c5, t, 4.0 * (double)c.c4), t,
+                                      3.0 * (double)c.c3), t, 2.0 * c.c2), t, c.c1);
         dg[f] = dp * dtdT;
     }
     RatesD r;
@@ -120,7 +118,7 @@ __device__ RatesD rates_d(const Phys &ph, const double *tab, double T)
 // ob = adjoint of its output, returns the adjoint of its input; adds to
 // bn0 and bS.
 template <int G>
-__device__ Cell<G> trial_adj(const Phys &ph, const double *tab, double nunit, double n0,
+__device__ Cell<G> trial_adj(const Phys &ph, const RateCoef *tab, double nunit, double n0,
                              const double *S, const Cell<G> &s, double dtau, const Cell<G> &ob,
                              double &bn0, double *bS)
 {
@@ -247,7 +245,7 @@ k_chem_adj(const BoxDev *__restrict__ boxes, Phys ph, const double *__restrict__
            double *lamx, double *lamT, double gx, double *dn0, double *dS, unsigned *err)
 {
     const BoxDev &B = boxes[0];
-    const double *tab = ph.rates_const ? nullptr : ph.rtab;
+    const RateCoef *tab = ph.rates_const ? nullptr : ph.rtab;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < B.ncell;
          c += (int64_t)gridDim.x * blockDim.x) {
         Cell<G> s;

@@ -56,8 +56,8 @@ inline void transport_layout(rtd::BoxDev &B, int ngroups, int variant = 0)
 cudaError_t fill_tune_state(void *U, int64_t n, cudaStream_t s);
 
 // rate tables of the chemistry kernel (rate_table.cu); false = unusable
-bool build_rate_table(bool ots, double *out);
-constexpr size_t rate_table_doubles() { return (size_t)RTD_TAB_NF * RTD_TAB_NINT * RTD_TAB_NC; }
+bool build_rate_table(bool ots, rtd::RateCoef *out);
+constexpr size_t rate_table_entries() { return (size_t)RTD_TAB_NF * RTD_TAB_NINT; }
 
 // reverse-mode kernels of one FP64 step on a periodic single box (adjoint.cu)
 cudaError_t chem_adj(int G, const rtd::BoxDev *boxes, const rtd::Phys &ph, const double *Us,

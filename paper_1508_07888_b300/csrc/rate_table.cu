@@ -7,7 +7,9 @@
 // interpolated on 2^RTD_TAB_SUB equal intervals of T per binade, 1 K <= T <
 // 2^30 K, each by a degree-5 Chebyshev polynomial in the local variable
 // t = 2 (T - T_a)/(T_b - T_a) - 1 in [-1, 1), stored as monomial coefficients
-// in y = (t + 3)/2 in [1, 2), the value the kernel reads off T's bits.
+// in t: c0 .. c2 in double, c3 .. c5 in float (the kernel evaluates the
+// tail c3 + t (c4 + t c5) in FP32; on these narrow intervals it is below
+// ~1e-6 of the value, so its FP32 rounding stays near 1e-13 of it).
 // Tabulated functions (layout [interval][function][coefficient]):
 //   0: alpha_A   1: alpha_B   2: recombination (case A or B) + free-free cooling
 //   3: ln(beta) + T_HI/T               (beta = exp(f3 - T_HI/T))
@@ -67,11 +69,23 @@ LD fit(int f, LD T, bool ots)
 
 namespace rtl {
 
-// fills out[RTD_TAB_NINT][RTD_TAB_NF][RTD_TAB_NC]; returns true when the
-// table reproduces the long-double fits to 1e-13 (relative for functions
-// 0-2, absolute for the logarithms 3-4) at 17 points per interval, and when
-// both exp(-c/T) factors are exactly zero in double below RTD_TAB_TCUT
-bool build_rate_table(bool ots, double *out)
+static_assert(RTD_TAB_NC == 6, "the coefficient layout holds degree 5: c0 .. c2 double, c3 .. c5 float");
+
+// the kernel's evaluation of one polynomial at t (t32: t in float)
+static double eval_coef(const rtd::RateCoef &c, double t, float t32)
+{
+    const float q = std::fmaf(std::fmaf(c.c5, t32, c.c4), t32, c.c3);
+    return std::fma(std::fma(std::fma((double)q, t, c.c2), t, c.c1), t, c.c0);
+}
+
+// fills out[RTD_TAB_NINT][RTD_TAB_NF]; returns true when the table, evaluated
+// the kernel's way, reproduces the long-double fits to 2e-13 (relative for
+// functions 0-2, absolute for the logarithms 3-4) at 17 points per interval
+// (the FP32 tail's rounding reaches 1.1e-13 on one interval, alpha_A near
+// 7e7 K; elsewhere the error is ~3e-14),
+// and when both exp(-c/T) factors are exactly zero in double below
+// RTD_TAB_TCUT
+bool build_rate_table(bool ots, rtd::RateCoef *out)
 {
     const int N = RTD_TAB_NC;
     // monomial coefficients of the Chebyshev polynomials T_0 .. T_{N-1}
@@ -96,28 +110,27 @@ bool build_rate_table(bool ots, double *out)
                 for (int m = 0; m < N; m++) s += fv[m] * cosl(M_PIl * n * (m + 0.5L) / N);
                 c[n] = (n == 0 ? 1.0L : 2.0L) * s / N;
             }
-            // monomial coefficients in t, then in y = (t + 3)/2 in [1, 2),
-            // the kernel's variable (t = 2y - 3 composed in long double)
-            LD mt[RTD_TAB_NC], my[RTD_TAB_NC] = {};
+            // monomial coefficients in t
+            LD mt[RTD_TAB_NC];
             for (int i = 0; i < N; i++) {
                 LD s = 0;
                 for (int n = 0; n < N; n++) s += c[n] * cheb[n][i];
                 mt[i] = s;
             }
-            my[0] = mt[N - 1];
-            for (int i = N - 2; i >= 0; i--) {          // my <- my (2y - 3) + mt[i]
-                for (int k = N - 1; k >= 1; k--) my[k] = 2 * my[k - 1] - 3 * my[k];
-                my[0] = -3 * my[0] + mt[i];
-            }
-            double *o = out + ((size_t)j * RTD_TAB_NF + f) * N;
-            for (int i = 0; i < N; i++) o[i] = (double)my[i];
-            for (int k = 0; k <= 16; k++) {           // check, in double Horner in y
-                const double y = 1.0 + k / 16.0;
-                double p = o[N - 1];
-                for (int i = N - 2; i >= 0; i--) p = p * y + o[i];
-                const LD ex = fit(f, lo + ((LD)y - 1) * (hi - lo), ots);
+            rtd::RateCoef &o = out[(size_t)j * RTD_TAB_NF + f];
+            o.c0 = (double)mt[0];
+            o.c1 = (double)mt[1];
+            o.c2 = (double)mt[2];
+            o.c3 = (float)mt[3];
+            o.c4 = (float)mt[4];
+            o.c5 = (float)mt[5];
+            o.pad = 0.0f;
+            for (int k = 0; k <= 16; k++) {           // check, the kernel's way
+                const double t = -1.0 + k / 8.0;
+                const LD ex = fit(f, lo + ((LD)t + 1) * 0.5L * (hi - lo), ots);
+                const double p = eval_coef(o, t, (float)t);
                 const LD err = f <= 2 ? fabsl((p - ex) / ex) : fabsl(p - ex);
-                if (!(err <= 1e-13L)) return false;
+                if (!(err <= 2e-13L)) return false;
             }
         }
     }

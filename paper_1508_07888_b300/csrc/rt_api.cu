@@ -60,7 +60,7 @@ struct rt_handle {
     unsigned *d_done = nullptr;              // per-box group counters of the fused reduction
     rtd::DiagPart *d_gpart = nullptr;        // per-group partials
     unsigned *d_gdone = nullptr;             // per-group item counters
-    double *d_rtab = nullptr;                // rate table (null: fits evaluated directly)
+    rtd::RateCoef *d_rtab = nullptr;         // rate table (null: fits evaluated directly)
     double *d_hll_d = nullptr;               // HLL wave speeds (FP64, FP32 copies)
     float *d_hll_f = nullptr;
     float4 *d_hll_f4 = nullptr;
@@ -463,10 +463,10 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMalloc(&h->d_done, sizeof(unsigned) * nboxes));
                 CU(h, cudaMemset(h->d_done, 0, sizeof(unsigned) * nboxes));
                 if (!p->rates_const) {
-                    std::vector<double> tab(rtl::rate_table_doubles());
+                    std::vector<rtd::RateCoef> tab(rtl::rate_table_entries());
                     if (rtl::build_rate_table(p->ots != 0, tab.data())) {
-                        CU(h, cudaMalloc(&h->d_rtab, sizeof(double) * tab.size()));
-                        CU(h, cudaMemcpy(h->d_rtab, tab.data(), sizeof(double) * tab.size(),
+                        CU(h, cudaMalloc(&h->d_rtab, sizeof(rtd::RateCoef) * tab.size()));
+                        CU(h, cudaMemcpy(h->d_rtab, tab.data(), sizeof(rtd::RateCoef) * tab.size(),
                                          cudaMemcpyHostToDevice));
                         h->ph.rtab = h->d_rtab;
                     }

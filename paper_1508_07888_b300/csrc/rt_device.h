@@ -36,7 +36,9 @@
 // rate tables: piecewise polynomials in T.  T in [2^E0, 2^E1) falls in
 // interval j = 2^SUB (e - E0) + (top SUB bits of T's mantissa), e = T's binary
 // exponent, so the index and the local variable t in [-1, 1) come from T's
-// bits (no logarithm); 2^SUB equal intervals per binade (see rate_table.cu)
+// bits (no logarithm); 2^SUB equal intervals per binade (see rate_table.cu).
+// Each polynomial p(t) = c0 + t (c1 + t (c2 + t q)) keeps c0 .. c2 in FP64
+// and its tail q = c3 + t (c4 + t c5), terms below ~1e-6 of p, in FP32.
 #define RTD_TAB_NF 5         // aA, aB, kR, ln(beta) + T_HI/T, ln(cce) + 118348/T
 #define RTD_TAB_E0 0         // 1 K
 #define RTD_TAB_E1 30        // 2^30 K = 1.07e9 K
@@ -48,6 +50,12 @@
 #define RTD_TAB_TCUT 155.0
 
 namespace rtd {
+
+// coefficients of one tabulated polynomial (one function on one interval)
+struct RateCoef {
+    double c0, c1, c2;
+    float c3, c4, c5, pad;
+};
 
 // physical constants (cgs)
 constexpr double KB = 1.380649e-16;         // erg/K
@@ -66,7 +74,7 @@ struct Phys {
     double alphaA, alphaB, beta;  // rates_const values
     double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250
     double ln2THI;                // ln(2 T_HI)
-    const double *rtab;           // rate table [RTD_TAB_NINT][RTD_TAB_NF][RTD_TAB_NC] or null
+    const RateCoef *rtab;         // rate table [RTD_TAB_NINT][RTD_TAB_NF] or null
     int flux;                     // RTD_FLUX_GLF / RTD_FLUX_HLL
     const float *hll_f;           // HLL wave speeds [RTD_HLL_NF + 1][RTD_HLL_NM + 1], FP32 copy
     const double *hll_d;          // the same in FP64

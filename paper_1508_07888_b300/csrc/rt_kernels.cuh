@@ -28,6 +28,7 @@ using rtd::DiagBuf;
 using rtd::DiagPart;
 using rtd::FineDev;
 using rtd::Phys;
+using rtd::RateCoef;
 
 // ------------------------------------------------------------- vector I/O
 template <typename R>
@@ -1296,11 +1297,13 @@ struct Rates {
     double aA, aB, beta;   // cm^3/s
     double kR;             // cooling per n_e n_HII: recombination + bremsstrahlung
     double kC;             // cooling per n_e n_HI: collisional ionisation + excitation
+    bool cold;             // beta = kC = 0 exactly (tabulated rates below RTD_TAB_TCUT)
 };
 
 __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
 {
     Rates r;
+    r.cold = false;
     if (ph.rates_const) {
         r.aA = ph.alphaA; r.aB = ph.alphaB; r.beta = ph.beta;
         r.kR = 0.0; r.kC = 0.0;
@@ -1330,55 +1333,60 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
 }
 
 // Position of T in the rate tables (rate_table.cu): interval j and local
-// variable y in [1, 2), both from T's bits.  For T = 2^e (1 + m), m in [0, 1),
-// j = 2^SUB (e - E0) + floor(2^SUB m) and y = 1 + frac(2^SUB m), exactly (the
-// tables hold their polynomials in y, so no arithmetic forms it).
+// variable t in [-1, 1), both from T's bits.  For T = 2^e (1 + m), m in
+// [0, 1), j = 2^SUB (e - E0) + floor(2^SUB m) and y = 1 + frac(2^SUB m) in
+// [1, 2) exactly; t = 2 y - 3 (exact), and t32 = the same with y's mantissa
+// cut to float's 23 bits (exact in float; the FP32 tail needs ~1e-6 of t).
 // Returns false outside [2^E0, 2^E1) (and for T <= 0, NaN, Inf).
-__device__ __forceinline__ bool tab_pos(double T, int &j, double &t)
+__device__ __forceinline__ bool tab_pos(double T, int &j, double &t, float &t32)
 {
     const long long bits = __double_as_longlong(T);
     const int e = (int)(bits >> 52) - 1023;
     if (e < RTD_TAB_E0 || e >= RTD_TAB_E1) return false;
     constexpr int low = 52 - RTD_TAB_SUB;
     j = ((e - RTD_TAB_E0) << RTD_TAB_SUB) + (int)((bits >> low) & ((1 << RTD_TAB_SUB) - 1));
-    // 1 + frac in [1, 2): the mantissa bits below the top SUB, moved up
-    t = __longlong_as_double(0x3FF0000000000000ll | ((bits & ((1ll << low) - 1)) << RTD_TAB_SUB));
+    // y: the mantissa bits below the top SUB, moved up
+    const long long ym = (bits & ((1ll << low) - 1)) << RTD_TAB_SUB;
+    t = fma(2.0, __longlong_as_double(0x3FF0000000000000ll | ym), -3.0);
+    t32 = fmaf(2.0f, __int_as_float(0x3F800000 | (int)(ym >> 29)), -3.0f);
     return true;
 }
 
-__device__ __forceinline__ double tab_poly(const double *c, double t)
+// p(t) = c0 + t (c1 + t (c2 + t q)) with the tail q = c3 + t (c4 + t c5) in FP32
+__device__ __forceinline__ double tab_eval(const RateCoef *c, double t, float t32)
 {
-    double p = __ldg(c + RTD_TAB_NC - 1);
-#pragma unroll
-    for (int i = RTD_TAB_NC - 2; i >= 0; i--) p = p * t + __ldg(c + i);
-    return p;
+    const float q = fmaf(fmaf(__ldg(&c->c5), t32, __ldg(&c->c4)), t32, __ldg(&c->c3));
+    return fma(fma(fma(f2d(q), t, __ldg(&c->c2)), t, __ldg(&c->c1)), t, __ldg(&c->c0));
 }
 
 // The same rates from the tables built at set-up (rate_table.cu): degree-5
-// Chebyshev interpolants on 64 intervals of T per binade, accurate to ~2e-14
+// Chebyshev interpolants on 64 intervals of T per binade, accurate to ~3e-14
 // relative; beta and the excitation cooling keep their exp(-c/T) factor
 // exact, and below RTD_TAB_TCUT, where both factors are exactly zero in
 // double, they are not evaluated.  Outside 1 K .. 2^30 K the fits are
 // evaluated directly.
 template <bool STRICT>
-__device__ __forceinline__ Rates rates_tab(const Phys &ph, const double *tab, double T)
+__device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, double T)
 {
     int j;
     double t;
-    if (!tab_pos(T, j, t)) return rates_at(ph, T);
-    const double *a = tab + (size_t)j * (RTD_TAB_NF * RTD_TAB_NC);
+    float t32;
+    if (!tab_pos(T, j, t, t32)) return rates_at(ph, T);
+    const RateCoef *a = tab + (size_t)j * RTD_TAB_NF;
     Rates r;
-    r.aB = tab_poly(a + 1 * RTD_TAB_NC, t);
-    r.aA = ph.ots ? r.aB : tab_poly(a, t);
-    r.kR = tab_poly(a + 2 * RTD_TAB_NC, t);
+    r.cold = false;
+    r.aB = tab_eval(a + 1, t, t32);
+    r.aA = ph.ots ? r.aB : tab_eval(a, t, t32);
+    r.kR = tab_eval(a + 2, t, t32);
     if (dbits(T) >= dbits(RTD_TAB_TCUT)) {       // T >= TCUT (both positive)
         const double invT = STRICT ? 1.0 / T : rcp_nr(T);
-        r.beta = exp(tab_poly(a + 3 * RTD_TAB_NC, t) - rtd::T_HI * invT);
-        const double cce = exp(tab_poly(a + 4 * RTD_TAB_NC, t) - 118348.0 * invT);
+        r.beta = exp(tab_eval(a + 3, t, t32) - rtd::T_HI * invT);
+        const double cce = exp(tab_eval(a + 4, t, t32) - 118348.0 * invT);
         r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
     } else {
         r.beta = 0.0;
         r.kC = 0.0;
+        r.cold = true;
     }
     return r;
 }
@@ -1476,6 +1484,7 @@ struct CellK {
     double n02, K, cvn; // n0^2, n0^2 / nunit (without OTS), (3/2) kB n0
     double cvn2;        // 3 kB n0
     float n0f, S32[G];  // n0 and the source terms in FP32 (FP32 photon update)
+    float K32;          // K in FP32
 };
 
 // DEFER: F is not carried through the trial (nothing in the chemistry reads
@@ -1484,17 +1493,20 @@ struct CellK {
 // sigma_N,i x_HI n0 dtau) and the scale of F, runs in FP32, the precision
 // N and F are stored in; x_HI, T, the rates and the photoionisation,
 // heating and cooling sums stay FP64
+// rec32 (N32 only): the recombination photons of group 1 per unit time in
+// FP32, (alpha_A - alpha_B) x^2 n0^2 / nunit, formed once per sub-cycle (it
+// depends on the sub-cycle's start state only)
 template <int G, bool DEFER, bool N32, typename FT>
 __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B, const CellK<G> &k,
                                                 double n0, const double *S, const Rates &r,
                                                 double alpha, const Cell<G> &s, double e0,
-                                                double dtau, Cell<G> &o, double &e1, FT *rdo)
+                                                double dtau, Cell<G> &o, double &e1, FT *rdo,
+                                                float rec32)
 {
     const double x = 1.0 - s.xHI;
     if constexpr (N32) {
         const float dt32 = d2f(dtau);
         const float q32 = (d2f(s.xHI) * k.n0f) * dt32;
-        const float rec32 = ph.ots ? 0.0f : d2f((r.aA - r.aB) * x * x * k.K);
 #pragma unroll
         for (int i = 0; i < G; i++) {
             const float rd = __frcp_rn(fmaf(ph.csig_f[i], q32, 1.0f));
@@ -1524,7 +1536,9 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
 #pragma unroll
     for (int i = 1; i < G; i++) gam = fma(B.gN[i], o.N[i], gam);
     const double xnum = fma(alpha * x * x, n0 * dtau, s.xHI);
-    const double xden = fma(dtau, fma(r.beta * x, n0, gam), 1.0);
+    // cold gas: beta = 0 exactly, the collisional term is skipped (warps of
+    // cold cells take this branch together)
+    const double xden = r.cold ? fma(dtau, gam, 1.0) : fma(dtau, fma(r.beta * x, n0, gam), 1.0);
     o.xHI = xnum * rcp_nr(xden);
     if (ph.isothermal) {
         o.T = s.T;
@@ -1535,7 +1549,8 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
 #pragma unroll
     for (int i = 1; i < G; i++) hs = fma(B.hN[i], o.N[i], hs);
     const double x1 = 1.0 - o.xHI;
-    const double cool = k.n02 * x1 * fma(x1, r.kR, o.xHI * r.kC);   // Lambda(n0, x^{p+1}, T^p)
+    // Lambda(n0, x^{p+1}, T^p); kC = 0 exactly in cold gas
+    const double cool = r.cold ? k.n02 * x1 * (x1 * r.kR) : k.n02 * x1 * fma(x1, r.kR, o.xHI * r.kC);
     e1 = fma(dtau, fma(o.xHI * n0, hs, -cool), e0);
     o.T = e1 * rcp_nr(fma(-k.cvn, o.xHI, k.cvn2));    // (3/2) kB n0 (2 - x_HI)
 }
@@ -1561,7 +1576,7 @@ __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
 }
 
 template <int G, bool STRICT, class Trace = NoTrace, typename FT = double>
-__device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDev &B, double n0,
+__device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,
                                   int &ncyc, Trace *tr = nullptr, FT *fac = nullptr)
 {
@@ -1576,7 +1591,10 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         k.cvn = (1.5 * rtd::KB) * n0;
         k.cvn2 = 2.0 * k.cvn;
     }
-    if (!STRICT) k.n0f = d2f(n0);
+    if (!STRICT) {
+        k.n0f = d2f(n0);
+        k.K32 = d2f(k.K);
+    }
     if (N32) {
 #pragma unroll
         for (int i = 0; i < G; i++) {
@@ -1650,12 +1668,18 @@ __device__ unsigned int chem_span(const Phys &ph, const double *tab, const BoxDe
         Cell<G> o;
         double ep, e1;
         FT rd[G];
+        float rec32 = 0.0f;
+        if (N32 && !ph.ots) {
+            const float x32 = d2f(1.0 - s.xHI);
+            rec32 = (d2f(r.aA) - d2f(r.aB)) * (x32 * x32) * k.K32;
+        }
         for (int h = 0;; h++) {
             if (STRICT) {
                 chem_trial<G, true>(ph, B.nunit, B.inv_nunit, n0, S, r, alpha, s, dtau, o, ep, e1);
             } else {
                 ep = ep0;
-                chem_trial_fast<G, DEFER, N32, FT>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd);
+                chem_trial_fast<G, DEFER, N32, FT>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd,
+                                                   rec32);
             }
             if (ph.isothermal) break;
             const bool finite = STRICT ? isfinite(e1) : finite_bits(e1);
@@ -1879,7 +1903,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
        DiagBuf db)
 {
     const int lane = threadIdx.x & 31;
-    const double *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
+    const RateCoef *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
     // split form: each row of 32 cells' inputs (U* of every group, x_HI, T,
     // n0) is staged into the warp's shared-memory buffers by cp.async while
     // the lanes work on the previous row, so the DRAM latency of a cell's
@@ -2133,7 +2157,7 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
             int64_t nitems, Phys ph, Ctl *ctl)
 {
     const int lane = threadIdx.x & 31;
-    const double *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
+    const RateCoef *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
     for (;;) {
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(&ctl->fine_next, 1ull);

@@ -7,8 +7,8 @@
 //      on exponents around the float range with exact ties, near-ties and
 //      carries into the exponent, in the normal and the subnormal results;
 //   3. the rate table (rate_table.cu) evaluated the kernel's way (interval
-//      and local variable from T's bits) against the rate fits in long
-//      double at random temperatures.
+//      and local variable from T's bits, the polynomial's tail in FP32)
+//      against the rate fits in long double at random temperatures.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -85,7 +85,7 @@ int main()
     fails += bad2 != 0;
 
     for (int ots = 0; ots < 2; ots++) {
-        std::vector<double> tab(rtl::rate_table_doubles());
+        std::vector<rtd::RateCoef> tab(rtl::rate_table_entries());
         if (!rtl::build_rate_table(ots != 0, tab.data())) { printf("table build failed\n"); return 1; }
         if (ots) continue;                      // the OTS table differs in kR only
         std::uniform_real_distribution<double> lu(0.0, 30.0 * 0.6931471805599453);
@@ -97,15 +97,19 @@ int main()
             if (e < RTD_TAB_E0 || e >= RTD_TAB_E1) continue;
             const int low = 52 - RTD_TAB_SUB;
             const int j = ((e - RTD_TAB_E0) << RTD_TAB_SUB) + (int)((bits >> low) & ((1 << RTD_TAB_SUB) - 1));
-            const double y = rtk::dfrom(0x3FF0000000000000ull | ((bits & ((1ull << low) - 1)) << RTD_TAB_SUB));
-            const double t = y;                  // the tables' variable
-            const double *a = tab.data() + (size_t)j * RTD_TAB_NF * RTD_TAB_NC;
+            // the kernel's local variable: t = 2 y - 3, and t32 from y's top 23 mantissa bits
+            const unsigned long long ym = (bits & ((1ull << low) - 1)) << RTD_TAB_SUB;
+            const double t = std::fma(2.0, rtk::dfrom(0x3FF0000000000000ull | ym), -3.0);
+            const unsigned int y32 = 0x3F800000u | (unsigned int)(ym >> 29);
+            float y32f;
+            std::memcpy(&y32f, &y32, 4);
+            const float t32 = std::fmaf(2.0f, y32f, -3.0f);
+            const rtd::RateCoef *a = tab.data() + (size_t)j * RTD_TAB_NF;
             double gv[RTD_TAB_NF];
             for (int f = 0; f < RTD_TAB_NF; f++) {
-                const double *c = a + f * RTD_TAB_NC;
-                double p = c[RTD_TAB_NC - 1];
-                for (int i = RTD_TAB_NC - 2; i >= 0; i--) p = std::fma(p, t, c[i]);
-                gv[f] = p;
+                const rtd::RateCoef &c = a[f];
+                const float q = std::fmaf(std::fmaf(c.c5, t32, c.c4), t32, c.c3);
+                gv[f] = std::fma(std::fma(std::fma((double)q, t, c.c2), t, c.c1), t, c.c0);
             }
             const LD ex3[3] = {aA(T), aB(T), kR(T)};
             for (int f = 0; f < 3; f++) w[f] = std::fmax(w[f], (double)fabsl((gv[f] - ex3[f]) / ex3[f]));
@@ -121,9 +125,10 @@ int main()
             }
         }
         printf("table: max rel err aA %.2e aB %.2e kR %.2e beta %.2e cce %.2e\n", w[0], w[1], w[2], w[3], w[4]);
-        // alpha, kR: interpolation error; beta, cce: exp of arguments up to
-        // ~800 in magnitude, whose own rounding (~1e-13 relative) dominates
-        fails += !(w[0] < 3e-14 && w[1] < 3e-14 && w[2] < 3e-14 && w[3] < 1e-12 && w[4] < 1e-12);
+        // alpha, kR: interpolation error and the FP32 tail's rounding (the
+        // table's own bound, 2e-13); beta, cce: exp of arguments up to ~800
+        // in magnitude, whose own rounding (~1e-13 relative) dominates
+        fails += !(w[0] < 2e-13 && w[1] < 2e-13 && w[2] < 2e-13 && w[3] < 1e-12 && w[4] < 1e-12);
     }
     printf(fails ? "FAIL\n" : "OK\n");
     return fails ? 1 : 0;

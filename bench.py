@@ -597,8 +597,11 @@ def chem_flops_per_subcycle(G: int, ots: bool, split: bool = True) -> float:
     """Algorithmic FP64 flops of one accepted chemistry sub-cycle (a5-a8 and
     the rate fits), counted from the formulas as written.  The split form
     runs the photon update of each group (1 + c sigma x_HI n0 dtau: 4, (N + S
-    dtau)/den: 3, F/den: 3) in FP32, 10 G flops that are not FP64 work."""
-    return (12.0 if split else 22.0) * G + 111.0 - (14.0 if ots else 0.0)
+    dtau)/den: 3, F/den: 3) in FP32, 10 G flops that are not FP64 work, and
+    the recombination photons of group 1 ((alpha_A - alpha_B) x^2 n0^2 /
+    nunit: 7 flops, absent with OTS) too.  OTS also drops the alpha_A fit (7)."""
+    base = 111.0 - (14.0 if ots else (7.0 if split else 0.0))
+    return (12.0 if split else 22.0) * G + base
 
 
 # FP64 flops of one GLF transport cell-group, counted from the formulas as
@@ -797,9 +800,9 @@ def main():
     # beta 11, excitation cooling 6, k_C 2; OTS needs no alpha_A), the dtau
     # estimate 4 G + 19, the trial 18 G + 47 (7 of them the recombination
     # photons of group 1 without OTS) -> 22 G + 111; the split form's photon
-    # update (10 G of the trial's flops) runs in FP32 -> 12 G + 111 FP64
-    # flops, against the FP64 pipe peak: 148 SMs x 2 DFMA/clock x 2 flop x
-    # 2032 MHz
+    # update (10 G of the trial's flops) and the recombination photons (7)
+    # run in FP32 -> 12 G + 104 FP64 flops, against the FP64 pipe peak: 148
+    # SMs x 2 DFMA/clock x 2 flop x 2032 MHz
     fp64_peak = fp64_peak_tflops()
     c_flops = chem_flops_per_subcycle(G, w.ots) * box.ncell * mean_sub
     c_ach = c_flops / (per_launch["chemistry"] * 1e-3) / 1e12
@@ -808,7 +811,8 @@ def main():
               "traffic": traffic.get("chemistry"),
               "algorithmic_flops_per_launch": c_flops, "mean_subcycles": mean_sub,
               "peak_note": "FP64 pipe, derived from ncu's 2 DFMA/clock/SM and the 2032 MHz "
-                           "maximum clock"}
+                           "maximum clock (a DFMA-loop kernel measured 1.97 DFMA/clock/SM at "
+                           "the clock it ran at)"}
     dominant = max(shares, key=shares.get) if shares else "transport"
     roofline = roof_c if dominant == "chemistry" else roof_t
 

@@ -87,7 +87,8 @@ static cudaError_t transport_hll(const Launch &L, int zc, const rtd::Phys &ph, r
 {
     cudaError_t e = hll_attr<TX, TY>();
     if (e != cudaSuccess) return e;
-    rtk::k_transport_hll<TX, TY><<<L.grid, dim3(TX, TY), rtk::transport_hll_smem_bytes<TX, TY>(), L.stream>>>(
+    rtk::k_transport_hll<TX, TY><<<L.grid, rtk::transport_pm_threads<TX, TY>(),
+                                   rtk::transport_hll_smem_bytes<TX, TY>(), L.stream>>>(
         L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
     return cudaSuccess;
 }
@@ -207,7 +208,8 @@ template <int TX, int TY>
 static int hll_occupancy()
 {
     hll_attr<TX, TY>();
-    return occ((const void *)rtk::k_transport_hll<TX, TY>, TX * TY, rtk::transport_hll_smem_bytes<TX, TY>());
+    return occ((const void *)rtk::k_transport_hll<TX, TY>, rtk::transport_pm_threads<TX, TY>(),
+               rtk::transport_hll_smem_bytes<TX, TY>());
 }
 
 template <int TX, int TY>

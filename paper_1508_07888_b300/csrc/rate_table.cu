@@ -83,8 +83,9 @@ static double eval_coef(const rtd::RateCoef &c, double t, float t32)
 // functions 0-2, absolute for the logarithms 3-4) at 17 points per interval
 // (the FP32 tail's rounding reaches 1.1e-13 on one interval, alpha_A near
 // 7e7 K; elsewhere the error is ~3e-14),
-// and when both exp(-c/T) factors are exactly zero in double below
-// RTD_TAB_TCUT
+// when both exp(-c/T) factors are exactly zero in double below
+// RTD_TAB_TCUT, and when the terms they make are below 2^-60 of what they
+// enter below RTD_TAB_TWARM at n0 dtau <= RTD_TAB_NDMAX
 bool build_rate_table(bool ots, rtd::RateCoef *out)
 {
     const int N = RTD_TAB_NC;
@@ -138,6 +139,24 @@ bool build_rate_table(bool ots, rtd::RateCoef *out)
     const double tc = RTD_TAB_TCUT;
     if (std::exp((double)fit_lnbeta_plus(tc) - (double)THI / tc) != 0.0) return false;
     if (std::exp((double)fit_lncce_plus(tc) - 118348.0 / tc) != 0.0) return false;
+    // below RTD_TAB_TWARM with n0 dtau <= RTD_TAB_NDMAX: beta n0 dtau (against
+    // 1 in the x_HI denominator) and kC n0 dtau / (1.5 kB T) (the cooling
+    // against the internal energy, x_HI, 1 - x_HI <= 1) below 2^-60; both
+    // grow with T on [TCUT, TWARM], checked on a fine grid
+    const LD kB = 1.380649e-16L, lim = ldexpl(1.0L, -60);
+    LD prev_b = 0, prev_c = 0;
+    for (int k = 0; k <= 4096; k++) {
+        const LD T = RTD_TAB_TCUT + (RTD_TAB_TWARM - RTD_TAB_TCUT) * k / 4096.0L;
+        const LD b = expl(fit_lnbeta_plus(T) - THI / T);
+        const LD kc = kB * THI * b + expl(fit_lncce_plus(T) - 118348.0L / T);
+        if (b < prev_b || kc < prev_c) return false;
+        prev_b = b;
+        prev_c = kc;
+    }
+    const LD Tw = RTD_TAB_TWARM;
+    const LD bw = expl(fit_lnbeta_plus(Tw) - THI / Tw);
+    const LD cw = (kB * THI * bw + expl(fit_lncce_plus(Tw) - 118348.0L / Tw)) / (1.5L * kB * Tw);
+    if (!((LD)RTD_TAB_NDMAX * bw <= lim && (LD)RTD_TAB_NDMAX * cw <= lim)) return false;
     return true;
 }
 

@@ -48,6 +48,14 @@
 // below this temperature both exp(-T_HI/T) and exp(-118348/T) factors of the
 // fits are exactly zero in double precision (checked when the table is built)
 #define RTD_TAB_TCUT 155.0
+// below this temperature beta < 1e-77 cm^3/s and kC / (1.5 kB T) < 2e-57
+// cm^3/s, so in a cell with n0 dtau <= RTD_TAB_NDMAX (cm^-3 s) the
+// collisional ionisation and cooling terms are below 2^-60 of the terms
+// they enter (1 in the x_HI denominator, the internal energy), below any
+// FP64 rounding; the chemistry then treats the cell as cold (both bounds
+// checked when the table is built)
+#define RTD_TAB_TWARM 1000.0
+#define RTD_TAB_NDMAX 1e38f
 
 namespace rtd {
 

@@ -1074,12 +1074,12 @@ __device__ __forceinline__ void hll_cell(const float4 *__restrict__ tab, const V
 }
 
 template <int TX, int TY>
-struct TransportSmemHLL {
-    V4<float> U[TP_STAGES][TY + 2][TX + 2];
-    float4 Gx[2][TY + 2][TX + 2];      // G_x of two planes
-    float4 Gy[2][TY + 2][TX + 2];      // G_y of two planes
-    float2 Sx[2][TY + 2][TX + 2];      // (min, max) speeds along x of two planes
-    float2 Sy[2][TY + 2][TX + 2];      // along y
+struct TransportSmemHLL {              // rows padded by one cell, as in k_transport_pm
+    V4<float> U[TP_STAGES][TY + 2][TX + 3];
+    float4 Gx[2][TY + 2][TX + 3];      // G_x of two planes
+    float4 Gy[2][TY + 2][TX + 3];      // G_y of two planes
+    float2 Sx[2][TY + 2][TX + 3];      // (min, max) speeds along x of two planes
+    float2 Sy[2][TY + 2][TX + 3];      // along y
 };
 
 template <int TX, int TY>
@@ -1091,18 +1091,21 @@ constexpr size_t transport_hll_smem_bytes() { return sizeof(TransportSmemHLL<TX,
 // in registers, and the z-face flux carried from plane to plane.  Halo cells
 // evaluate the one axis their face needs; reflective halos keep their
 // negated state in shared memory (the flux reads U of both sides).  After the
-// update |F| <= N is restored as in k_transport.
+// update |F| <= N is restored as in k_transport.  The block holds one thread
+// per interior and per halo column (the layout of k_transport_pm), so every
+// thread evaluates one cell per plane.
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 3)
+__global__ void __launch_bounds__(transport_pm_threads<TX, TY>(), 2)
 k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
 {
-    static_assert(2 * TX + 2 * TY <= TX * TY, "one halo cell per thread at most");
     constexpr int S = TP_STAGES;
     extern __shared__ __align__(16) unsigned char tp_smem_raw[];
     TransportSmemHLL<TX, TY> &sm = *reinterpret_cast<TransportSmemHLL<TX, TY> *>(tp_smem_raw);
     const float4 *__restrict__ tab = ph.hll_f4;
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int tid = threadIdx.x;
+    const bool interior = tid < TX * TY;
+    const int tx = interior ? tid % TX : 0, ty = interior ? tid / TX : 0;
     if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
 
     const int64_t ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
@@ -1123,7 +1126,7 @@ k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, in
         const int x0 = ix * TX, y0 = iy * TY;
         const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
         const int x = x0 + tx, y = y0 + ty;
-        const bool act = (tx < ntx) && (ty < nty);
+        const bool act = interior && (tx < ntx) && (ty < nty);
         const int L = (z1 - z0) + 2;
         const V4<float> *Ug = reinterpret_cast<const V4<float> *>(B.U) + (int64_t)g * B.ncell;
         V4<float> *Og = reinterpret_cast<V4<float> *>(B.Us) + (int64_t)g * B.ncell;
@@ -1135,8 +1138,8 @@ k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, in
         int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0, hk = 0;
         float hin = 0.0f;
         bool hif = false;
-        {
-            int t = tid;
+        if (!interior) {
+            int t = tid - TX * TY;
             if (t < nty) {
                 hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1; hk = 0;
                 if (sx < 0) {
@@ -1297,7 +1300,7 @@ struct Rates {
     double aA, aB, beta;   // cm^3/s
     double kR;             // cooling per n_e n_HII: recombination + bremsstrahlung
     double kC;             // cooling per n_e n_HI: collisional ionisation + excitation
-    bool cold;             // beta = kC = 0 exactly (tabulated rates below RTD_TAB_TCUT)
+    bool cold;             // beta = kC = 0 (tabulated rates below the cut of rates_tab)
 };
 
 __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
@@ -1365,8 +1368,11 @@ __device__ __forceinline__ double tab_eval(const RateCoef *c, double t, float t3
 // exact, and below RTD_TAB_TCUT, where both factors are exactly zero in
 // double, they are not evaluated.  Outside 1 K .. 2^30 K the fits are
 // evaluated directly.
+// warm: the cut is RTD_TAB_TWARM (the cell's n0 dtau allows it: below it the
+// two factors' terms are below 2^-60 of what they enter), else RTD_TAB_TCUT
 template <bool STRICT>
-__device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, double T)
+__device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, double T,
+                                           bool warm = false)
 {
     int j;
     double t;
@@ -1378,7 +1384,7 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, 
     r.aB = tab_eval(a + 1, t, t32);
     r.aA = ph.ots ? r.aB : tab_eval(a, t, t32);
     r.kR = tab_eval(a + 2, t, t32);
-    if (dbits(T) >= dbits(RTD_TAB_TCUT)) {       // T >= TCUT (both positive)
+    if (dbits(T) >= (warm ? dbits(RTD_TAB_TWARM) : dbits(RTD_TAB_TCUT))) {   // T >= cut (both positive)
         const double invT = STRICT ? 1.0 / T : rcp_nr(T);
         r.beta = exp(tab_eval(a + 3, t, t32) - rtd::T_HI * invT);
         const double cce = exp(tab_eval(a + 4, t, t32) - 118348.0 * invT);
@@ -1575,10 +1581,13 @@ __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
     s.T = o.T;
 }
 
+// warm_cut (fast forms): n0 dtau <= RTD_TAB_NDMAX for every dtau of the span,
+// so the rates may take the RTD_TAB_TWARM cut
 template <int G, bool STRICT, class Trace = NoTrace, typename FT = double>
 __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,
-                                  int &ncyc, Trace *tr = nullptr, FT *fac = nullptr)
+                                  int &ncyc, Trace *tr = nullptr, FT *fac = nullptr,
+                                  bool warm_cut = false)
 {
     constexpr bool DEFER = !STRICT && std::is_same<Trace, NoTrace>::value;
     constexpr bool N32 = DEFER && std::is_same<FT, float>::value;
@@ -1605,7 +1614,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
     }
     double rem = span;                          // span - tau, tau = 0 in the first sub-cycle
     for (;;) {
-        const Rates r = tab ? rates_tab<STRICT>(ph, tab, s.T) : rates_at(ph, s.T);
+        const Rates r = tab ? rates_tab<STRICT>(ph, tab, s.T, !STRICT && warm_cut) : rates_at(ph, s.T);
         const double alpha = ph.ots ? r.aB : r.aA;
         double dtau = rem;
         bool last = true;
@@ -2027,12 +2036,17 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 ca1 = ph.acos[ctl->step + 1];
                 cosmo_in<G, STRICT>(ca, s, S, n0c, span, B.dt);
             }
+            // the warm cut holds for every sub-cycle when n0 times the whole
+            // step is within its bound (in FP32; an overflow to Inf fails)
+            const bool warm_cut = !STRICT && d2f(n0c) * d2f(span) <= RTD_TAB_NDMAX;
             if (ph.nsub > 0) {
                 const double h = span / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
+                    err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
+                                                             warm_cut);
             } else {
-                err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
+                err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
+                                                         warm_cut);
             }
             if (ph.cosmo) {
                 cosmo_out<G, STRICT>(ca, ca1, s);
@@ -2204,12 +2218,15 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         unsigned int err = 0;
         double span = B.dt, n0c = n0;
         if (ph.cosmo) cosmo_in<G, STRICT>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
+        const bool warm_cut = !STRICT && d2f(n0c) * d2f(span) <= RTD_TAB_NDMAX;
         if (ph.nsub > 0) {
             const double h = span / ph.nsub;
             for (int q = 0; q < ph.nsub; q++)
-                err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac);
+                err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
+                                                         warm_cut);
         } else {
-            err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac);
+            err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
+                                                     warm_cut);
         }
         if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
         if (!finite_bits(s.xHI) || !finite_bits(s.T)) err |= RTD_ERR_NONFINITE;

@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-256", action="store_true", help="skip the 256^3 workload's row")
     ap.add_argument("--config-table", action="store_true",
                     help="instead of the bench line: one JSON line per workload x form")
+    ap.add_argument("--only", choices=["reion256", "ensemble", "hll"], default=None,
+                    help="run that row alone and print it (profiling commands)")
     ap.add_argument("--tune", type=int, default=1,
                     help="rt_params.tune of the split form: 1 = time the transport's launch "
                          "shapes at create, 2 + k = shape k (profiling runs fix the shape)")
@@ -265,6 +267,8 @@ def time_device(w, precision, K, W, nsteps, ws, profile):
     mean_sub = float(np.sum(h[:, :, 4] * cells) / (nsteps * cells.sum()))
     nbytes = r.state_bytes
     launch = {"transport_tile": [st.tile_x, st.tile_y], "transport_grid": st.transport_grid,
+              "transport_zchunk": st.transport_zchunk, "transport_tma": bool(st.transport_tma),
+              "transport_lockstep": st.transport_lockstep,
               "chemistry_grid": st.chem_grid, "tuned": bool(r.p.tune)}
     r.close()
     return ms, kern, diag, nbytes, mean_sub, launch
@@ -456,7 +460,7 @@ def crta_run(K=3, nsteps=100):
             "all_cell_updates_per_s": (w.cells + nf) * nsteps * K / (ms * 1e-3)}
 
 
-def hll_run(K=3):
+def hll_run(K=3, nsteps=None):
     """The HLL flux (the less diffusive flux the paper plans) on the same
     128^3 workload, split form, 500 steps per run: whole-step throughput and
     the transport kernel's time and HBM rate (algorithmic 32 B per
@@ -464,23 +468,24 @@ def hll_run(K=3):
     import torch
     from paper_1508_07888_b300 import binding as B
     w = workload()
+    nsteps = nsteps or w.steps
     r = DeviceRun(w, B.RT_PREC_SPLIT, flux=1)
     r.reset()
-    r.run(w.steps)
+    r.run(nsteps)
     B.rt_set_profiling(r.solver.h, 1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(K):
         r.reset()
-        r.run(w.steps)
+        r.run(nsteps)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     st = B.rt_query(r.solver.h)
     r.close()
     t_ms = st.kernel_ms[0] / max(st.kernel_launches[0], 1)
-    return {"value": w.cells * w.steps * K / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms / K,
+    return {"value": w.cells * nsteps * K / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms / K,
             "transport_ms_per_launch": t_ms,
             "transport_gbs": 32.0 * w.ngroups * w.cells / (t_ms * 1e-3) / 1e9,
             "transport_traffic": profiled_traffic().get("transport_hll"),
@@ -701,6 +706,15 @@ def main():
     TUNE = args.tune
     if args.config_table:
         config_table()
+        return
+    if args.only:
+        import torch
+        from paper_1508_07888_b300 import binding as B
+        torch.cuda.set_device(0)
+        row = {"reion256": lambda: reion256_run(B, 1, K=args.steps, nsteps=args.rt_steps),
+               "ensemble": lambda: ensemble_run(B, 1, K=args.steps),
+               "hll": lambda: hll_run(K=args.steps, nsteps=args.rt_steps)}[args.only]()
+        print(json.dumps({"only": args.only, **row}), flush=True)
         return
     ws, rank, local = dist_setup(args)
     w = workload()

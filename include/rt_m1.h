@@ -114,8 +114,14 @@ typedef struct rt_params {
                                             for tile t (32x8, 16x16, 64x4) at b = 1..3 resident
                                             blocks per SM (capped by what fits), k = 9 + 2 t +
                                             (j - 1) for tile t at j = 1, 2 blocks per tile
-                                            column; k >= 15 is RT_ERR_ARG.  Ignored by the
-                                            FP64 forms */
+                                            column, k = 15 + 3 t + c for tile t at the most
+                                            resident blocks with the plane units in z-chunks
+                                            of 16, 32, 64 planes (c = 0, 1, 2), k = 24 + 2 t +
+                                            s for tile t in lockstep rows by per-thread copies
+                                            (s = 0) or TMA (s = 1), k = 30 + t for tile t with
+                                            TMA (GLF; TMA and lockstep rows fall back to the
+                                            default where they do not apply); k >= 33 is
+                                            RT_ERR_ARG.  Ignored by the FP64 forms */
     int    flux;                         /* rt_flux; rt_adjoint and rt_transport_static need GLF */
     double inflow[6];                    /* photons/cm^2/s entering through each RT_BC_INFLOW face */
     int    cosmo;                        /* 1: supercomoving units (Sec. 3).  U holds the comoving
@@ -156,6 +162,13 @@ typedef struct rt_stats {
     int     tile_x, tile_y;              /* transport tile (columns x rows per block) */
     int     transport_grid, chem_grid;   /* blocks of the persistent transport / chemistry grids */
     double  a;                           /* cosmo: current expansion factor (1 otherwise) */
+    int     transport_zchunk;            /* z-chunk length of the transport's work order
+                                            (0: whole tile columns) */
+    int     transport_tma;               /* 1: the SPLIT form's GLF transport loads its planes
+                                            by TMA (tensor maps of every box encoded);
+                                            0: per-thread copies */
+    int     transport_lockstep;          /* tile columns per row of the lockstep-rows work
+                                            order (0: off) */
 } rt_stats;
 
 typedef struct rt_handle rt_handle;

@@ -82,6 +82,9 @@ class rt_stats(C.Structure):
         ("tile_x", C.c_int), ("tile_y", C.c_int),
         ("transport_grid", C.c_int), ("chem_grid", C.c_int),
         ("a", C.c_double),
+        ("transport_zchunk", C.c_int),
+        ("transport_tma", C.c_int),
+        ("transport_lockstep", C.c_int),
     ]
 
 

@@ -36,30 +36,37 @@ static cudaError_t transport_generic(const Launch &L, int zc, const rtd::Phys &p
 }
 
 // the FP32 transport with a TX x TY tile: shared-memory attribute set once
-// per device, then the launch
-template <int TX, int TY>
+// per device, then the launch (TMA: the boxes' tensor maps are set)
+template <int TX, int TY, bool TMA>
 static cudaError_t pm_attr()
 {
     static int done_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (done_dev == dev) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport_pm<TX, TY>,
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport_pm<TX, TY, TMA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rtk::transport_pm_smem_bytes<TX, TY>());
+                                         (int)rtk::transport_pm_smem_bytes<TX, TY, TMA>());
     if (e == cudaSuccess) done_dev = dev;
     return e;
+}
+
+template <int TX, int TY, bool TMA>
+static cudaError_t transport_pm_t(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
+{
+    cudaError_t e = pm_attr<TX, TY, TMA>();
+    if (e != cudaSuccess) return e;
+    (void)zc;
+    rtk::k_transport_pm<TX, TY, TMA><<<L.grid, rtk::transport_pm_threads<TX, TY>(),
+                                       rtk::transport_pm_smem_bytes<TX, TY, TMA>(), L.stream>>>(
+        L.boxes, L.nboxes, L.nitems, L.lockstep, ph, ctl);
+    return cudaSuccess;
 }
 
 template <int TX, int TY>
 static cudaError_t transport_pm(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
-    cudaError_t e = pm_attr<TX, TY>();
-    if (e != cudaSuccess) return e;
-    rtk::k_transport_pm<TX, TY><<<L.grid, rtk::transport_pm_threads<TX, TY>(),
-                                  rtk::transport_pm_smem_bytes<TX, TY>(), L.stream>>>(
-        L.boxes, L.nboxes, L.nitems, zc, ph, ctl);
-    return cudaSuccess;
+    return L.tma ? transport_pm_t<TX, TY, true>(L, zc, ph, ctl) : transport_pm_t<TX, TY, false>(L, zc, ph, ctl);
 }
 
 template <int TX, int TY>
@@ -215,9 +222,10 @@ static int hll_occupancy()
 template <int TX, int TY>
 static int pm_occupancy()
 {
-    pm_attr<TX, TY>();
-    return occ((const void *)rtk::k_transport_pm<TX, TY>, rtk::transport_pm_threads<TX, TY>(),
-               rtk::transport_pm_smem_bytes<TX, TY>());
+    // the TMA form holds a little more shared memory; its residency bounds both
+    pm_attr<TX, TY, true>();
+    return occ((const void *)rtk::k_transport_pm<TX, TY, true>, rtk::transport_pm_threads<TX, TY>(),
+               rtk::transport_pm_smem_bytes<TX, TY, true>());
 }
 
 __global__ void k_fill_tune(float4 *U, int64_t n)

@@ -20,7 +20,16 @@ struct Launch {
     int grid;
     cudaStream_t stream;
     int variant = 0;                 // tile shape of the FP32 transport (kTileX/kTileY)
+    bool tma = false;                // FP32 GLF transport: every box has its tensor maps
+    int lockstep = 0;                // FP32 GLF transport: tile columns of the lockstep-rows
+                                     // order (every box has that many; grid a multiple), 0 = off
 };
+
+// the three TMA tensor maps of a box's FP32 radiation state U for tile shape
+// `variant` (the tile with its halo, a halo column, a halo row), written to
+// out (3 x 128 bytes, host memory); false when the map cannot be encoded
+// (the transport then copies per thread)
+bool transport_tensor_maps(const rtd::BoxDev &B, int ngroups, int variant, void *out);
 
 // tile shapes (columns x rows, one thread per column) of the FP32 transport
 // kernel; the FP64 kernels always use variant 0 (RTD_TX x RTD_TY)
@@ -40,14 +49,16 @@ cudaError_t chem_fine_fast(bool fp64, int G, const Launch &L, const rtd::FineDev
 cudaError_t chem_fine_strict(int G, const Launch &L, const rtd::FineDev *fines, const rtd::Phys &ph,
                              rtd::Ctl *ctl);
 
-// transport tiling of a box: x/y tiles and the number of plane units
-// (ngroups x tiles_x x tiles_y x nz) the transport kernel spreads over its grid
-inline void transport_layout(rtd::BoxDev &B, int ngroups, int variant = 0)
+// transport tiling of a box: x/y tiles, the z-chunk length of the unit order
+// (zlen <= 0 or >= nz: whole columns; only the FP32 kernels take chunks) and
+// the number of plane units (ngroups x tiles_x x tiles_y x nz) the transport
+// kernel spreads over its grid
+inline void transport_layout(rtd::BoxDev &B, int ngroups, int variant = 0, int zlen = 0)
 {
     const int tx = kTileX[variant], ty = kTileY[variant];
     B.tiles_x = (B.nx + tx - 1) / tx;
     B.tiles_y = (B.ny + ty - 1) / ty;
-    B.zchunks = 1;
+    B.zlen = zlen <= 0 || zlen >= B.nz ? B.nz : zlen;
     B.ntitems = (int64_t)ngroups * B.tiles_x * B.tiles_y * B.nz;
 }
 

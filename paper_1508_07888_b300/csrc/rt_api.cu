@@ -72,6 +72,10 @@ struct rt_handle {
     int zc = 32;
     int tgrid = 1, cgrid = 1;
     int tvariant = 0;                        // tile shape of the FP32 transport (rtl::kTileX/Y)
+    int tzlen = 0;                           // its z-chunk length (0: whole columns)
+    void *d_tmaps = nullptr;                 // FP32 GLF transport: 3 TMA tensor maps per box
+    bool tma = false;                        // every box has its maps (the TMA kernel runs)
+    int tlock = 0;                           // lockstep-rows order: tile columns per row (0: off)
     int nsm = 1, chem_occ = 1;               // SMs, resident chemistry blocks per SM
     std::vector<rtd::FineDev> fdev;          // CRTA fine level per box (host mirror)
     rtd::FineDev *d_fines = nullptr;
@@ -123,6 +127,7 @@ static void release(rt_handle *h)
     for (auto *p : h->d_src_cell) cudaFree(p);
     for (auto *p : h->d_src_S) cudaFree(p);
     cudaFree(h->d_boxes);
+    cudaFree(h->d_tmaps);
     cudaFree(h->d_partials);
     cudaFree(h->d_lanes);
     cudaFree(h->d_done);
@@ -210,22 +215,38 @@ extern "C" double rt_timestep(const rt_params *p, double dx)
 //   k = 9 + 2 t + (j - 1): tile t with j = 1, 2 blocks per tile column, so
 //     the runs of neighbouring columns start at the same planes and each
 //     reads its x/y halo while the neighbour's plane is still in L2.
+//   k = 24 + 2 t + s: tile t in lockstep rows (groups of as many blocks as a
+//     row has tiles, all of a group on the same planes of one row, so a
+//     tile's x-halo lines are read by its neighbour at the same time), by
+//     per-thread copies (s = 0) or TMA (s = 1); GLF only, and only when every
+//     box has the same number of tile columns (else the default order);
+//   k = 30 + t: tile t at the most resident blocks, planes loaded by TMA;
+//   k = 15 + 3 t + c: tile t at the most resident blocks, the plane units in
+//     z-chunks of 16, 32 or 64 planes (c = 0, 1, 2): a block's consecutive
+//     runs are neighbouring tiles over the same planes, so a run's x-halo
+//     lines were read as interior by the run before, still in L2 (whole
+//     columns are far apart in time on large boxes and their halos come
+//     from DRAM again).
 // tune = 1 times every candidate on the handle's boxes (on a synthetic
 // realizable state in scratch, so the caller's state is not touched) and
 // keeps the fastest; the choice is cached per device, flux, group count and
 // box set for later handles.  tune = 2 + k selects candidate k without timing.
 struct TuneChoice {
     int variant, grid;
+    int zlen;                 // z-chunk length of the unit order (0: whole columns)
+    int lockx;                // lockstep rows: tile columns per row (0: off)
+    bool tma;                 // GLF planes loaded by TMA
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune_cache;
-constexpr int kTuneCandidates = 5 * rtl::kTileVariants;
+constexpr int kTuneCandidates = 11 * rtl::kTileVariants;
+constexpr int kTuneChunk[3] = {16, 32, 64};
 
-static void apply_layout(rt_handle *h, std::vector<rtd::BoxDev> &bd, int variant)
+static void apply_layout(rt_handle *h, std::vector<rtd::BoxDev> &bd, int variant, int zlen = 0)
 {
     int64_t titem = 0;
     for (auto &D : bd) {
-        rtl::transport_layout(D, h->p.ngroups, variant);
+        rtl::transport_layout(D, h->p.ngroups, variant, zlen);
         D.titem0 = titem;
         titem += D.ntitems;
     }
@@ -240,7 +261,11 @@ static int tgrid_of(int64_t ntitems, int blocks_per_sm, int nsm)
 static TuneChoice tune_candidate(rt_handle *h, int k, int nsm)
 {
     constexpr int V = rtl::kTileVariants;
-    const int v = k < 3 * V ? k / 3 : (k - 3 * V) / 2;
+    const int v = k < 3 * V ? k / 3
+                : k < 5 * V ? (k - 3 * V) / 2
+                : k < 8 * V ? (k - 5 * V) / 3
+                : k < 10 * V ? (k - 8 * V) / 2
+                : k - 10 * V;
     const int occ = rtl::transport_occupancy(false, false, v, h->p.flux);
     std::vector<rtd::BoxDev> bd = h->bdev;
     apply_layout(h, bd, v);
@@ -249,10 +274,51 @@ static TuneChoice tune_candidate(rt_handle *h, int k, int nsm)
         nt += D.ntitems;
         ncol += D.ntitems / D.nz;
     }
-    if (k < 3 * V) return {v, tgrid_of(nt, std::min(k % 3 + 1, occ), nsm)};
+    const bool glf = h->p.flux == RT_FLUX_GLF;
+    if (k < 3 * V) return {v, tgrid_of(nt, std::min(k % 3 + 1, occ), nsm), 0, 0, false};
+    if (k >= 10 * V) return {v, tgrid_of(nt, occ, nsm), 0, 0, glf};
+    if (k >= 8 * V) {
+        const int tx = bd[0].tiles_x;
+        bool same = glf;
+        for (const auto &D : bd) same = same && D.tiles_x == tx;
+        const int m = (occ * nsm) / tx;
+        if (!same || m < 1) return {v, tgrid_of(nt, occ, nsm), 0, 0, false};
+        return {v, m * tx, 0, tx, glf && (k - 8 * V) % 2 == 1};
+    }
+    if (k >= 5 * V) return {v, tgrid_of(nt, occ, nsm), kTuneChunk[(k - 5 * V) % 3], 0, false};
     const int64_t j = (k - 3 * V) % 2 + 1;
     const int64_t g = std::min<int64_t>(j * ncol, (int64_t)occ * nsm);
-    return {v, (int)std::max<int64_t>(1, std::min<int64_t>(g, (nt + 3) / 4))};
+    return {v, (int)std::max<int64_t>(1, std::min<int64_t>(g, (nt + 3) / 4)), 0, 0, false};
+}
+
+// TMA tensor maps of descriptors bd (tile shape `variant`) written to the
+// device buffer dmaps (3 x 128 bytes per box); true when every box has them
+static bool build_tmaps(rt_handle *h, std::vector<rtd::BoxDev> &bd, int variant, void *dmaps)
+{
+    for (auto &D : bd) D.tmap = nullptr;
+    if (h->fp64 || h->p.flux != RT_FLUX_GLF || !dmaps) return false;
+    struct alignas(64) Maps { unsigned char b[384]; };                // a box's three maps
+    std::vector<Maps> buf(bd.size());
+    for (size_t b = 0; b < bd.size(); b++)
+        if (!rtl::transport_tensor_maps(bd[b], h->p.ngroups, variant, buf[b].b)) return false;
+    if (cudaMemcpy(dmaps, buf.data(), buf.size() * sizeof(Maps), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    for (size_t b = 0; b < bd.size(); b++) bd[b].tmap = static_cast<char *>(dmaps) + 384 * b;
+    return true;
+}
+
+// the handle's maps for its current layout when `want` (allocated once per
+// handle); without them the transport copies per thread
+static int setup_tma(rt_handle *h, bool want)
+{
+    h->tma = false;
+    for (auto &D : h->bdev) D.tmap = nullptr;
+    if (!want || h->fp64 || h->p.flux != RT_FLUX_GLF) return RT_OK;
+    if (!h->d_tmaps) CU(h, cudaMalloc(&h->d_tmaps, (size_t)384 * h->nboxes));
+    h->tma = build_tmaps(h, h->bdev, h->tvariant, h->d_tmaps);
+    return RT_OK;
 }
 
 static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
@@ -261,13 +327,15 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
     for (int k = 0; k < kTuneCandidates; k++) {
         const TuneChoice c = tune_candidate(h, k, nsm);
         bool dup = false;
-        for (const auto &o : cand) dup |= o.variant == c.variant && o.grid == c.grid;
+        for (const auto &o : cand)
+            dup |= o.variant == c.variant && o.grid == c.grid && o.zlen == c.zlen && o.lockx == c.lockx &&
+                   o.tma == c.tma;
         if (!dup) cand.push_back(c);
     }
     std::string key = std::to_string(dev) + "/" + std::to_string(h->p.flux) + "/" + std::to_string(h->p.ngroups);
     for (const auto &D : h->bdev)
         key += "/" + std::to_string(D.nx) + "x" + std::to_string(D.ny) + "x" + std::to_string(D.nz);
-    TuneChoice best{0, 1};
+    TuneChoice best{0, 1, 0, 0, false};
     bool have = false;
     if (tune >= 2) {
         if (tune - 2 >= kTuneCandidates)
@@ -283,11 +351,12 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
         // scratch copy of the descriptors whose U is a synthetic state
         int64_t nU = 0;
         for (const auto &D : h->bdev) nU += (int64_t)h->p.ngroups * D.ncell;
-        void *tU = nullptr;
+        void *tU = nullptr, *tmaps = nullptr;
         rtd::BoxDev *tbox = nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         auto cleanup = [&]() {
             cudaFree(tU);
+            cudaFree(tmaps);
             cudaFree(tbox);
             if (e0) cudaEventDestroy(e0);
             if (e1) cudaEventDestroy(e1);
@@ -295,6 +364,7 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
         int rc = [&]() -> int {
             CU(h, cudaMalloc(&tU, (size_t)nU * 16));
             CU(h, cudaMalloc(&tbox, sizeof(rtd::BoxDev) * h->nboxes));
+            if (h->p.flux == RT_FLUX_GLF) CU(h, cudaMalloc(&tmaps, (size_t)384 * h->nboxes));
             CU(h, cudaEventCreate(&e0));
             CU(h, cudaEventCreate(&e1));
             CU(h, rtl::fill_tune_state(tU, nU, h->s));
@@ -306,12 +376,18 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
             }
             float best_ms = 0.f;
             for (const auto &c : cand) {
-                apply_layout(h, bd, c.variant);
+                apply_layout(h, bd, c.variant, c.zlen);
                 int64_t nt = 0;
                 for (const auto &D : bd) nt += D.ntitems;
+                CU(h, cudaStreamSynchronize(h->s));               // the maps' buffer is rewritten
+                const bool tma = c.tma && build_tmaps(h, bd, c.variant, tmaps);
+                if (!tma)
+                    for (auto &D : bd) D.tmap = nullptr;
                 CU(h, cudaMemcpyAsync(tbox, bd.data(), sizeof(rtd::BoxDev) * h->nboxes,
                                       cudaMemcpyHostToDevice, h->s));
                 rtl::Launch L{tbox, h->nboxes, nt, c.grid, h->s, c.variant};
+                L.tma = tma;
+                L.lockstep = c.lockx;
                 CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));      // warm-up
                 CU(h, cudaEventRecord(e0, h->s));
                 for (int r = 0; r < 5; r++) CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));
@@ -328,11 +404,14 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    apply_layout(h, h->bdev, best.variant);
+    apply_layout(h, h->bdev, best.variant, best.zlen);
     h->ntitems = 0;
     for (const auto &D : h->bdev) h->ntitems += D.ntitems;
     h->tvariant = best.variant;
     h->tgrid = best.grid;
+    h->tzlen = best.zlen;
+    h->tlock = best.lockx;
+    if (int rc2 = setup_tma(h, best.tma)) return rc2;
     CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * h->nboxes, cudaMemcpyHostToDevice));
     return RT_OK;
 }
@@ -452,6 +531,7 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 }
                 h->ntitems = titem;
                 h->ncitems = citem;
+                if (int rc2 = setup_tma(h, false)) return rc2;
                 CU(h, cudaMalloc(&h->d_boxes, sizeof(rtd::BoxDev) * nboxes));
                 CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * nboxes,
                                  cudaMemcpyHostToDevice));
@@ -612,6 +692,8 @@ static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = 
                                 bool fine = true)
 {
     rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s, h->tvariant};
+    Lt.tma = h->tma;
+    Lt.lockstep = h->tlock;
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
     const rtd::DiagBuf db{h->d_partials, h->d_lanes, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
     cudaError_t e;
@@ -1041,6 +1123,9 @@ extern "C" int rt_query(rt_handle *h, rt_stats *st)
     st->tile_x = rtl::kTileX[v];
     st->tile_y = rtl::kTileY[v];
     st->transport_grid = h->tgrid;
+    st->transport_zchunk = h->fp64 ? 0 : h->tzlen;
+    st->transport_tma = h->tma ? 1 : 0;
+    st->transport_lockstep = h->fp64 ? 0 : h->tlock;
     st->chem_grid = h->cgrid;
     st->a = h->p.cosmo ? h->a_now : 1.0;
     return RT_OK;

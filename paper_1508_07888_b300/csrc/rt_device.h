@@ -24,6 +24,7 @@
 #define RTD_ERR_NONFINITE 1u
 #define RTD_ERR_REALIZ 2u
 #define RTD_ERR_SUBCYCLE 4u
+#define RTD_ERR_TIMEOUT 8u      // a bounded device wait (TMA arrival) gave up
 
 #define RTD_MAXCYC 1000000   // sub-cycles per cell and step before giving up
 
@@ -96,7 +97,9 @@ struct Phys {
 // One box (array in device memory, indexed by work items).
 struct BoxDev {
     int nx, ny, nz;
-    int tiles_x, tiles_y, zchunks;   // transport tiling (zchunks unused: runs are balanced)
+    int tiles_x, tiles_y;             // transport tiling
+    int zlen;                         // plane units ordered (group, y-tile, z-chunk of zlen
+                                      // planes, x-tile, z); zlen = nz: whole columns
     int64_t ncell;
     double dx, nunit, dt, lam;        // lam = c dt / dx (Courant number)
     double inv_nunit;                 // 1 / nunit
@@ -104,6 +107,9 @@ struct BoxDev {
     double hN[RTD_MAXG];              // c nunit Sigma_E,i
     void *U;                          // caller's state, [G][nz][ny][nx][4]
     void *Us;                         // post-transport state (library scratch)
+    const void *tmap;                 // FP32 transport: three TMA tensor maps of U (the tile
+                                      // with halo, a halo column, a halo row), 64-byte aligned
+                                      // in device memory; null: per-thread copies
     double *xHI, *T;
     const void *n0;
     const int64_t *src_cell;          // sorted unique source cells (nsrc)

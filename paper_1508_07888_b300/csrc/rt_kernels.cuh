@@ -418,6 +418,58 @@ __device__ __forceinline__ void cp_cell(V4<R> *dst, const V4<R> *src)
     }
 }
 
+// TMA and mbarrier (FP32 GLF transport).  A tiled 4-D bulk copy of a box of
+// the tensor map tm (dims: 4 components, x, y, z + nz g) into shared memory,
+// completing on mbarrier bar with its byte count; waits poll the barrier's
+// phase a bounded number of times.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// true once phase `parity` of bar has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned limit)
+{
+    const unsigned a = smem_u32(bar);
+    for (unsigned i = 0; i < limit; i++) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// orders this thread's earlier shared-memory accesses (after a barrier: the
+// block's) before later async-proxy (TMA) writes to the same memory
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tm, int c0, int c1, int c2, int c3,
+                                            unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+                 ::"r"(smem_u32(dst)), "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+                 : "memory");
+}
+// polls of an mbarrier before a wait gives up (each poll waits up to the
+// hardware's own time slice; far above any copy's latency)
+constexpr unsigned RTK_TMA_POLLS = 1u << 22;
+
 // Shared-memory layout of the transport pipeline: a ring of TP_STAGES planes
 // of U over the (TY+2) x (TX+2) tile-with-halo, and two planes of the closure
 // P (the plane being updated and the next one).
@@ -798,6 +850,35 @@ __device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
+// The run of plane units of box B that starts at unit loc (relative to the
+// box) and takes at most `left` units: group g, tile (ix, iy), planes
+// z0 .. z1-1.  Units are ordered (group, y-tile, z-chunk, x-tile, z) with
+// z-chunks of B.zlen planes (the last one shorter), so with chunks shorter
+// than the box a block's consecutive runs are neighbouring tiles over the
+// same planes and the x-halo lines of one run were read as interior by the
+// run before, still in L2.  B.zlen = nz is the column order.
+__device__ __forceinline__ void transport_run(const BoxDev &B, int64_t loc, int64_t left, int &g,
+                                              int &iy, int &ix, int &z0, int &z1)
+{
+    const int nz = B.nz, Lz = B.zlen;
+    const int64_t per_row = (int64_t)nz * B.tiles_x;        // units of one row of tiles
+    const int64_t row = loc / per_row;
+    int64_t r = loc - row * per_row;
+    iy = (int)(row % B.tiles_y);
+    g = (int)(row / B.tiles_y);
+    const int nfull = nz / Lz;                                // full chunks
+    const int64_t full = (int64_t)B.tiles_x * Lz;             // units of a full chunk
+    int zc = (int)(r / full), Lc = Lz;
+    if (zc >= nfull) { zc = nfull; Lc = nz - nfull * Lz; }
+    r -= (int64_t)zc * full;
+    ix = (int)(r / Lc);
+    const int zz = (int)(r - (int64_t)ix * Lc);
+    z0 = zc * Lz + zz;
+    const int zend = zc * Lz + Lc;
+    const int64_t lim = (int64_t)z0 + left;
+    z1 = lim < (int64_t)zend ? (int)lim : zend;
+}
+
 // the FP32 GLF kernel streams one plane deeper than the others (4 planes
 // ahead): it is the one bound by DRAM latency
 constexpr int TP_STAGES_PM = 6;
@@ -810,8 +891,31 @@ struct TransportSmemPM {
     float4 H[2][4][TY + 2][TX + 3];    // per cell: Rx, Lx, Ry, Ly of two planes
 };
 
+// The TMA ring: each plane's tile with its halo as the dense box the copy
+// writes (128-byte aligned slots), the wrapped halo columns and rows of
+// periodic faces (their own small boxes), one mbarrier per slot.
 template <int TX, int TY>
-constexpr size_t transport_pm_smem_bytes() { return sizeof(TransportSmemPM<TX, TY>); }
+struct alignas(128) PMSlot {
+    V4<float> c[TY + 2][TX + 2];
+};
+template <int N>
+struct alignas(128) PMLine {
+    V4<float> c[N];
+};
+template <int TX, int TY>
+struct TransportSmemPMT {
+    PMSlot<TX, TY> U[TP_STAGES_PM];
+    PMLine<TY> Wx[TP_STAGES_PM][2];    // x = nx - 1 (left halo), x = 0 (right halo)
+    PMLine<TX> Wy[TP_STAGES_PM][2];    // y = ny - 1 (bottom halo), y = 0 (top halo)
+    float4 H[2][4][TY + 2][TX + 3];
+    unsigned long long bar[TP_STAGES_PM];
+};
+
+template <int TX, int TY, bool TMA = false>
+constexpr size_t transport_pm_smem_bytes()
+{
+    return TMA ? sizeof(TransportSmemPMT<TX, TY>) : sizeof(TransportSmemPM<TX, TY>);
+}
 
 // threads of the FP32 GLF kernel's block: TX x TY interior cells and the
 // 2 (TX + TY) halo cells of the tile, one cell each, rounded up to warps
@@ -830,34 +934,92 @@ constexpr int transport_pm_threads() { return (TX * TY + 2 * (TX + TY) + 31) / 3
 // right, y: bottom and top), so every thread evaluates exactly one closure
 // per plane and no warp waits at the plane's barrier for another's second
 // closure; the halo threads take no part in the update.
-template <int TX, int TY>
+// TMA: one thread issues each plane as a TMA copy of the tile with its halo
+// (rows of TX + 2 cells), completing on the slot's mbarrier; tiles on a
+// periodic face add the wrapped column or row as a small box of its own.
+// Otherwise every thread copies its own cell by cp.async.
+// lockx > 0 (every box has lockx tile columns): lockstep rows.  The grid is
+// groups of lockx blocks; block (k, ix) of group k takes tile column ix of
+// the k-th equal share of the row-planes (box, group, y-tile, z), so the
+// blocks of a group work on the tiles of one row at the same planes at the
+// same time, and the lines a tile reads for its x-halo are its neighbours'
+// interior lines, read at once from L2 instead of again from DRAM.
+template <int TX, int TY, bool TMA>
 __global__ void __launch_bounds__(transport_pm_threads<TX, TY>(), 2)
-k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int, Phys ph, Ctl *ctl)
+k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int lockx, Phys ph,
+               Ctl *ctl)
 {
     constexpr int S = TP_STAGES_PM;
-    extern __shared__ __align__(16) unsigned char tp_smem_raw[];
-    TransportSmemPM<TX, TY> &sm = *reinterpret_cast<TransportSmemPM<TX, TY> *>(tp_smem_raw);
+    extern __shared__ __align__(128) unsigned char tp_smem_pm[];
+    TransportSmemPM<TX, TY> &sm = *reinterpret_cast<TransportSmemPM<TX, TY> *>(tp_smem_pm);
+    TransportSmemPMT<TX, TY> &st = *reinterpret_cast<TransportSmemPMT<TX, TY> *>(tp_smem_pm);
+    auto ring = [&](int slot, int yy, int xx) -> V4<float> & {
+        if constexpr (TMA) return st.U[slot].c[yy][xx];
+        else return sm.U[slot][yy][xx];
+    };
+    auto Hs = [&](int hs, int k, int yy, int xx) -> float4 & {
+        if constexpr (TMA) return st.H[hs][k][yy][xx];
+        else return sm.H[hs][k][yy][xx];
+    };
 
     const int tid = threadIdx.x;
     const bool interior = tid < TX * TY;
     const int tx = interior ? tid % TX : 0, ty = interior ? tid / TX : 0;
     if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
+    if constexpr (TMA) {
+        // the copies write 128-byte aligned slots: a misplaced window is
+        // reported, not copied into (the same test in every thread)
+        if (smem_u32(tp_smem_pm) & 127u) {
+            if (tid == 0) atomicOr(&ctl->err, RTD_ERR_TIMEOUT);
+            return;
+        }
+        if (tid == 0) {
+            for (int k = 0; k < S; k++) mbar_init(&st.bar[k], 1u);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
+    unsigned pl_issued = 0, pl_done = 0;      // planes issued / consumed by the block
 
-    const int64_t ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
-    const int64_t uend = nunits * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    int64_t ubeg, uend;
+    int lix = 0;                              // lockstep: this block's tile column
+    if (lockx > 0) {
+        const int64_t m = gridDim.x / lockx, k = blockIdx.x / lockx;
+        lix = (int)(blockIdx.x - k * lockx);
+        const int64_t nrp = nunits / lockx;   // row-planes of all boxes
+        ubeg = nrp * k / m;
+        uend = nrp * (k + 1) / m;
+    } else {
+        ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
+        uend = nunits * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    }
     for (int64_t u = ubeg; u < uend;) {
-        const int b = find_box_unit(boxes, nboxes, u);
+        int b, g, iy, ix, z0, z1;
+        if (lockx > 0) {
+            // box of row-plane u: the last with titem0 / lockx <= u
+            int lo = 0, hi = nboxes - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (boxes[mid].titem0 / lockx <= u) lo = mid; else hi = mid - 1;
+            }
+            b = lo;
+            const BoxDev &Bb = boxes[b];
+            const int64_t loc = u - Bb.titem0 / lockx;
+            const int64_t row = loc / Bb.nz;
+            z0 = (int)(loc - row * Bb.nz);
+            const int64_t lim = (int64_t)z0 + (uend - u);
+            z1 = lim < (int64_t)Bb.nz ? (int)lim : Bb.nz;
+            iy = (int)(row % Bb.tiles_y);
+            g = (int)(row / Bb.tiles_y);
+            ix = lix;
+        } else {
+            b = find_box_unit(boxes, nboxes, u);
+            transport_run(boxes[b], u - boxes[b].titem0, uend - u, g, iy, ix, z0, z1);
+        }
         const BoxDev &B = boxes[b];
         const int nx = B.nx, ny = B.ny, nz = B.nz;
-        const int64_t loc = u - B.titem0;
-        int64_t colid = loc / nz;
-        const int z0 = (int)(loc - colid * nz);
-        const int64_t zlim = (int64_t)z0 + (uend - u);
-        const int z1 = zlim < (int64_t)nz ? (int)zlim : nz;
         u += z1 - z0;
-        const int ix = (int)(colid % B.tiles_x); colid /= B.tiles_x;
-        const int iy = (int)(colid % B.tiles_y);
-        const int g = (int)(colid / B.tiles_y);
+        if (ix >= B.tiles_x) continue;        // (lockstep on a box of other width: not set up)
         const int x0 = ix * TX, y0 = iy * TY;
         const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
         const int x = x0 + tx, y = y0 + ty;
@@ -868,34 +1030,51 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         const float lam = (float)B.lam;
         const float c0 = 1.0f - 3.0f * lam, c1 = 0.5f * lam;
         const int64_t sxy = (int64_t)nx * ny;
+        // periodic faces of this tile (TMA: their wrapped halo lines come as
+        // boxes of their own)
+        const bool wl = x0 == 0 && ph.bc[0] == 0, wr = x0 + ntx == nx && ph.bc[1] == 0;
+        const bool wb = y0 == 0 && ph.bc[2] == 0, wt = y0 + nty == ny && ph.bc[3] == 0;
 
         // halo cell of a halo thread and which half of it the tile needs:
         // 0 = Rx (left column), 1 = Lx (right), 2 = Ry (bottom), 3 = Ly (top)
         int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0, hk = 0;
         float hin = 0.0f;                 // inflow ghost: beam density, sign = direction
         bool hif = false;                 // the halo cell is an inflow ghost
+        // TMA: where the halo cell is read: the box at (hry, hrx), or (hw >= 0)
+        // wrapped line hw (0 Wx left, 1 Wx right, 2 Wy bottom, 3 Wy top) at hwi
+        int hry = 0, hrx = 0, hw = -1, hwi = 0;
         if (!interior) {
             int t = tid - TX * TY;
             if (t < nty) {
                 hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1; hk = 0;
+                hry = hy; hrx = 0;
                 if (sx < 0) {
-                    if (ph.bc[0] == 0) sx = nx - 1;
-                    else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; }
+                    if (ph.bc[0] == 0) { sx = nx - 1; hw = 0; hwi = t; }
+                    else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; hrx = 1; }
                     if (ph.bc[0] == 3) { hif = true; hin = (float)(ph.inflow_c[0][g] * B.inv_nunit); }
                 }
             } else if ((t -= nty) < nty) {
                 hx = ntx + 1; hy = t + 1; sy = y0 + t; sx = x0 + ntx; hk = 1;
+                hry = hy; hrx = ntx + 1;
                 if (sx >= nx) {
-                    if (ph.bc[1] == 0) sx = 0;
-                    else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; }
+                    if (ph.bc[1] == 0) { sx = 0; hw = 1; hwi = t; }
+                    else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; hrx = ntx; }
                     if (ph.bc[1] == 3) { hif = true; hin = -(float)(ph.inflow_c[1][g] * B.inv_nunit); }
                 }
             } else if ((t -= nty) < ntx) {
                 hx = t + 1; hy = 0; sx = x0 + t; sy = y0 - 1; hk = 2;
-                if (sy < 0) { if (ph.bc[2] == 0) sy = ny - 1; else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; } }
+                hry = 0; hrx = hx;
+                if (sy < 0) {
+                    if (ph.bc[2] == 0) { sy = ny - 1; hw = 2; hwi = t; }
+                    else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; hry = 1; }
+                }
             } else if ((t -= ntx) < ntx) {
                 hx = t + 1; hy = nty + 1; sx = x0 + t; sy = y0 + nty; hk = 3;
-                if (sy >= ny) { if (ph.bc[3] == 0) sy = 0; else { sy = ny - 1; hneg = ph.bc[3] == 2 ? 2 : 0; } }
+                hry = nty + 1; hrx = hx;
+                if (sy >= ny) {
+                    if (ph.bc[3] == 0) { sy = 0; hw = 3; hwi = t; }
+                    else { sy = ny - 1; hneg = ph.bc[3] == 2 ? 2 : 0; hry = nty; }
+                }
             }
         }
         // source pointers of this thread's own and halo cells, advanced one
@@ -905,22 +1084,48 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         const V4<float> *ghalo = Ug + (int64_t)sy * nx + sx;
         const bool zneg_first = z0 == 0 && ph.bc[4] == 2, zneg_last = z1 == nz && ph.bc[5] == 2;
         int zi = z0 - 1;                          // plane of the next issue
-        int slot_i = 0;                           // its ring slot
+        int slot_i = (int)(pl_issued % S);        // its ring slot
         // offset of plane zi inside the box (advanced by one plane per
         // issue) and of the two ghost planes
         int64_t pl_in = (int64_t)zi * sxy;
         const int64_t pl_lo = ph.bc[4] == 0 ? (int64_t)(nz - 1) * sxy : 0;
         const int64_t pl_hi = ph.bc[5] == 0 ? 0 : (int64_t)(nz - 1) * sxy;
+        const int zlo = ph.bc[4] == 0 ? nz - 1 : 0, zhi = ph.bc[5] == 0 ? 0 : nz - 1;
+        const void *tm = B.tmap;
         auto issue = [&]() {
             if (zi < z1 + 1) {
-                const int64_t pl = zi < 0 ? pl_lo : (zi >= nz ? pl_hi : pl_in);
-                if (act) cp_async16(&sm.U[slot_i][ty + 1][tx + 1], gown + pl);
-                if (hx >= 0) {
-                    if (hif) sm.U[slot_i][hy][hx] = V4<float>{fabsf(hin), hin, 0.0f, 0.0f};
-                    else cp_async16(&sm.U[slot_i][hy][hx], ghalo + pl);
+                if constexpr (TMA) {
+                    if (tid == 0) {
+                        // the ring slot was read in an earlier plane (the
+                        // barrier before the issue ordered those reads)
+                        fence_proxy_async_smem();
+                        const int zz = zi < 0 ? zlo : (zi >= nz ? zhi : zi);
+                        const int c3 = g * nz + zz;
+                        unsigned bytes = (unsigned)sizeof(PMSlot<TX, TY>::c);
+                        if (wl) bytes += (unsigned)sizeof(PMLine<TY>::c);
+                        if (wr) bytes += (unsigned)sizeof(PMLine<TY>::c);
+                        if (wb) bytes += (unsigned)sizeof(PMLine<TX>::c);
+                        if (wt) bytes += (unsigned)sizeof(PMLine<TX>::c);
+                        unsigned long long *bar = &st.bar[slot_i];
+                        mbar_expect_tx(bar, bytes);
+                        const char *tmc = static_cast<const char *>(tm);
+                        tma_load_4d(&st.U[slot_i].c[0][0], tmc, 0, x0 - 1, y0 - 1, c3, bar);
+                        if (wl) tma_load_4d(&st.Wx[slot_i][0].c[0], tmc + 128, 0, nx - 1, y0, c3, bar);
+                        if (wr) tma_load_4d(&st.Wx[slot_i][1].c[0], tmc + 128, 0, 0, y0, c3, bar);
+                        if (wb) tma_load_4d(&st.Wy[slot_i][0].c[0], tmc + 256, 0, x0, ny - 1, c3, bar);
+                        if (wt) tma_load_4d(&st.Wy[slot_i][1].c[0], tmc + 256, 0, x0, 0, c3, bar);
+                    }
+                } else {
+                    const int64_t pl = zi < 0 ? pl_lo : (zi >= nz ? pl_hi : pl_in);
+                    if (act) cp_async16(&sm.U[slot_i][ty + 1][tx + 1], gown + pl);
+                    if (hx >= 0) {
+                        if (hif) sm.U[slot_i][hy][hx] = V4<float>{fabsf(hin), hin, 0.0f, 0.0f};
+                        else cp_async16(&sm.U[slot_i][hy][hx], ghalo + pl);
+                    }
                 }
+                pl_issued++;
             }
-            cp_async_commit();
+            if constexpr (!TMA) cp_async_commit();
             zi++;
             pl_in += sxy;
             slot_i = slot_i + 1 == S ? 0 : slot_i + 1;
@@ -931,44 +1136,62 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
         V4<float> uc = {};                  // own cell of plane q-1
         float4 Rz_prev = {}, Rz_c = {};     // right-going z halves of planes q-2 and q-1
         V4<float> *out = Og + (int64_t)z0 * sxy + (int64_t)y * nx + x;
-        int slot = 0;                       // ring slot of plane q
+        int slot = (int)(pl_done % S);      // ring slot of plane q
 #pragma unroll 3
         for (int q = 0; q < L; q++) {
-            cp_async_wait<S - 3>();
-            __syncthreads();
+            if constexpr (TMA) {
+                // plane q landed (every thread observes its slot's phase);
+                // a wait that gives up stops the whole block at the barrier
+                const bool ok = mbar_wait(&st.bar[slot], (pl_done / S) & 1u, RTK_TMA_POLLS);
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) atomicOr(&ctl->err, RTD_ERR_TIMEOUT);
+                    return;
+                }
+            } else {
+                cp_async_wait<S - 3>();
+                __syncthreads();
+            }
+            pl_done++;
             issue();
             const int hs = q & 1;
             const bool zneg = (q == 0 && zneg_first) || (q == L - 1 && zneg_last);
             V4<float> un = {};
             float4 Rz_n = {}, Lz_n = {};
             if (act) {
-                un = sm.U[slot][ty + 1][tx + 1];
+                un = ring(slot, ty + 1, tx + 1);
                 if (zneg) un.w = -un.w;
                 Halves hv;
                 cell_halves(un, hv);
                 Rz_n = hv.R[2];
                 Lz_n = hv.L[2];
-                sm.H[hs][0][ty + 1][tx + 1] = hv.R[0];
-                sm.H[hs][1][ty + 1][tx + 1] = hv.L[0];
-                sm.H[hs][2][ty + 1][tx + 1] = hv.R[1];
-                sm.H[hs][3][ty + 1][tx + 1] = hv.L[1];
+                Hs(hs, 0, ty + 1, tx + 1) = hv.R[0];
+                Hs(hs, 1, ty + 1, tx + 1) = hv.L[0];
+                Hs(hs, 2, ty + 1, tx + 1) = hv.R[1];
+                Hs(hs, 3, ty + 1, tx + 1) = hv.L[1];
             }
             if (hx >= 0) {
-                V4<float> h = sm.U[slot][hy][hx];
+                V4<float> h;
+                if constexpr (TMA) {
+                    if (hif) h = V4<float>{fabsf(hin), hin, 0.0f, 0.0f};
+                    else if (hw >= 0) h = hw < 2 ? st.Wx[slot][hw].c[hwi] : st.Wy[slot][hw - 2].c[hwi];
+                    else h = st.U[slot].c[hry][hrx];
+                } else {
+                    h = sm.U[slot][hy][hx];
+                }
                 if (zneg) h.w = -h.w;
                 if (hneg == 1) h.y = -h.y;
                 else if (hneg == 2) h.z = -h.z;
                 Halves hv;
                 cell_halves(h, hv);
-                sm.H[hs][hk][hy][hx] = hk == 0 ? hv.R[0] : hk == 1 ? hv.L[0] : hk == 2 ? hv.R[1] : hv.L[1];
+                Hs(hs, hk, hy, hx) = hk == 0 ? hv.R[0] : hk == 1 ? hv.L[0] : hk == 2 ? hv.R[1] : hv.L[1];
             }
             if (act && q >= 2) {
                 // update plane c = q - 1 (z = z0 + q - 2)
                 const int cs = hs ^ 1;
-                const float4 l = sm.H[cs][0][ty + 1][tx];        // Rx of the left cell
-                const float4 r = sm.H[cs][1][ty + 1][tx + 2];    // Lx of the right cell
-                const float4 d = sm.H[cs][2][ty][tx + 1];        // Ry of the cell below
-                const float4 p = sm.H[cs][3][ty + 2][tx + 1];    // Ly of the cell above
+                const float4 l = Hs(cs, 0, ty + 1, tx);        // Rx of the left cell
+                const float4 r = Hs(cs, 1, ty + 1, tx + 2);    // Lx of the right cell
+                const float4 d = Hs(cs, 2, ty, tx + 1);        // Ry of the cell below
+                const float4 p = Hs(cs, 3, ty + 2, tx + 1);    // Ly of the cell above
                 const float2 slo = __fadd2_rn(__fadd2_rn(__fadd2_rn(lo2(l), lo2(r)), __fadd2_rn(lo2(d), lo2(p))),
                                               __fadd2_rn(lo2(Rz_prev), lo2(Lz_n)));
                 const float2 shi = __fadd2_rn(__fadd2_rn(__fadd2_rn(hi2(l), hi2(r)), __fadd2_rn(hi2(d), hi2(p))),
@@ -984,7 +1207,7 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
             uc = un;
             slot = slot + 1 == S ? 0 : slot + 1;
         }
-        cp_async_wait<0>();
+        if constexpr (!TMA) cp_async_wait<0>();
         __syncthreads();
     }
 }
@@ -1114,15 +1337,9 @@ k_transport_hll(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, in
         const int b = find_box_unit(boxes, nboxes, u);
         const BoxDev &B = boxes[b];
         const int nx = B.nx, ny = B.ny, nz = B.nz;
-        const int64_t loc = u - B.titem0;
-        int64_t colid = loc / nz;
-        const int z0 = (int)(loc - colid * nz);
-        const int64_t zlim = (int64_t)z0 + (uend - u);
-        const int z1 = zlim < (int64_t)nz ? (int)zlim : nz;
+        int g, iy, ix, z0, z1;
+        transport_run(B, u - B.titem0, uend - u, g, iy, ix, z0, z1);
         u += z1 - z0;
-        const int ix = (int)(colid % B.tiles_x); colid /= B.tiles_x;
-        const int iy = (int)(colid % B.tiles_y);
-        const int g = (int)(colid / B.tiles_y);
         const int x0 = ix * TX, y0 = iy * TY;
         const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
         const int x = x0 + tx, y = y0 + ty;

@@ -2,6 +2,7 @@
 oracle and through the C-ABI library on the same seeded inputs."""
 from __future__ import annotations
 
+import json
 import os
 
 import numpy as np
@@ -147,3 +148,13 @@ def field_errors(gpu_box, ora_box, G):
     err["xHI"] = linf_rel(xg, xo)
     err["T"] = linf_rel(Tg, To)
     return err
+
+
+def report(name: str, form: str, steps: int, errs: dict) -> None:
+    """Append a test's measured errors as one JSON line to the file that
+    RT_PARITY_REPORT names (nothing when it is unset)."""
+    path = os.environ.get("RT_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"workload": name, "form": form, "steps": steps,
+                                "linf": {k: float(v) for k, v in errs.items()}}) + "\n")

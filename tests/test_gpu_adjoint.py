@@ -14,7 +14,7 @@ import oracle as O
 from paper_1508_07888_b300 import binding as B
 from paper_1508_07888_b300 import inputs as I
 
-from _harness import gpu_params, oracle_params, tables
+from _harness import gpu_params, oracle_params, report, tables
 
 pytestmark = pytest.mark.gpu
 
@@ -59,8 +59,11 @@ def test_adjoint_matches_oracle_adjoint(prec):
     X = run.forward(Q, n0)
     dQg, dn0g = run.backward(torch.as_tensor(wts, device="cuda"))
     run.close()
-    np.testing.assert_allclose(dQg.numpy(), dQo, rtol=1e-9)
     d = dn0g.cpu().numpy().reshape(-1)
+    report("adjoint 14x10x12 (vs the oracle's adjoint)", prec, steps,
+           {"dL_dQ": np.max(np.abs(dQg.numpy() - dQo) / np.abs(dQo)),
+            "dL_dn0": np.max(np.abs(d - dn0)) / np.max(np.abs(dn0))})
+    np.testing.assert_allclose(dQg.numpy(), dQo, rtol=1e-9)
     assert np.max(np.abs(d - dn0)) <= 1e-9 * np.max(np.abs(dn0))
     assert np.abs(dQo).min() > 0
 
@@ -97,18 +100,21 @@ def test_config5_gradients_match_finite_differences():
     gn = n0.grad.detach()
     assert L.item() > 0
     h = 1e-4
+    worst = {"dL_dQ": 0.0, "dL_dn0_directional": 0.0, "dL_dn0_cells": 0.0}
     with torch.no_grad():
         for k in range(len(Q0)):
             Qp, Qm = Q0.clone(), Q0.clone()
             Qp[k] *= 1 + h
             Qm[k] *= 1 - h
             fd = (loss(Qp, n00) - loss(Qm, n00)).item() / (2 * h * Q0[k].item())
+            worst["dL_dQ"] = max(worst["dL_dQ"], abs(gQ[k] - fd) / max(abs(fd), 1e-3 * np.abs(gQ).max()))
             assert gQ[k] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(gQ).max()), (k, gQ[k], fd)
         rng = np.random.default_rng(55)
         for _ in range(4):                       # directional derivatives
             v = torch.as_tensor(rng.standard_normal(n00.shape), device="cuda") * n00
             fd = (loss(Q0, n00 + h * v) - loss(Q0, n00 - h * v)).item() / (2 * h)
             ad = torch.sum(gn * v).item()
+            worst["dL_dn0_directional"] = max(worst["dL_dn0_directional"], abs(ad - fd) / abs(fd))
             assert ad == pytest.approx(fd, rel=1e-3, abs=0), (ad, fd)
         flat = gn.reshape(-1).cpu().numpy()
         top = np.argsort(-np.abs(flat))[:2000]
@@ -117,5 +123,8 @@ def test_config5_gradients_match_finite_differences():
             e[int(c)] = n00.reshape(-1)[int(c)]
             e = e.reshape(n00.shape)
             fd = (loss(Q0, n00 + h * e) - loss(Q0, n00 - h * e)).item() / (2 * h * e.reshape(-1)[int(c)].item())
+            worst["dL_dn0_cells"] = max(worst["dL_dn0_cells"],
+                                        abs(flat[c] - fd) / max(abs(fd), 1e-3 * np.abs(flat).max()))
             assert flat[c] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(flat).max()), (c, flat[c], fd)
+    report("adjoint 64^3 (gradient vs central differences)", "fp64", 200, worst)
     run.close()

@@ -16,25 +16,14 @@ steps.  The oracle runs on every host core (the ensemble's boxes side by
 side).  When RT_PARITY_REPORT names a file, each test appends its measured
 errors to it as one JSON line.
 """
-import json
-import os
-
 import numpy as np
 import pytest
 
 from paper_1508_07888_b300 import binding as B
 
-from _harness import field_errors, run_gpu
+from _harness import field_errors, report, run_gpu
 
 pytestmark = pytest.mark.gpu
-
-
-def report(name, prec, steps, errs):
-    path = os.environ.get("RT_PARITY_REPORT")
-    if path:
-        with open(path, "a") as f:
-            f.write(json.dumps({"workload": name, "form": prec, "steps": steps,
-                                "linf": errs}) + "\n")
 
 
 def check(prec, errs, name):

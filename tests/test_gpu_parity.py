@@ -13,7 +13,7 @@ import oracle as O
 from paper_1508_07888_b300 import binding as B
 from paper_1508_07888_b300 import inputs as I
 
-from _harness import field_errors, linf_rel, make_solver, run_gpu, run_oracle, tables
+from _harness import field_errors, linf_rel, make_solver, report, run_gpu, run_oracle, tables
 
 pytestmark = pytest.mark.gpu
 
@@ -78,10 +78,12 @@ def test_stromgren_config1_fp64_and_split():
     ora = run_oracle(w, 100)[0]
     gpu = run_gpu(w, 100, "fp64")[0][0]
     err = field_errors(gpu, ora, 1)
+    report("Stromgren 32^3", "fp64", 100, err)
     assert max(err.values()) <= 1e-12, err
     assert np.count_nonzero(gpu[1] < 0.5) == np.count_nonzero(ora[1] < 0.5)
     spl = run_gpu(w, 100, "split")[0][0]
     err = field_errors(spl, ora, 1)
+    report("Stromgren 32^3", "split", 100, err)
     print("split config-1 errors", err)
     assert err["N0"] <= 1e-4 and err["F0"] <= 1e-4, err
     assert err["xHI"] <= 1e-4, err
@@ -211,13 +213,18 @@ def test_transport_launch_shapes_are_bitwise_equal(shape, bc, flux):
         except B.RTError as e:
             assert e.code == B.RT_ERR_ARG and k >= 3, (k, e)
             break
-        shapes.add((stats.tile_x, stats.tile_y, stats.transport_grid))
+        shapes.add((stats.tile_x, stats.tile_y, stats.transport_grid, stats.transport_zchunk,
+                    stats.transport_lockstep, stats.transport_tma))
         for a, b in zip(out[:3], ref[:3]):
             np.testing.assert_array_equal(a, b)
         k += 1
     assert len({s[:2] for s in shapes}) == 3            # three tile shapes were run
+    assert len({s[3] for s in shapes}) >= 2              # whole columns and z-chunks
     (out,), stats = run_gpu(w, 3, "split", None, st, tune=1, flux=flux)
-    assert (stats.tile_x, stats.tile_y, stats.transport_grid) in shapes
+    assert (stats.tile_x, stats.tile_y, stats.transport_grid, stats.transport_zchunk,
+            stats.transport_lockstep, stats.transport_tma) in shapes
+    if flux == 0:                                        # GLF: lockstep rows and TMA were run
+        assert any(s[4] > 0 for s in shapes) and any(s[5] for s in shapes)
     for a, b in zip(out[:3], ref[:3]):
         np.testing.assert_array_equal(a, b)
 
@@ -231,15 +238,20 @@ def test_tuned_full_step_matches_default():
     for a, b in zip(out[:4], ref[:4]):
         np.testing.assert_array_equal(a, b)
     assert st.tile_x * st.tile_y == 256 and st.chem_grid > 0
+    (_,), st = run_gpu(w, 2, "split", tune=2 + 31)       # 16x16 tiles, planes by TMA
+    assert st.transport_tma == 1
+    (_,), st64 = run_gpu(w, 2, "fp64")
+    assert st64.transport_tma == 0
 
 
 def test_ensemble_launch_shapes_are_bitwise_equal():
     """Uneven boxes in one launch: every transport launch shape, the
-    column-aligned grids included (their runs then straddle boxes of other
-    depths), gives the same bits, state and history, as the default."""
+    column-aligned grids and the z-chunked orders included (their runs then
+    straddle boxes of other depths), gives the same bits, state and history,
+    as the default."""
     w = I.ensemble(nboxes=5, steps=6, sides=(8, 12, 16, 20), seed=11)
     ref, _ = run_gpu(w, 6, "split")
-    for k in (0, 5, 7, 9, 12, 14):
+    for k in (0, 5, 7, 9, 12, 14, 15, 18, 19, 23, 26, 27, 31):
         out, _ = run_gpu(w, 6, "split", tune=2 + k)
         for b in range(5):
             for x, y in zip(out[b][:4], ref[b][:4]):

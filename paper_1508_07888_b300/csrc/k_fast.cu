@@ -70,7 +70,7 @@ static cudaError_t transport_pm(const Launch &L, int zc, const rtd::Phys &ph, rt
 }
 
 template <int TX, int TY>
-static int pm_occupancy();
+static int pm_occupancy(bool tma);
 template <int TX, int TY>
 static int hll_occupancy();
 
@@ -193,7 +193,7 @@ static int generic_occupancy()
                rtk::transport_smem_bytes<R, FLUX>());
 }
 
-int transport_occupancy_fast(bool fp64, int variant, int flux)
+int transport_occupancy_fast(bool fp64, int variant, int flux, bool tma)
 {
     if (flux == RTD_FLUX_HLL && fp64) return generic_occupancy<double, RTD_FLUX_HLL>();
     if (flux == RTD_FLUX_HLL) {
@@ -205,9 +205,9 @@ int transport_occupancy_fast(bool fp64, int variant, int flux)
     }
     if (fp64) return generic_occupancy<double, RTD_FLUX_GLF>();
     switch (variant) {
-    case 1: return pm_occupancy<kTileX[1], kTileY[1]>();
-    case 2: return pm_occupancy<kTileX[2], kTileY[2]>();
-    default: return pm_occupancy<kTileX[0], kTileY[0]>();
+    case 1: return pm_occupancy<kTileX[1], kTileY[1]>(tma);
+    case 2: return pm_occupancy<kTileX[2], kTileY[2]>(tma);
+    default: return pm_occupancy<kTileX[0], kTileY[0]>(tma);
     }
 }
 
@@ -220,12 +220,16 @@ static int hll_occupancy()
 }
 
 template <int TX, int TY>
-static int pm_occupancy()
+static int pm_occupancy(bool tma)
 {
-    // the TMA form holds a little more shared memory; its residency bounds both
-    pm_attr<TX, TY, true>();
-    return occ((const void *)rtk::k_transport_pm<TX, TY, true>, rtk::transport_pm_threads<TX, TY>(),
-               rtk::transport_pm_smem_bytes<TX, TY, true>());
+    if (tma) {
+        pm_attr<TX, TY, true>();
+        return occ((const void *)rtk::k_transport_pm<TX, TY, true>, rtk::transport_pm_threads<TX, TY>(),
+                   rtk::transport_pm_smem_bytes<TX, TY, true>());
+    }
+    pm_attr<TX, TY, false>();
+    return occ((const void *)rtk::k_transport_pm<TX, TY, false>, rtk::transport_pm_threads<TX, TY>(),
+               rtk::transport_pm_smem_bytes<TX, TY, false>());
 }
 
 __global__ void k_fill_tune(float4 *U, int64_t n)

@@ -78,10 +78,10 @@ static int occ(const void *f, int threads, size_t smem = 0)
     return n > 0 ? n : 1;
 }
 
-int transport_occupancy_fast(bool fp64, int variant, int flux);
+int transport_occupancy_fast(bool fp64, int variant, int flux, bool tma);
 int chem_occupancy_fast(bool fp64, int G);
 
-int transport_occupancy(bool fp64, bool strict, int variant, int flux)
+int transport_occupancy(bool fp64, bool strict, int variant, int flux, bool tma)
 {
     if (strict) {
         if (flux == RTD_FLUX_HLL) {
@@ -93,7 +93,7 @@ int transport_occupancy(bool fp64, bool strict, int variant, int flux)
         return occ((const void *)rtk::k_transport<double, true, RTD_FLUX_GLF>, RTD_TX * RTD_TY,
                    rtk::transport_smem_bytes<double, RTD_FLUX_GLF>());
     }
-    return transport_occupancy_fast(fp64, variant, flux);
+    return transport_occupancy_fast(fp64, variant, flux, tma);
 }
 
 int chem_occupancy(bool fp64, bool strict, int G)

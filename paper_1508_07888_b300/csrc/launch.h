@@ -83,7 +83,9 @@ cudaError_t transport_adj(int G, const rtd::BoxDev *boxes, const double *U, cons
 void set_thread_error(const char *msg);
 
 // resident blocks per SM of each kernel (for persistent grid sizing)
-int transport_occupancy(bool fp64, bool strict, int variant = 0, int flux = RTD_FLUX_GLF);
+// blocks per SM of the transport kernel a launch runs (tma: the FP32 GLF
+// kernel's TMA form)
+int transport_occupancy(bool fp64, bool strict, int variant = 0, int flux = RTD_FLUX_GLF, bool tma = false);
 int chem_occupancy(bool fp64, bool strict, int G);
 
 }  // namespace rtl

@@ -267,6 +267,7 @@ static TuneChoice tune_candidate(rt_handle *h, int k, int nsm)
                 : k < 10 * V ? (k - 8 * V) / 2
                 : k - 10 * V;
     const int occ = rtl::transport_occupancy(false, false, v, h->p.flux);
+    const int occ_tma = rtl::transport_occupancy(false, false, v, h->p.flux, true);
     std::vector<rtd::BoxDev> bd = h->bdev;
     apply_layout(h, bd, v);
     int64_t nt = 0, ncol = 0;
@@ -276,14 +277,15 @@ static TuneChoice tune_candidate(rt_handle *h, int k, int nsm)
     }
     const bool glf = h->p.flux == RT_FLUX_GLF;
     if (k < 3 * V) return {v, tgrid_of(nt, std::min(k % 3 + 1, occ), nsm), 0, 0, false};
-    if (k >= 10 * V) return {v, tgrid_of(nt, occ, nsm), 0, 0, glf};
+    if (k >= 10 * V) return {v, tgrid_of(nt, glf ? occ_tma : occ, nsm), 0, 0, glf};
     if (k >= 8 * V) {
         const int tx = bd[0].tiles_x;
         bool same = glf;
         for (const auto &D : bd) same = same && D.tiles_x == tx;
-        const int m = (occ * nsm) / tx;
+        const bool tma = glf && (k - 8 * V) % 2 == 1;
+        const int m = ((tma ? occ_tma : occ) * nsm) / tx;
         if (!same || m < 1) return {v, tgrid_of(nt, occ, nsm), 0, 0, false};
-        return {v, m * tx, 0, tx, glf && (k - 8 * V) % 2 == 1};
+        return {v, m * tx, 0, tx, tma};
     }
     if (k >= 5 * V) return {v, tgrid_of(nt, occ, nsm), kTuneChunk[(k - 5 * V) % 3], 0, false};
     const int64_t j = (k - 3 * V) % 2 + 1;

@@ -815,10 +815,11 @@ struct Halves {
 
 __device__ __forceinline__ float4 f4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
 
-__device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
+__device__ __forceinline__ void cell_closure(const V4<float> &u, float &P0, float &P1, float &P2, float &P3,
+                                             float &P4, float &P5)
 {
     const float N = u.x;
-    float P0 = 0.f, P1 = 0.f, P2 = 0.f, P3 = 0.f, P4 = 0.f, P5 = 0.f;
+    P0 = 0.f; P1 = 0.f; P2 = 0.f; P3 = 0.f; P4 = 0.f; P5 = 0.f;
     if (N > 1e-37f) {
         const float rN = rcp_approx(N);
         float ux = u.y * rN, uy = u.z * rN, uz = u.w * rN;
@@ -837,6 +838,11 @@ __device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
         P0 = gx * ux + Na; P3 = gy * uy + Na; P5 = gz * uz + Na;
         P1 = gx * uy; P2 = gx * uz; P4 = gy * uz;
     }
+}
+
+__device__ __forceinline__ void halves_of(const V4<float> &u, float P0, float P1, float P2, float P3, float P4,
+                                          float P5, Halves &h)
+{
     // scalar adds: the flux vectors' components are not aligned register
     // pairs, so packed adds would need moves to assemble them (same rounding)
     const float G[3][4] = {{u.y, P0, P1, P2}, {u.z, P1, P3, P4}, {u.w, P2, P4, P5}};
@@ -845,6 +851,13 @@ __device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
         h.R[d] = make_float4(u.x + G[d][0], u.y + G[d][1], u.z + G[d][2], u.w + G[d][3]);
         h.L[d] = make_float4(u.x - G[d][0], u.y - G[d][1], u.z - G[d][2], u.w - G[d][3]);
     }
+}
+
+__device__ __forceinline__ void cell_halves(const V4<float> &u, Halves &h)
+{
+    float P0, P1, P2, P3, P4, P5;
+    cell_closure(u, P0, P1, P2, P3, P4, P5);
+    halves_of(u, P0, P1, P2, P3, P4, P5, h);
 }
 
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
@@ -922,6 +935,54 @@ constexpr size_t transport_pm_smem_bytes()
 template <int TX, int TY>
 constexpr int transport_pm_threads() { return (TX * TY + 2 * (TX + TY) + 31) / 32 * 32; }
 
+// This block's share [ubeg, uend) of the launch's plane units.  lockx > 0
+// (lockstep rows): the grid is groups of lockx blocks; group k takes the
+// k-th equal share of the row-planes (box, group, y-tile, z) and block lix
+// of the group their tile column lix.
+__device__ __forceinline__ void pm_share(int64_t nunits, int lockx, int64_t &ubeg, int64_t &uend, int &lix)
+{
+    lix = 0;
+    if (lockx > 0) {
+        const int64_t m = gridDim.x / lockx, k = blockIdx.x / lockx;
+        lix = (int)(blockIdx.x - k * lockx);
+        const int64_t nrp = nunits / lockx;   // row-planes of all boxes
+        ubeg = nrp * k / m;
+        uend = nrp * (k + 1) / m;
+    } else {
+        ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
+        uend = nunits * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    }
+}
+
+// The run that starts at unit u of the share (at most uend - u units):
+// returns its box; group g, tile (ix, iy), planes z0 .. z1-1.  Lockstep: u
+// counts row-planes and the tile column is lix.
+__device__ __forceinline__ int pm_run(const BoxDev *__restrict__ boxes, int nboxes, int64_t u, int64_t uend,
+                                      int lockx, int lix, int &g, int &iy, int &ix, int &z0, int &z1)
+{
+    if (lockx > 0) {
+        // box of row-plane u: the last with titem0 / lockx <= u
+        int lo = 0, hi = nboxes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (boxes[mid].titem0 / lockx <= u) lo = mid; else hi = mid - 1;
+        }
+        const BoxDev &Bb = boxes[lo];
+        const int64_t loc = u - Bb.titem0 / lockx;
+        const int64_t row = loc / Bb.nz;
+        z0 = (int)(loc - row * Bb.nz);
+        const int64_t lim = (int64_t)z0 + (uend - u);
+        z1 = lim < (int64_t)Bb.nz ? (int)lim : Bb.nz;
+        iy = (int)(row % Bb.tiles_y);
+        g = (int)(row / Bb.tiles_y);
+        ix = lix;
+        return lo;
+    }
+    const int b = find_box_unit(boxes, nboxes, u);
+    transport_run(boxes[b], u - boxes[b].titem0, uend - u, g, iy, ix, z0, z1);
+    return b;
+}
+
 // FP32 transport of the split form.  Same pipeline and work split as
 // k_transport; the unsplit GLF update is evaluated in its convex form
 //   U* = (1 - 3 lam) U + (lam/2) sum_d [ (U + G_d)(left_d) + (U - G_d)(right_d) ],
@@ -982,40 +1043,11 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
     unsigned pl_issued = 0, pl_done = 0;      // planes issued / consumed by the block
 
     int64_t ubeg, uend;
-    int lix = 0;                              // lockstep: this block's tile column
-    if (lockx > 0) {
-        const int64_t m = gridDim.x / lockx, k = blockIdx.x / lockx;
-        lix = (int)(blockIdx.x - k * lockx);
-        const int64_t nrp = nunits / lockx;   // row-planes of all boxes
-        ubeg = nrp * k / m;
-        uend = nrp * (k + 1) / m;
-    } else {
-        ubeg = nunits * (int64_t)blockIdx.x / gridDim.x;
-        uend = nunits * (int64_t)(blockIdx.x + 1) / gridDim.x;
-    }
+    int lix;                                  // lockstep: this block's tile column
+    pm_share(nunits, lockx, ubeg, uend, lix);
     for (int64_t u = ubeg; u < uend;) {
-        int b, g, iy, ix, z0, z1;
-        if (lockx > 0) {
-            // box of row-plane u: the last with titem0 / lockx <= u
-            int lo = 0, hi = nboxes - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (boxes[mid].titem0 / lockx <= u) lo = mid; else hi = mid - 1;
-            }
-            b = lo;
-            const BoxDev &Bb = boxes[b];
-            const int64_t loc = u - Bb.titem0 / lockx;
-            const int64_t row = loc / Bb.nz;
-            z0 = (int)(loc - row * Bb.nz);
-            const int64_t lim = (int64_t)z0 + (uend - u);
-            z1 = lim < (int64_t)Bb.nz ? (int)lim : Bb.nz;
-            iy = (int)(row % Bb.tiles_y);
-            g = (int)(row / Bb.tiles_y);
-            ix = lix;
-        } else {
-            b = find_box_unit(boxes, nboxes, u);
-            transport_run(boxes[b], u - boxes[b].titem0, uend - u, g, iy, ix, z0, z1);
-        }
+        int g, iy, ix, z0, z1;
+        const int b = pm_run(boxes, nboxes, u, uend, lockx, lix, g, iy, ix, z0, z1);
         const BoxDev &B = boxes[b];
         const int nx = B.nx, ny = B.ny, nz = B.nz;
         u += z1 - z0;

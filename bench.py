@@ -61,6 +61,8 @@ def parse():
                     help="instead of the bench line: one JSON line per workload x form")
     ap.add_argument("--only", choices=["reion256", "ensemble", "hll"], default=None,
                     help="run that row alone and print it (profiling commands)")
+    ap.add_argument("--chem-tune", type=int, default=1,
+                    help="chemistry launch shape: 1 = tuned at create, 2 + k = shape k, 0 = default")
     ap.add_argument("--tune", type=int, default=1,
                     help="rt_params.tune of the split form: 1 = time the transport's launch "
                          "shapes at create, 2 + k = shape k (profiling runs fix the shape)")
@@ -178,16 +180,19 @@ def group_table(w):
 
 
 TUNE = 1
+CHEM_TUNE = 1
 
 
-def make_params(w, precision, tune=None):
-    """tune = 1: the library times the transport's launch shapes at create
-    (outside every timed region) and keeps the fastest."""
+def make_params(w, precision, tune=None, chem_tune=None):
+    """tune = 1 / chem_tune = 1: the library times the transport's and the
+    chemistry's launch shapes at create (outside every timed region) and keeps
+    the fastest."""
     tune = TUNE if tune is None else tune
+    chem_tune = CHEM_TUNE if chem_tune is None else chem_tune
     from paper_1508_07888_b300 import binding as B
     return B.make_params(w.ngroups, group_table(w), w.c_red, cfl=w.cfl, ots=w.ots,
                          isothermal=w.isothermal, nsub=w.nsub, bc=w.bc, precision=precision,
-                         tune=tune, rates_const=w.rates_const, alphaA=w.alphaA,
+                         tune=tune, chem_tune=chem_tune, rates_const=w.rates_const, alphaA=w.alphaA,
                          alphaB=w.alphaB, beta=w.beta)
 
 
@@ -269,7 +274,8 @@ def time_device(w, precision, K, W, nsteps, ws, profile):
     launch = {"transport_tile": [st.tile_x, st.tile_y], "transport_grid": st.transport_grid,
               "transport_zchunk": st.transport_zchunk, "transport_tma": bool(st.transport_tma),
               "transport_lockstep": st.transport_lockstep,
-              "chemistry_grid": st.chem_grid, "tuned": bool(r.p.tune)}
+              "chemistry_grid": st.chem_grid, "chemistry_grab": st.chem_grab,
+              "tuned": bool(r.p.tune), "chemistry_tuned": bool(r.p.chem_tune)}
     r.close()
     return ms, kern, diag, nbytes, mean_sub, launch
 
@@ -701,9 +707,10 @@ def config_table():
 
 
 def main():
-    global TUNE
+    global TUNE, CHEM_TUNE
     args = parse()
     TUNE = args.tune
+    CHEM_TUNE = args.chem_tune
     if args.config_table:
         config_table()
         return

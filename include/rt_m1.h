@@ -119,9 +119,12 @@ typedef struct rt_params {
                                             of 16, 32, 64 planes (c = 0, 1, 2), k = 24 + 2 t +
                                             s for tile t in lockstep rows by per-thread copies
                                             (s = 0) or TMA (s = 1), k = 30 + t for tile t with
-                                            TMA (GLF; TMA and lockstep rows fall back to the
-                                            default where they do not apply); k >= 33 is
-                                            RT_ERR_ARG.  Ignored by the FP64 forms */
+                                            TMA, k = 33 + 2 t + s for tile t with two photon
+                                            groups per block in column order (s = 0) or
+                                            lockstep rows (s = 1) (GLF; TMA, lockstep rows and
+                                            groups per block fall back to the default where
+                                            they do not apply); k >= 39 is RT_ERR_ARG.  Ignored
+                                            by the FP64 forms */
     int    flux;                         /* rt_flux; rt_adjoint and rt_transport_static need GLF */
     double inflow[6];                    /* photons/cm^2/s entering through each RT_BC_INFLOW face */
     int    cosmo;                        /* 1: supercomoving units (Sec. 3).  U holds the comoving
@@ -132,6 +135,17 @@ typedef struct rt_params {
                                             equation.  Every box must have the same dx. */
     double H0, omega_m, omega_l;         /* cosmo: Hubble constant (1/s), matter and vacuum densities */
     double a0;                           /* cosmo: expansion factor at rt_create (> 0) */
+    int    chem_tune;                    /* launch shape of the chemistry of the SPLIT and FP64
+                                            forms (the results do not depend on it): 0 = default
+                                            (the most resident blocks per SM, one work item per
+                                            draw), 1 = time every shape at rt_create on scratch
+                                            copies of the boxes' state and keep the fastest
+                                            (cached per device, form and box set for the
+                                            process; cosmo runs take the default), 2 + k = shape
+                                            k = 3 (b - 1) + j: b = 1, 2 resident blocks per SM
+                                            (capped by what fits), j = 0, 1, 2 for 1, 2, 4 work
+                                            items (128 cells each) per draw from the counter;
+                                            k >= 6 is RT_ERR_ARG.  Ignored by the strict form */
 } rt_params;
 
 typedef struct rt_box {
@@ -169,6 +183,8 @@ typedef struct rt_stats {
                                             0: per-thread copies */
     int     transport_lockstep;          /* tile columns per row of the lockstep-rows work
                                             order (0: off) */
+    int     chem_grab;                   /* chemistry work items a warp takes per draw */
+    int     transport_gpb;               /* photon groups per block of the FP32 GLF transport */
 } rt_stats;
 
 typedef struct rt_handle rt_handle;

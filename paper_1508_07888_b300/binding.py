@@ -54,6 +54,7 @@ class rt_params(C.Structure):
         ("cosmo", C.c_int),
         ("H0", C.c_double), ("omega_m", C.c_double), ("omega_l", C.c_double),
         ("a0", C.c_double),
+        ("chem_tune", C.c_int),
     ]
 
 
@@ -85,6 +86,8 @@ class rt_stats(C.Structure):
         ("transport_zchunk", C.c_int),
         ("transport_tma", C.c_int),
         ("transport_lockstep", C.c_int),
+        ("chem_grab", C.c_int),
+        ("transport_gpb", C.c_int),
     ]
 
 
@@ -254,7 +257,7 @@ def rt_transport_static(p: rt_params, box: rt_box, nsteps: int, stream_ptr: int 
 # ------------------------------------------------------------------ helpers
 def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, isothermal=False,
                 nsub=0, rates_const=False, alphaA=0.0, alphaB=0.0, beta=0.0, bc=(0,) * 6,
-                max_halvings=30, precision=RT_PREC_SPLIT, tune=0, flux=0,
+                max_halvings=30, precision=RT_PREC_SPLIT, tune=0, flux=0, chem_tune=0,
                 inflow=(0.0,) * 6, cosmo=None) -> rt_params:
     """cosmo: None, or (H0 [1/s], omega_m, omega_l, a0) for supercomoving units."""
     p = rt_params()
@@ -270,6 +273,7 @@ def make_params(ngroups: int, table: dict, c_red: float, *, cfl=0.9, ots=False, 
     p.max_halvings = max_halvings
     p.precision = precision
     p.tune = int(tune)
+    p.chem_tune = int(chem_tune)
     p.flux = int(flux)
     for k in range(6):
         p.inflow[k] = float(inflow[k])

@@ -63,14 +63,38 @@ static cudaError_t transport_pm_t(const Launch &L, int zc, const rtd::Phys &ph, 
     return cudaSuccess;
 }
 
+// groups per block (two photon groups of each tile in one block)
+template <int TX, int TY, int NG>
+static cudaError_t pmg_attr()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rtk::k_transport_pmg<TX, TY, NG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rtk::transport_pmg_smem_bytes<TX, TY, NG>());
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
 template <int TX, int TY>
 static cudaError_t transport_pm(const Launch &L, int zc, const rtd::Phys &ph, rtd::Ctl *ctl)
 {
+    if (L.gpb == 2 && !L.tma) {
+        cudaError_t e = pmg_attr<TX, TY, 2>();
+        if (e != cudaSuccess) return e;
+        rtk::k_transport_pmg<TX, TY, 2><<<L.grid, rtk::transport_pm_threads<TX, TY>(),
+                                          rtk::transport_pmg_smem_bytes<TX, TY, 2>(), L.stream>>>(
+            L.boxes, L.nboxes, L.nitems, L.lockstep, ph, ctl);
+        return cudaSuccess;
+    }
+    if (L.gpb != 1) return cudaErrorInvalidValue;
     return L.tma ? transport_pm_t<TX, TY, true>(L, zc, ph, ctl) : transport_pm_t<TX, TY, false>(L, zc, ph, ctl);
 }
 
 template <int TX, int TY>
-static int pm_occupancy(bool tma);
+static int pm_occupancy(bool tma, int gpb);
 template <int TX, int TY>
 static int hll_occupancy();
 
@@ -131,10 +155,10 @@ static void chem_g(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ct
 {
     if (fp64) {
         auto k = rtk::k_chem<G, double, double, false>;
-        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db);
+        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db, L.grab);
     } else {
         auto k = rtk::k_chem<G, float, float, false>;
-        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db);
+        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db, L.grab);
     }
 }
 
@@ -193,7 +217,7 @@ static int generic_occupancy()
                rtk::transport_smem_bytes<R, FLUX>());
 }
 
-int transport_occupancy_fast(bool fp64, int variant, int flux, bool tma)
+int transport_occupancy_fast(bool fp64, int variant, int flux, bool tma, int gpb)
 {
     if (flux == RTD_FLUX_HLL && fp64) return generic_occupancy<double, RTD_FLUX_HLL>();
     if (flux == RTD_FLUX_HLL) {
@@ -205,9 +229,9 @@ int transport_occupancy_fast(bool fp64, int variant, int flux, bool tma)
     }
     if (fp64) return generic_occupancy<double, RTD_FLUX_GLF>();
     switch (variant) {
-    case 1: return pm_occupancy<kTileX[1], kTileY[1]>(tma);
-    case 2: return pm_occupancy<kTileX[2], kTileY[2]>(tma);
-    default: return pm_occupancy<kTileX[0], kTileY[0]>(tma);
+    case 1: return pm_occupancy<kTileX[1], kTileY[1]>(tma, gpb);
+    case 2: return pm_occupancy<kTileX[2], kTileY[2]>(tma, gpb);
+    default: return pm_occupancy<kTileX[0], kTileY[0]>(tma, gpb);
     }
 }
 
@@ -220,8 +244,13 @@ static int hll_occupancy()
 }
 
 template <int TX, int TY>
-static int pm_occupancy(bool tma)
+static int pm_occupancy(bool tma, int gpb)
 {
+    if (gpb == 2 && !tma) {
+        pmg_attr<TX, TY, 2>();
+        return occ((const void *)rtk::k_transport_pmg<TX, TY, 2>, rtk::transport_pm_threads<TX, TY>(),
+                   rtk::transport_pmg_smem_bytes<TX, TY, 2>());
+    }
     if (tma) {
         pm_attr<TX, TY, true>();
         return occ((const void *)rtk::k_transport_pm<TX, TY, true>, rtk::transport_pm_threads<TX, TY>(),

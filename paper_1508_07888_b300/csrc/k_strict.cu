@@ -42,7 +42,7 @@ cudaError_t chem_strict(int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *c
 {
 #define CHEM_G(g)                                                                                \
     rtk::k_chem<g, double, double, true><<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(               \
-        L.boxes, L.nboxes, L.nitems, ph, ctl, db)
+        L.boxes, L.nboxes, L.nitems, ph, ctl, db, L.grab)
     switch (G) {
     case 1: CHEM_G(1); break;
     case 2: CHEM_G(2); break;
@@ -78,10 +78,10 @@ static int occ(const void *f, int threads, size_t smem = 0)
     return n > 0 ? n : 1;
 }
 
-int transport_occupancy_fast(bool fp64, int variant, int flux, bool tma);
+int transport_occupancy_fast(bool fp64, int variant, int flux, bool tma, int gpb);
 int chem_occupancy_fast(bool fp64, int G);
 
-int transport_occupancy(bool fp64, bool strict, int variant, int flux, bool tma)
+int transport_occupancy(bool fp64, bool strict, int variant, int flux, bool tma, int gpb)
 {
     if (strict) {
         if (flux == RTD_FLUX_HLL) {
@@ -93,7 +93,7 @@ int transport_occupancy(bool fp64, bool strict, int variant, int flux, bool tma)
         return occ((const void *)rtk::k_transport<double, true, RTD_FLUX_GLF>, RTD_TX * RTD_TY,
                    rtk::transport_smem_bytes<double, RTD_FLUX_GLF>());
     }
-    return transport_occupancy_fast(fp64, variant, flux, tma);
+    return transport_occupancy_fast(fp64, variant, flux, tma, gpb);
 }
 
 int chem_occupancy(bool fp64, bool strict, int G)

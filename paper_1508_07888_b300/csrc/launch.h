@@ -23,6 +23,8 @@ struct Launch {
     bool tma = false;                // FP32 GLF transport: every box has its tensor maps
     int lockstep = 0;                // FP32 GLF transport: tile columns of the lockstep-rows
                                      // order (every box has that many; grid a multiple), 0 = off
+    int grab = 1;                    // chemistry: work items a warp takes per draw
+    int gpb = 1;                     // FP32 GLF transport: photon groups per block (1 or 2)
 };
 
 // the three TMA tensor maps of a box's FP32 radiation state U for tile shape
@@ -53,13 +55,14 @@ cudaError_t chem_fine_strict(int G, const Launch &L, const rtd::FineDev *fines, 
 // (zlen <= 0 or >= nz: whole columns; only the FP32 kernels take chunks) and
 // the number of plane units (ngroups x tiles_x x tiles_y x nz) the transport
 // kernel spreads over its grid
-inline void transport_layout(rtd::BoxDev &B, int ngroups, int variant = 0, int zlen = 0)
+inline void transport_layout(rtd::BoxDev &B, int ngroups, int variant = 0, int zlen = 0, int gpb = 1)
 {
     const int tx = kTileX[variant], ty = kTileY[variant];
     B.tiles_x = (B.nx + tx - 1) / tx;
     B.tiles_y = (B.ny + ty - 1) / ty;
     B.zlen = zlen <= 0 || zlen >= B.nz ? B.nz : zlen;
-    B.ntitems = (int64_t)ngroups * B.tiles_x * B.tiles_y * B.nz;
+    const int gblocks = (ngroups + gpb - 1) / gpb;  // units count blocks of gpb groups
+    B.ntitems = (int64_t)gblocks * B.tiles_x * B.tiles_y * B.nz;
 }
 
 // a realizable radiation state (N = 1, F = (0.3, 0.2, 0.1)) in n cells of
@@ -85,7 +88,8 @@ void set_thread_error(const char *msg);
 // resident blocks per SM of each kernel (for persistent grid sizing)
 // blocks per SM of the transport kernel a launch runs (tma: the FP32 GLF
 // kernel's TMA form)
-int transport_occupancy(bool fp64, bool strict, int variant = 0, int flux = RTD_FLUX_GLF, bool tma = false);
+int transport_occupancy(bool fp64, bool strict, int variant = 0, int flux = RTD_FLUX_GLF, bool tma = false,
+                        int gpb = 1);
 int chem_occupancy(bool fp64, bool strict, int G);
 
 }  // namespace rtl

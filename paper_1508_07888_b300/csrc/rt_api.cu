@@ -71,11 +71,13 @@ struct rt_handle {
     int64_t ntitems = 0, ncitems = 0;
     int zc = 32;
     int tgrid = 1, cgrid = 1;
+    int cgrab = 1;                           // chemistry: work items per draw
     int tvariant = 0;                        // tile shape of the FP32 transport (rtl::kTileX/Y)
     int tzlen = 0;                           // its z-chunk length (0: whole columns)
     void *d_tmaps = nullptr;                 // FP32 GLF transport: 3 TMA tensor maps per box
     bool tma = false;                        // every box has its maps (the TMA kernel runs)
     int tlock = 0;                           // lockstep-rows order: tile columns per row (0: off)
+    int tgpb = 1;                            // FP32 GLF transport: photon groups per block
     int nsm = 1, chem_occ = 1;               // SMs, resident chemistry blocks per SM
     std::vector<rtd::FineDev> fdev;          // CRTA fine level per box (host mirror)
     rtd::FineDev *d_fines = nullptr;
@@ -152,6 +154,11 @@ static void release(rt_handle *h)
     delete h;
 }
 
+// chemistry launch shapes: k = 3 (b - 1) + j, b = 1, 2 resident blocks per
+// SM (capped by what fits), j: 1, 2, 4 work items per draw
+static constexpr int kChemCandidates = 6;
+static constexpr int kChemGrab[3] = {1, 2, 4};
+
 static int check_params(const rt_params *p)
 {
     if (!p) return fail(nullptr, RT_ERR_ARG, "params is NULL");
@@ -173,6 +180,8 @@ static int check_params(const rt_params *p)
     if (p->precision < RT_PREC_SPLIT || p->precision > RT_PREC_FP64_STRICT)
         return fail(nullptr, RT_ERR_ARG, "unknown precision %d", p->precision);
     if (p->tune < 0) return fail(nullptr, RT_ERR_ARG, "tune must be >= 0");
+    if (p->chem_tune < 0 || p->chem_tune >= 2 + kChemCandidates)
+        return fail(nullptr, RT_ERR_ARG, "chem_tune %d outside [0, %d]", p->chem_tune, 1 + kChemCandidates);
     if (p->flux != RT_FLUX_GLF && p->flux != RT_FLUX_HLL)
         return fail(nullptr, RT_ERR_ARG, "unknown flux %d", p->flux);
     if (p->cosmo != 0 && p->cosmo != 1) return fail(nullptr, RT_ERR_ARG, "cosmo must be 0 or 1");
@@ -236,17 +245,18 @@ struct TuneChoice {
     int zlen;                 // z-chunk length of the unit order (0: whole columns)
     int lockx;                // lockstep rows: tile columns per row (0: off)
     bool tma;                 // GLF planes loaded by TMA
+    int gpb = 1;              // GLF photon groups per block
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune_cache;
-constexpr int kTuneCandidates = 11 * rtl::kTileVariants;
+constexpr int kTuneCandidates = 13 * rtl::kTileVariants;
 constexpr int kTuneChunk[3] = {16, 32, 64};
 
-static void apply_layout(rt_handle *h, std::vector<rtd::BoxDev> &bd, int variant, int zlen = 0)
+static void apply_layout(rt_handle *h, std::vector<rtd::BoxDev> &bd, int variant, int zlen = 0, int gpb = 1)
 {
     int64_t titem = 0;
     for (auto &D : bd) {
-        rtl::transport_layout(D, h->p.ngroups, variant, zlen);
+        rtl::transport_layout(D, h->p.ngroups, variant, zlen, gpb);
         D.titem0 = titem;
         titem += D.ntitems;
     }
@@ -265,7 +275,8 @@ static TuneChoice tune_candidate(rt_handle *h, int k, int nsm)
                 : k < 5 * V ? (k - 3 * V) / 2
                 : k < 8 * V ? (k - 5 * V) / 3
                 : k < 10 * V ? (k - 8 * V) / 2
-                : k - 10 * V;
+                : k < 11 * V ? k - 10 * V
+                : (k - 11 * V) / 2;
     const int occ = rtl::transport_occupancy(false, false, v, h->p.flux);
     const int occ_tma = rtl::transport_occupancy(false, false, v, h->p.flux, true);
     std::vector<rtd::BoxDev> bd = h->bdev;
@@ -276,6 +287,28 @@ static TuneChoice tune_candidate(rt_handle *h, int k, int nsm)
         ncol += D.ntitems / D.nz;
     }
     const bool glf = h->p.flux == RT_FLUX_GLF;
+    if (k >= 11 * V) {
+        // two photon groups per block (GLF with G >= 2), column order or lockstep rows
+        if (!glf || h->p.ngroups < 2) return {v, tgrid_of(nt, occ, nsm), 0, 0, false};
+        std::vector<rtd::BoxDev> b2 = h->bdev;
+        apply_layout(h, b2, v, 0, 2);
+        int64_t nt2 = 0;
+        for (const auto &D : b2) nt2 += D.ntitems;
+        const int occ2 = rtl::transport_occupancy(false, false, v, h->p.flux, false, 2);
+        TuneChoice c{v, tgrid_of(nt2, occ2, nsm), 0, 0, false};
+        c.gpb = 2;
+        if ((k - 11 * V) % 2 == 1) {
+            const int tx = b2[0].tiles_x;
+            bool same = true;
+            for (const auto &D : b2) same = same && D.tiles_x == tx;
+            const int m = (occ2 * nsm) / tx;
+            if (same && m >= 1) {
+                c.grid = m * tx;
+                c.lockx = tx;
+            }
+        }
+        return c;
+    }
     if (k < 3 * V) return {v, tgrid_of(nt, std::min(k % 3 + 1, occ), nsm), 0, 0, false};
     if (k >= 10 * V) return {v, tgrid_of(nt, glf ? occ_tma : occ, nsm), 0, 0, glf};
     if (k >= 8 * V) {
@@ -331,7 +364,7 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
         bool dup = false;
         for (const auto &o : cand)
             dup |= o.variant == c.variant && o.grid == c.grid && o.zlen == c.zlen && o.lockx == c.lockx &&
-                   o.tma == c.tma;
+                   o.tma == c.tma && o.gpb == c.gpb;
         if (!dup) cand.push_back(c);
     }
     std::string key = std::to_string(dev) + "/" + std::to_string(h->p.flux) + "/" + std::to_string(h->p.ngroups);
@@ -378,7 +411,7 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
             }
             float best_ms = 0.f;
             for (const auto &c : cand) {
-                apply_layout(h, bd, c.variant, c.zlen);
+                apply_layout(h, bd, c.variant, c.zlen, c.gpb);
                 int64_t nt = 0;
                 for (const auto &D : bd) nt += D.ntitems;
                 CU(h, cudaStreamSynchronize(h->s));               // the maps' buffer is rewritten
@@ -390,6 +423,7 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
                 rtl::Launch L{tbox, h->nboxes, nt, c.grid, h->s, c.variant};
                 L.tma = tma;
                 L.lockstep = c.lockx;
+                L.gpb = c.gpb;
                 CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));      // warm-up
                 CU(h, cudaEventRecord(e0, h->s));
                 for (int r = 0; r < 5; r++) CU(h, rtl::transport_fast(false, L, h->zc, h->ph, h->d_ctl));
@@ -406,15 +440,127 @@ static int tune_transport(rt_handle *h, int tune, int dev, int nsm)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    apply_layout(h, h->bdev, best.variant, best.zlen);
+    apply_layout(h, h->bdev, best.variant, best.zlen, best.gpb);
     h->ntitems = 0;
     for (const auto &D : h->bdev) h->ntitems += D.ntitems;
     h->tvariant = best.variant;
     h->tgrid = best.grid;
     h->tzlen = best.zlen;
     h->tlock = best.lockx;
+    h->tgpb = best.gpb;
     if (int rc2 = setup_tma(h, best.tma)) return rc2;
     CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * h->nboxes, cudaMemcpyHostToDevice));
+    return RT_OK;
+}
+
+// chemistry launch shape k (grid and work items per draw)
+static void chem_candidate(const rt_handle *h, int k, int &grid, int &grab)
+{
+    const int b = std::min(k / 3 + 1, std::max(h->chem_occ, 1));
+    grab = kChemGrab[k % 3];
+    const int64_t wpb = RTD_CHEM_BLOCK / 32;             // warps (work items) per block
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->ncitems + wpb - 1) / wpb, (int64_t)b * h->nsm));
+}
+
+static std::map<std::string, int> g_chem_cache;
+
+// chem_tune = 2 + k fixes shape k; chem_tune = 1 times every shape on scratch
+// copies of the boxes' state (x_HI, T, and U as the post-transport field; the
+// outputs go to scratch, so the caller's state is not touched): one warm-up,
+// then three launches each, CUDA events.  The shape does not enter any result
+// (every cell's arithmetic and every sum's order are fixed), so the fastest is
+// kept.  Supercomoving runs take the default (their a(t) table is filled per call).
+static int tune_chem(rt_handle *h, int tune, int dev)
+{
+    int best = 0;
+    if (tune >= 2) {
+        best = tune - 2;
+    } else if (!h->p.cosmo) {
+        std::string key = std::to_string(dev) + "/" + std::to_string(h->fp64) + "/" +
+                          std::to_string(h->p.ngroups) + "/" + std::to_string(h->p.ots);
+        for (const auto &D : h->bdev)
+            key += "/" + std::to_string(D.nx) + "x" + std::to_string(D.ny) + "x" + std::to_string(D.nz);
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_chem_cache.find(key);
+            if (it != g_chem_cache.end()) { best = it->second; have = true; }
+        }
+        if (!have) {
+            const size_t es = h->fp64 ? 8 : 4;
+            const int G = h->p.ngroups;
+            std::vector<void *> bufs;
+            rtd::BoxDev *tbox = nullptr;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            auto cleanup = [&]() {
+                for (void *q : bufs) cudaFree(q);
+                cudaFree(tbox);
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
+            };
+            int rc = [&]() -> int {
+                std::vector<rtd::BoxDev> bd = h->bdev;
+                std::vector<double *> x0(h->nboxes), T0(h->nboxes);
+                for (int b = 0; b < h->nboxes; b++) {
+                    rtd::BoxDev &D = bd[b];
+                    const size_t nU = (size_t)G * D.ncell * 4 * es;
+                    void *uo = nullptr, *xs = nullptr, *ts = nullptr;
+                    CU(h, cudaMalloc(&uo, nU));
+                    bufs.push_back(uo);
+                    CU(h, cudaMalloc(&xs, (size_t)D.ncell * 8));
+                    bufs.push_back(xs);
+                    CU(h, cudaMalloc(&ts, (size_t)D.ncell * 8));
+                    bufs.push_back(ts);
+                    // the library's post-transport scratch holds the caller's field
+                    CU(h, cudaMemcpyAsync(D.Us, D.U, nU, cudaMemcpyDeviceToDevice, h->s));
+                    x0[b] = D.xHI;
+                    T0[b] = D.T;
+                    D.U = uo;
+                    D.xHI = static_cast<double *>(xs);
+                    D.T = static_cast<double *>(ts);
+                }
+                auto restore = [&]() -> int {
+                    for (int b = 0; b < h->nboxes; b++) {
+                        CU(h, cudaMemcpyAsync(bd[b].xHI, x0[b], (size_t)bd[b].ncell * 8, cudaMemcpyDeviceToDevice, h->s));
+                        CU(h, cudaMemcpyAsync(bd[b].T, T0[b], (size_t)bd[b].ncell * 8, cudaMemcpyDeviceToDevice, h->s));
+                    }
+                    return RT_OK;
+                };
+                CU(h, cudaMalloc(&tbox, sizeof(rtd::BoxDev) * h->nboxes));
+                CU(h, cudaMemcpyAsync(tbox, bd.data(), sizeof(rtd::BoxDev) * h->nboxes, cudaMemcpyHostToDevice, h->s));
+                CU(h, cudaEventCreate(&e0));
+                CU(h, cudaEventCreate(&e1));
+                const rtd::DiagBuf db{h->d_partials, h->d_lanes, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
+                float best_ms = 0.f;
+                for (int k = 0; k < kChemCandidates; k++) {
+                    int grid, grab;
+                    chem_candidate(h, k, grid, grab);
+                    rtl::Launch L{tbox, h->nboxes, h->ncitems, grid, h->s};
+                    L.grab = grab;
+                    if (int r2 = restore()) return r2;
+                    CU(h, rtl::chem_fast(h->fp64, G, L, h->ph, h->d_ctl, db));          // warm-up
+                    if (int r2 = restore()) return r2;
+                    CU(h, cudaEventRecord(e0, h->s));
+                    for (int r = 0; r < 3; r++) CU(h, rtl::chem_fast(h->fp64, G, L, h->ph, h->d_ctl, db));
+                    CU(h, cudaEventRecord(e1, h->s));
+                    CU(h, cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CU(h, cudaEventElapsedTime(&ms, e0, e1));
+                    if (k == 0 || ms < best_ms) { best = k; best_ms = ms; }
+                }
+                // the timing launches' counters and diagnostics are not the run's
+                CU(h, cudaMemsetAsync(h->d_ctl, 0, sizeof(rtd::Ctl), h->s));
+                CU(h, cudaMemsetAsync(h->d_lastdiag, 0, sizeof(double) * RTD_NDIAG * h->nboxes, h->s));
+                CU(h, cudaStreamSynchronize(h->s));
+                return RT_OK;
+            }();
+            cleanup();
+            if (rc) return rc;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_chem_cache[key] = best;
+        }
+    }
+    chem_candidate(h, best, h->cgrid, h->cgrab);
     return RT_OK;
 }
 
@@ -616,7 +762,8 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMemcpy(h->d_fines, h->fdev.data(), sizeof(rtd::FineDev) * nboxes,
                                  cudaMemcpyHostToDevice));
                 if (!fp64 && p->tune > 0)
-                    return tune_transport(h, p->tune, dev, nsm);
+                    if (int rc2 = tune_transport(h, p->tune, dev, nsm)) return rc2;
+                if (!h->strict && p->chem_tune > 0) return tune_chem(h, p->chem_tune, dev);
                 return RT_OK;
             }()))
             return bail(rc);
@@ -696,7 +843,9 @@ static cudaError_t enqueue_step(rt_handle *h, cudaStream_t s, cudaEvent_t *ev = 
     rtl::Launch Lt{h->d_boxes, h->nboxes, h->ntitems, h->tgrid, s, h->tvariant};
     Lt.tma = h->tma;
     Lt.lockstep = h->tlock;
+    Lt.gpb = h->tgpb;
     rtl::Launch Lc{h->d_boxes, h->nboxes, h->ncitems, h->cgrid, s};
+    Lc.grab = h->cgrab;
     const rtd::DiagBuf db{h->d_partials, h->d_lanes, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
@@ -1129,6 +1278,8 @@ extern "C" int rt_query(rt_handle *h, rt_stats *st)
     st->transport_tma = h->tma ? 1 : 0;
     st->transport_lockstep = h->fp64 ? 0 : h->tlock;
     st->chem_grid = h->cgrid;
+    st->chem_grab = h->cgrab;
+    st->transport_gpb = h->tgpb;
     st->a = h->p.cosmo ? h->a_now : 1.0;
     return RT_OK;
 }

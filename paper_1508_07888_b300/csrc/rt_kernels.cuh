@@ -1244,6 +1244,211 @@ k_transport_pm(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int
     }
 }
 
+// Groups per block: the FP32 GLF transport with NG photon groups of each
+// tile in one block (the units count group blocks, ceil(G / NG) per tile and
+// plane).  Every thread copies and updates its cell in each of the block's
+// groups per plane: NG independent closures between two barriers, and the
+// barrier, the plane bookkeeping and the halo logic shared by the groups.
+// Layout, work orders (column, z-chunked, lockstep rows), per-cell arithmetic
+// and results are those of k_transport_pm with per-thread copies; the ring
+// and the halves hold NG groups, so NG = 2 takes one block per SM.
+template <int TX, int TY, int NG>
+struct TransportSmemPMG {
+    V4<float> U[TP_STAGES_PM][NG][TY + 2][TX + 3];
+    float4 H[2][NG][4][TY + 2][TX + 3];
+};
+
+template <int TX, int TY, int NG>
+constexpr size_t transport_pmg_smem_bytes() { return sizeof(TransportSmemPMG<TX, TY, NG>); }
+
+template <int TX, int TY, int NG>
+__global__ void __launch_bounds__(transport_pm_threads<TX, TY>(), 1)
+k_transport_pmg(const BoxDev *__restrict__ boxes, int nboxes, int64_t nunits, int lockx, Phys ph,
+                Ctl *ctl)
+{
+    static_assert(NG >= 2 && NG <= RTD_MAXG, "groups per block");
+    constexpr int S = TP_STAGES_PM;
+    extern __shared__ __align__(128) unsigned char tp_smem_pmg[];
+    auto &sm = *reinterpret_cast<TransportSmemPMG<TX, TY, NG> *>(tp_smem_pmg);
+
+    const int tid = threadIdx.x;
+    const bool interior = tid < TX * TY;
+    const int tx = interior ? tid % TX : 0, ty = interior ? tid / TX : 0;
+    if (blockIdx.x == 0 && tid == 0) ctl->step += 1;
+
+    int64_t ubeg, uend;
+    int lix;
+    pm_share(nunits, lockx, ubeg, uend, lix);
+    for (int64_t u = ubeg; u < uend;) {
+        int gb, iy, ix, z0, z1;
+        const int b = pm_run(boxes, nboxes, u, uend, lockx, lix, gb, iy, ix, z0, z1);
+        const BoxDev &B = boxes[b];
+        const int nx = B.nx, ny = B.ny, nz = B.nz;
+        u += z1 - z0;
+        if (ix >= B.tiles_x) continue;        // (lockstep on a box of other width: not set up)
+        const int g0 = gb * NG, ng = min(NG, ph.G - g0);     // the block's groups g0 .. g0+ng-1
+        const int x0 = ix * TX, y0 = iy * TY;
+        const int ntx = min(TX, nx - x0), nty = min(TY, ny - y0);
+        const int x = x0 + tx, y = y0 + ty;
+        const bool act = interior && (tx < ntx) && (ty < nty);
+        const int L = (z1 - z0) + 2;
+        const int64_t gst = B.ncell;          // one group's cells
+        const V4<float> *Ug = reinterpret_cast<const V4<float> *>(B.U) + (int64_t)g0 * gst;
+        V4<float> *Og = reinterpret_cast<V4<float> *>(B.Us) + (int64_t)g0 * gst;
+        const float lam = (float)B.lam;
+        const float c0 = 1.0f - 3.0f * lam, c1 = 0.5f * lam;
+        const int64_t sxy = (int64_t)nx * ny;
+
+        // halo cell of a halo thread and which half of it the tile needs:
+        // 0 = Rx (left column), 1 = Lx (right), 2 = Ry (bottom), 3 = Ly (top)
+        int hx = -1, hy = -1, sx = 0, sy = 0, hneg = 0, hk = 0;
+        float hin[NG];                    // inflow ghost per group: beam density, sign = direction
+#pragma unroll
+        for (int k = 0; k < NG; k++) hin[k] = 0.0f;
+        bool hif = false;                 // the halo cell is an inflow ghost
+        if (!interior) {
+            int t = tid - TX * TY;
+            if (t < nty) {
+                hx = 0; hy = t + 1; sy = y0 + t; sx = x0 - 1; hk = 0;
+                if (sx < 0) {
+                    if (ph.bc[0] == 0) sx = nx - 1;
+                    else { sx = 0; hneg = ph.bc[0] == 2 ? 1 : 0; }
+                    if (ph.bc[0] == 3) {
+                        hif = true;
+#pragma unroll
+                        for (int k = 0; k < NG; k++)
+                            if (k < ng) hin[k] = (float)(ph.inflow_c[0][g0 + k] * B.inv_nunit);
+                    }
+                }
+            } else if ((t -= nty) < nty) {
+                hx = ntx + 1; hy = t + 1; sy = y0 + t; sx = x0 + ntx; hk = 1;
+                if (sx >= nx) {
+                    if (ph.bc[1] == 0) sx = 0;
+                    else { sx = nx - 1; hneg = ph.bc[1] == 2 ? 1 : 0; }
+                    if (ph.bc[1] == 3) {
+                        hif = true;
+#pragma unroll
+                        for (int k = 0; k < NG; k++)
+                            if (k < ng) hin[k] = -(float)(ph.inflow_c[1][g0 + k] * B.inv_nunit);
+                    }
+                }
+            } else if ((t -= nty) < ntx) {
+                hx = t + 1; hy = 0; sx = x0 + t; sy = y0 - 1; hk = 2;
+                if (sy < 0) {
+                    if (ph.bc[2] == 0) sy = ny - 1;
+                    else { sy = 0; hneg = ph.bc[2] == 2 ? 2 : 0; }
+                }
+            } else if ((t -= ntx) < ntx) {
+                hx = t + 1; hy = nty + 1; sx = x0 + t; sy = y0 + nty; hk = 3;
+                if (sy >= ny) {
+                    if (ph.bc[3] == 0) sy = 0;
+                    else { sy = ny - 1; hneg = ph.bc[3] == 2 ? 2 : 0; }
+                }
+            }
+        }
+        // plane q is z0 - 1 + q, wrapped (periodic) or clamped (ghost planes
+        // copy the face plane, negated when reflective); the ring starts at
+        // slot 0 in every run (the previous run drained it)
+        const V4<float> *gown = Ug + (int64_t)y * nx + x;
+        const V4<float> *ghalo = Ug + (int64_t)sy * nx + sx;
+        const bool zneg_first = z0 == 0 && ph.bc[4] == 2, zneg_last = z1 == nz && ph.bc[5] == 2;
+        int zi = z0 - 1;
+        int slot_i = 0;
+        int64_t pl_in = (int64_t)zi * sxy;
+        const int64_t pl_lo = ph.bc[4] == 0 ? (int64_t)(nz - 1) * sxy : 0;
+        const int64_t pl_hi = ph.bc[5] == 0 ? 0 : (int64_t)(nz - 1) * sxy;
+        auto issue = [&]() {
+            if (zi < z1 + 1) {
+                const int64_t pl = zi < 0 ? pl_lo : (zi >= nz ? pl_hi : pl_in);
+#pragma unroll
+                for (int k = 0; k < NG; k++) {
+                    if (k < ng) {
+                        if (act) cp_async16(&sm.U[slot_i][k][ty + 1][tx + 1], gown + k * gst + pl);
+                        if (hx >= 0) {
+                            if (hif) sm.U[slot_i][k][hy][hx] = V4<float>{fabsf(hin[k]), hin[k], 0.0f, 0.0f};
+                            else cp_async16(&sm.U[slot_i][k][hy][hx], ghalo + k * gst + pl);
+                        }
+                    }
+                }
+            }
+            cp_async_commit();
+            zi++;
+            pl_in += sxy;
+            slot_i = slot_i + 1 == S ? 0 : slot_i + 1;
+        };
+#pragma unroll
+        for (int q = 0; q < S - 2; q++) issue();
+
+        V4<float> uc[NG];                   // own cell of plane q-1, per group
+        float4 Rz_prev[NG], Rz_c[NG];       // right-going z halves of planes q-2 and q-1
+#pragma unroll
+        for (int k = 0; k < NG; k++) {
+            uc[k] = V4<float>{0.0f, 0.0f, 0.0f, 0.0f};
+            Rz_prev[k] = Rz_c[k] = float4{};
+        }
+        V4<float> *out = Og + (int64_t)z0 * sxy + (int64_t)y * nx + x;
+        int slot = 0;
+#pragma unroll 1
+        for (int q = 0; q < L; q++) {
+            cp_async_wait<S - 3>();
+            __syncthreads();
+            issue();
+            const int hs = q & 1, cs = hs ^ 1;
+            const bool zneg = (q == 0 && zneg_first) || (q == L - 1 && zneg_last);
+#pragma unroll
+            for (int k = 0; k < NG; k++) {
+                if (k >= ng) continue;        // (the same in every thread)
+                V4<float> un = {};
+                float4 Rz_n = {}, Lz_n = {};
+                if (act) {
+                    un = sm.U[slot][k][ty + 1][tx + 1];
+                    if (zneg) un.w = -un.w;
+                    Halves hv;
+                    cell_halves(un, hv);
+                    Rz_n = hv.R[2];
+                    Lz_n = hv.L[2];
+                    sm.H[hs][k][0][ty + 1][tx + 1] = hv.R[0];
+                    sm.H[hs][k][1][ty + 1][tx + 1] = hv.L[0];
+                    sm.H[hs][k][2][ty + 1][tx + 1] = hv.R[1];
+                    sm.H[hs][k][3][ty + 1][tx + 1] = hv.L[1];
+                }
+                if (hx >= 0) {
+                    V4<float> h = sm.U[slot][k][hy][hx];
+                    if (zneg) h.w = -h.w;
+                    if (hneg == 1) h.y = -h.y;
+                    else if (hneg == 2) h.z = -h.z;
+                    Halves hv;
+                    cell_halves(h, hv);
+                    sm.H[hs][k][hk][hy][hx] = hk == 0 ? hv.R[0] : hk == 1 ? hv.L[0] : hk == 2 ? hv.R[1] : hv.L[1];
+                }
+                if (act && q >= 2) {
+                    // update plane c = q - 1 (z = z0 + q - 2) of group g0 + k
+                    const float4 l = sm.H[cs][k][0][ty + 1][tx];        // Rx of the left cell
+                    const float4 r = sm.H[cs][k][1][ty + 1][tx + 2];    // Lx of the right cell
+                    const float4 d = sm.H[cs][k][2][ty][tx + 1];        // Ry of the cell below
+                    const float4 p = sm.H[cs][k][3][ty + 2][tx + 1];    // Ly of the cell above
+                    const float4 Rzp = Rz_prev[k];
+                    const float2 slo = __fadd2_rn(__fadd2_rn(__fadd2_rn(lo2(l), lo2(r)), __fadd2_rn(lo2(d), lo2(p))),
+                                                  __fadd2_rn(lo2(Rzp), lo2(Lz_n)));
+                    const float2 shi = __fadd2_rn(__fadd2_rn(__fadd2_rn(hi2(l), hi2(r)), __fadd2_rn(hi2(d), hi2(p))),
+                                                  __fadd2_rn(hi2(Rzp), hi2(Lz_n)));
+                    const float2 cc0 = make_float2(c0, c0), cc1 = make_float2(c1, c1);
+                    const float2 olo = __ffma2_rn(cc0, make_float2(uc[k].x, uc[k].y), __fmul2_rn(cc1, slo));
+                    const float2 ohi = __ffma2_rn(cc0, make_float2(uc[k].z, uc[k].w), __fmul2_rn(cc1, shi));
+                    st4(out + k * gst, V4<float>{olo.x, olo.y, ohi.x, ohi.y});
+                }
+                Rz_prev[k] = Rz_c[k];
+                Rz_c[k] = Rz_n;
+                uc[k] = un;
+            }
+            if (act && q >= 2) out += sxy;
+            slot = slot + 1 == S ? 0 : slot + 1;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------- FP32 HLL transport
 // Both signal speeds of a state along one axis from the paired table: entry
 // (i, j), j < NM, holds the pairs (lambda_min, lambda_max) at mu_j and
@@ -2158,7 +2363,7 @@ __device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf
 template <int G, typename TU, typename TN, bool STRICT>
 __global__ void __launch_bounds__(RTD_CHEM_BLOCK)
 k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ctl *ctl,
-       DiagBuf db)
+       DiagBuf db, int grab)
 {
     const int lane = threadIdx.x & 31;
     const RateCoef *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
@@ -2175,13 +2380,19 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
     };
     __shared__ __align__(16) Row rows[STAGE ? RTD_CHEM_BLOCK / 32 : 1][STAGE ? 2 : 1];
     Row *wrow = rows[STAGE ? (threadIdx.x >> 5) : 0];
-    // items are handed out one at a time from a counter, so warps that draw
-    // cheap cells (cold gas) take more of them; the order of the work does
-    // not enter any result
+    // items are handed out `grab` at a time from a counter, so warps that
+    // draw cheap cells (cold gas) take more of them; the order of the work
+    // does not enter any result
+    unsigned long long knext = 0;
+    int kleft = 0;
     for (;;) {
-        unsigned long long k = 0;
-        if (lane == 0) k = atomicAdd(&ctl->chem_next, 1ull);
-        k = __shfl_sync(0xffffffffu, k, 0);
+        if (kleft == 0) {
+            if (lane == 0) knext = atomicAdd(&ctl->chem_next, (unsigned long long)grab);
+            knext = __shfl_sync(0xffffffffu, knext, 0);
+            kleft = grab;
+        }
+        const unsigned long long k = knext++;
+        kleft--;
         if (k >= (unsigned long long)nitems) break;
         const int64_t it = (int64_t)k;
         const int b = find_box(boxes, nboxes, it, true);

@@ -66,7 +66,7 @@ def _bad(**kw):
                                 dict(c_red=-1.0), dict(nsub=-1), dict(precision=7),
                                 dict(bc=(0, 1, 0, 0, 0, 0)), dict(bc=(3, 3, 0, 0, 0, 0)),
                                 dict(rates_const=True, isothermal=False),
-                                dict(max_halvings=-1)])
+                                dict(max_halvings=-1), dict(chem_tune=-1), dict(chem_tune=8)])
 def test_create_rejects_bad_params(kw):
     assert _bad(**kw) == B.RT_ERR_ARG
     assert B.rt_last_error(None)

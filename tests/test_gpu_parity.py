@@ -214,7 +214,7 @@ def test_transport_launch_shapes_are_bitwise_equal(shape, bc, flux):
             assert e.code == B.RT_ERR_ARG and k >= 3, (k, e)
             break
         shapes.add((stats.tile_x, stats.tile_y, stats.transport_grid, stats.transport_zchunk,
-                    stats.transport_lockstep, stats.transport_tma))
+                    stats.transport_lockstep, stats.transport_tma, stats.transport_gpb))
         for a, b in zip(out[:3], ref[:3]):
             np.testing.assert_array_equal(a, b)
         k += 1
@@ -222,9 +222,10 @@ def test_transport_launch_shapes_are_bitwise_equal(shape, bc, flux):
     assert len({s[3] for s in shapes}) >= 2              # whole columns and z-chunks
     (out,), stats = run_gpu(w, 3, "split", None, st, tune=1, flux=flux)
     assert (stats.tile_x, stats.tile_y, stats.transport_grid, stats.transport_zchunk,
-            stats.transport_lockstep, stats.transport_tma) in shapes
-    if flux == 0:                                        # GLF: lockstep rows and TMA were run
+            stats.transport_lockstep, stats.transport_tma, stats.transport_gpb) in shapes
+    if flux == 0:       # GLF: lockstep rows, TMA and two groups per block (3 = 2 + 1) were run
         assert any(s[4] > 0 for s in shapes) and any(s[5] for s in shapes)
+        assert any(s[6] == 2 for s in shapes) and any(s[6] == 2 and s[4] > 0 for s in shapes)
     for a, b in zip(out[:3], ref[:3]):
         np.testing.assert_array_equal(a, b)
 
@@ -244,14 +245,38 @@ def test_tuned_full_step_matches_default():
     assert st64.transport_tma == 0
 
 
+@pytest.mark.parametrize("prec", ["split", "fp64"])
+def test_chemistry_launch_shapes_are_bitwise_equal(prec):
+    """Every chemistry launch shape (rt_params.chem_tune = 2 + k: 1 or 2
+    resident blocks per SM x 1, 2 or 4 work items per draw) gives the same
+    bits, state and diagnostics history, as the default on uneven boxes with
+    sources; the tuner (chem_tune = 1) picks one of them and reports it."""
+    w = I.ensemble(nboxes=5, steps=6, sides=(8, 12, 16, 20), seed=11)
+    ref, st0 = run_gpu(w, 6, prec)
+    assert st0.chem_grab == 1
+    seen = set()
+    for k in range(6):
+        out, st = run_gpu(w, 6, prec, chem_tune=2 + k)
+        seen.add((st.chem_grid, st.chem_grab))
+        for b in range(len(w.boxes)):
+            for x, y in zip(out[b][:4], ref[b][:4]):
+                np.testing.assert_array_equal(x, y)
+    assert {g for _, g in seen} == {1, 2, 4}
+    out, st = run_gpu(w, 6, prec, chem_tune=1)
+    assert (st.chem_grid, st.chem_grab) in seen
+    for b in range(len(w.boxes)):
+        for x, y in zip(out[b][:4], ref[b][:4]):
+            np.testing.assert_array_equal(x, y)
+
+
 def test_ensemble_launch_shapes_are_bitwise_equal():
     """Uneven boxes in one launch: every transport launch shape, the
-    column-aligned grids and the z-chunked orders included (their runs then
-    straddle boxes of other depths), gives the same bits, state and history,
-    as the default."""
+    column-aligned grids, the z-chunked orders and two groups per block
+    included (their runs then straddle boxes of other depths), gives the same
+    bits, state and history, as the default."""
     w = I.ensemble(nboxes=5, steps=6, sides=(8, 12, 16, 20), seed=11)
     ref, _ = run_gpu(w, 6, "split")
-    for k in (0, 5, 7, 9, 12, 14, 15, 18, 19, 23, 26, 27, 31):
+    for k in (0, 5, 7, 9, 12, 14, 15, 18, 19, 23, 26, 27, 31, 33, 35, 36):
         out, _ = run_gpu(w, 6, "split", tune=2 + k)
         for b in range(5):
             for x, y in zip(out[b][:4], ref[b][:4]):

@@ -274,6 +274,7 @@ def time_device(w, precision, K, W, nsteps, ws, profile):
     launch = {"transport_tile": [st.tile_x, st.tile_y], "transport_grid": st.transport_grid,
               "transport_zchunk": st.transport_zchunk, "transport_tma": bool(st.transport_tma),
               "transport_lockstep": st.transport_lockstep,
+              "transport_gpb": st.transport_gpb,
               "chemistry_grid": st.chem_grid, "chemistry_grab": st.chem_grab,
               "tuned": bool(r.p.tune), "chemistry_tuned": bool(r.p.chem_tune)}
     r.close()
@@ -394,7 +395,12 @@ def reion256_run(B, ws, K=3, nsteps=20):
             "ms_per_run": sec * 1e3 / K,
             "transport_ms_per_launch": t_ms, "transport_gbs": gbs,
             "transport_frac": gbs / hbm,
-            "transport_traffic": profiled_traffic().get("transport_256"),
+            "transport_traffic": profiled_traffic().get(
+                "transport_256_lockstep" if st.transport_lockstep else "transport_256_columns"),
+            "launch": {"transport_tile": [st.tile_x, st.tile_y], "transport_grid": st.transport_grid,
+                       "transport_zchunk": st.transport_zchunk, "transport_lockstep": st.transport_lockstep,
+                       "transport_tma": bool(st.transport_tma), "transport_gpb": st.transport_gpb,
+                       "chemistry_grid": st.chem_grid, "chemistry_grab": st.chem_grab},
             "chemistry_ms_per_launch": c_ms,
             "peak_note": "of measured" if pk else "of fallback"}
 

@@ -78,14 +78,24 @@ static double eval_coef(const rtd::RateCoef &c, double t, float t32)
     return std::fma(std::fma(std::fma((double)q, t, c.c2), t, c.c1), t, c.c0);
 }
 
+// the kernel's FP32 evaluation of alpha_B from an interval's entries a[0..2]
+static float eval_aB32(const rtd::RateCoef *a, float t32)
+{
+    const float q = std::fmaf(std::fmaf(a[1].c5, t32, a[1].c4), t32, a[1].c3);
+    return std::fmaf(std::fmaf(std::fmaf(q, t32, a[2].b32), t32, a[1].b32), t32, a[0].b32);
+}
+
 // fills out[RTD_TAB_NINT][RTD_TAB_NF]; returns true when the table, evaluated
 // the kernel's way, reproduces the long-double fits to 2e-13 (relative for
 // functions 0-2, absolute for the logarithms 3-4) at 17 points per interval
 // (the FP32 tail's rounding reaches 1.1e-13 on one interval, alpha_A near
 // 7e7 K; elsewhere the error is ~3e-14),
-// when both exp(-c/T) factors are exactly zero in double below
-// RTD_TAB_TCUT, and when the terms they make are below 2^-60 of what they
-// enter below RTD_TAB_TWARM at n0 dtau <= RTD_TAB_NDMAX
+// when alpha_B's FP32 copy (the b32 fields with entry 1's FP32 tail)
+// reproduces it to 1e-6 relative at the same points (FP32 Horner of a degree-5
+// polynomial in |t| <= 1: a few ulp of float), when both exp(-c/T) factors
+// are exactly zero in double below RTD_TAB_TCUT, and when the terms they make
+// are below 2^-60 of what they enter below RTD_TAB_TWARM at n0 dtau <=
+// RTD_TAB_NDMAX
 bool build_rate_table(bool ots, rtd::RateCoef *out)
 {
     const int N = RTD_TAB_NC;
@@ -100,6 +110,7 @@ bool build_rate_table(bool ots, rtd::RateCoef *out)
     for (int j = 0; j < RTD_TAB_NINT; j++) {
         const LD lo = ldexpl(1.0L + (LD)(j % per) / per, RTD_TAB_E0 + j / per);
         const LD hi = ldexpl(1.0L + (LD)(j % per + 1) / per, RTD_TAB_E0 + j / per);
+        LD aBm[3] = {0, 0, 0};                        // alpha_B's c0 .. c2
         for (int f = 0; f < RTD_TAB_NF; f++) {
             LD fv[RTD_TAB_NC], c[RTD_TAB_NC];
             for (int m = 0; m < N; m++) {
@@ -125,7 +136,9 @@ bool build_rate_table(bool ots, rtd::RateCoef *out)
             o.c3 = (float)mt[3];
             o.c4 = (float)mt[4];
             o.c5 = (float)mt[5];
-            o.pad = 0.0f;
+            o.b32 = 0.0f;
+            if (f == 1)
+                for (int i = 0; i < 3; i++) aBm[i] = mt[i];
             for (int k = 0; k <= 16; k++) {           // check, the kernel's way
                 const double t = -1.0 + k / 8.0;
                 const LD ex = fit(f, lo + ((LD)t + 1) * 0.5L * (hi - lo), ots);
@@ -133,6 +146,13 @@ bool build_rate_table(bool ots, rtd::RateCoef *out)
                 const LD err = f <= 2 ? fabsl((p - ex) / ex) : fabsl(p - ex);
                 if (!(err <= 2e-13L)) return false;
             }
+        }
+        rtd::RateCoef *a = out + (size_t)j * RTD_TAB_NF;
+        for (int i = 0; i < 3; i++) a[i].b32 = (float)aBm[i];
+        for (int k = 0; k <= 16; k++) {
+            const double t = -1.0 + k / 8.0;
+            const LD ex = fit(1, lo + ((LD)t + 1) * 0.5L * (hi - lo), ots);
+            if (!(fabsl(((LD)eval_aB32(a, (float)t) - ex) / ex) <= 1e-6L)) return false;
         }
     }
     // the factors the kernel skips below RTD_TAB_TCUT (both grow with T)

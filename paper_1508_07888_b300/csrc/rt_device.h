@@ -63,7 +63,9 @@ namespace rtd {
 // coefficients of one tabulated polynomial (one function on one interval)
 struct RateCoef {
     double c0, c1, c2;
-    float c3, c4, c5, pad;
+    float c3, c4, c5;
+    float b32;      // entries 0, 1, 2 of an interval: c0, c1, c2 of alpha_B's polynomial in
+                    // FP32 (with entry 1's c3 .. c5, alpha_B wholly in FP32); 0 in entries 3, 4
 };
 
 // physical constants (cgs)

@@ -1755,6 +1755,7 @@ struct Rates {
     double kR;             // cooling per n_e n_HII: recombination + bremsstrahlung
     double kC;             // cooling per n_e n_HI: collisional ionisation + excitation
     bool cold;             // beta = kC = 0 (tabulated rates below the cut of rates_tab)
+    float aB32;            // alpha_B in FP32 (the split form's recombination photons)
 };
 
 __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
@@ -1764,6 +1765,7 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
     if (ph.rates_const) {
         r.aA = ph.alphaA; r.aB = ph.alphaB; r.beta = ph.beta;
         r.kR = 0.0; r.kC = 0.0;
+        r.aB32 = d2f(r.aB);
         return r;
     }
     const double l = 2.0 * rtd::T_HI / T;
@@ -1786,6 +1788,7 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
     const double cce = 7.5e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1.0e5));
     r.kR = crec + cff;
     r.kC = cci + cce;
+    r.aB32 = d2f(r.aB);
     return r;
 }
 
@@ -1826,7 +1829,7 @@ __device__ __forceinline__ double tab_eval(const RateCoef *c, double t, float t3
 // two factors' terms are below 2^-60 of what they enter), else RTD_TAB_TCUT
 template <bool STRICT>
 __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, double T,
-                                           bool warm = false)
+                                           bool warm = false, bool b32 = false)
 {
     int j;
     double t;
@@ -1835,7 +1838,16 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, 
     const RateCoef *a = tab + (size_t)j * RTD_TAB_NF;
     Rates r;
     r.cold = false;
-    r.aB = tab_eval(a + 1, t, t32);
+    if (b32) {
+        // alpha_B only for the FP32 recombination photons (no OTS): its
+        // polynomial in FP32, the FP64 value not formed
+        const float q = fmaf(fmaf(__ldg(&a[1].c5), t32, __ldg(&a[1].c4)), t32, __ldg(&a[1].c3));
+        r.aB32 = fmaf(fmaf(fmaf(q, t32, __ldg(&a[2].b32)), t32, __ldg(&a[1].b32)), t32, __ldg(&a[0].b32));
+        r.aB = 0.0;
+    } else {
+        r.aB = tab_eval(a + 1, t, t32);
+        r.aB32 = 0.0f;
+    }
     r.aA = ph.ots ? r.aB : tab_eval(a, t, t32);
     r.kR = tab_eval(a + 2, t, t32);
     if (dbits(T) >= (warm ? dbits(RTD_TAB_TWARM) : dbits(RTD_TAB_TCUT))) {   // T >= cut (both positive)
@@ -2068,7 +2080,8 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
     }
     double rem = span;                          // span - tau, tau = 0 in the first sub-cycle
     for (;;) {
-        const Rates r = tab ? rates_tab<STRICT>(ph, tab, s.T, !STRICT && warm_cut) : rates_at(ph, s.T);
+        const Rates r = tab ? rates_tab<STRICT>(ph, tab, s.T, !STRICT && warm_cut, N32 && !ph.ots)
+                            : rates_at(ph, s.T);
         const double alpha = ph.ots ? r.aB : r.aA;
         double dtau = rem;
         bool last = true;
@@ -2134,7 +2147,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         float rec32 = 0.0f;
         if (N32 && !ph.ots) {
             const float x32 = d2f(1.0 - s.xHI);
-            rec32 = (d2f(r.aA) - d2f(r.aB)) * (x32 * x32) * k.K32;
+            rec32 = (d2f(r.aA) - r.aB32) * (x32 * x32) * k.K32;
         }
         for (int h = 0;; h++) {
             if (STRICT) {

@@ -1754,14 +1754,12 @@ struct Rates {
     double aA, aB, beta;   // cm^3/s
     double kR;             // cooling per n_e n_HII: recombination + bremsstrahlung
     double kC;             // cooling per n_e n_HI: collisional ionisation + excitation
-    bool cold;             // beta = kC = 0 (tabulated rates below the cut of rates_tab)
     float aB32;            // alpha_B in FP32 (the split form's recombination photons)
 };
 
 __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
 {
     Rates r;
-    r.cold = false;
     if (ph.rates_const) {
         r.aA = ph.alphaA; r.aB = ph.alphaB; r.beta = ph.beta;
         r.kR = 0.0; r.kC = 0.0;
@@ -1837,7 +1835,6 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, 
     if (!tab_pos(T, j, t, t32)) return rates_at(ph, T);
     const RateCoef *a = tab + (size_t)j * RTD_TAB_NF;
     Rates r;
-    r.cold = false;
     if (b32) {
         // alpha_B only for the FP32 recombination photons (no OTS): its
         // polynomial in FP32, the FP64 value not formed
@@ -1858,7 +1855,6 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, 
     } else {
         r.beta = 0.0;
         r.kC = 0.0;
-        r.cold = true;
     }
     return r;
 }
@@ -1967,18 +1963,18 @@ struct CellK {
 // heating and cooling sums stay FP64
 // rec32 (N32 only): the recombination photons of group 1 per unit time in
 // FP32, (alpha_A - alpha_B) x^2 n0^2 / nunit, formed once per sub-cycle (it
-// depends on the sub-cycle's start state only)
+// depends on the sub-cycle's start state only); xh32: x_HI in FP32
 template <int G, bool DEFER, bool N32, typename FT>
 __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B, const CellK<G> &k,
                                                 double n0, const double *S, const Rates &r,
                                                 double alpha, const Cell<G> &s, double e0,
                                                 double dtau, Cell<G> &o, double &e1, FT *rdo,
-                                                float rec32)
+                                                float rec32, float xh32)
 {
     const double x = 1.0 - s.xHI;
     if constexpr (N32) {
         const float dt32 = d2f(dtau);
-        const float q32 = (d2f(s.xHI) * k.n0f) * dt32;
+        const float q32 = (xh32 * k.n0f) * dt32;
 #pragma unroll
         for (int i = 0; i < G; i++) {
             const float rd = __frcp_rn(fmaf(ph.csig_f[i], q32, 1.0f));
@@ -2008,9 +2004,10 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
 #pragma unroll
     for (int i = 1; i < G; i++) gam = fma(B.gN[i], o.N[i], gam);
     const double xnum = fma(alpha * x * x, n0 * dtau, s.xHI);
-    // cold gas: beta = 0 exactly, the collisional term is skipped (warps of
-    // cold cells take this branch together)
-    const double xden = r.cold ? fma(dtau, gam, 1.0) : fma(dtau, fma(r.beta * x, n0, gam), 1.0);
+    // one formula for every cell: in cold gas beta = kC = 0 exactly and the
+    // collisional terms add exact zeros (a per-cell choice of the shorter
+    // form ran both forms in every warp)
+    const double xden = fma(dtau, fma(r.beta * x, n0, gam), 1.0);
     o.xHI = xnum * rcp_nr(xden);
     if (ph.isothermal) {
         o.T = s.T;
@@ -2021,8 +2018,8 @@ __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B,
 #pragma unroll
     for (int i = 1; i < G; i++) hs = fma(B.hN[i], o.N[i], hs);
     const double x1 = 1.0 - o.xHI;
-    // Lambda(n0, x^{p+1}, T^p); kC = 0 exactly in cold gas
-    const double cool = r.cold ? k.n02 * x1 * (x1 * r.kR) : k.n02 * x1 * fma(x1, r.kR, o.xHI * r.kC);
+    // Lambda(n0, x^{p+1}, T^p)
+    const double cool = k.n02 * x1 * fma(x1, r.kR, o.xHI * r.kC);
     e1 = fma(dtau, fma(o.xHI * n0, hs, -cool), e0);
     o.T = e1 * rcp_nr(fma(-k.cvn, o.xHI, k.cvn2));    // (3/2) kB n0 (2 - x_HI)
 }
@@ -2049,11 +2046,16 @@ __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
 
 // warm_cut (fast forms): n0 dtau <= RTD_TAB_NDMAX for every dtau of the span,
 // so the rates may take the RTD_TAB_TWARM cut
+// in32 (FP32 photon update only, required there): the caller's FP32 copies,
+// in32[0] = n0 and in32[1 + i] = S_i, with s.n32 holding N in FP32 and s.N
+// its exact double.  Every float <-> double conversion costs FP64-pipe
+// issue slots (its rare-case instruction is issued, predicated, with the
+// warp), so values that arrive in FP32 are not converted back and forth.
 template <int G, bool STRICT, class Trace = NoTrace, typename FT = double>
 __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,
                                   int &ncyc, Trace *tr = nullptr, FT *fac = nullptr,
-                                  bool warm_cut = false)
+                                  bool warm_cut = false, const float *in32 = nullptr)
 {
     constexpr bool DEFER = !STRICT && std::is_same<Trace, NoTrace>::value;
     constexpr bool N32 = DEFER && std::is_same<FT, float>::value;
@@ -2066,17 +2068,13 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         k.cvn = (1.5 * rtd::KB) * n0;
         k.cvn2 = 2.0 * k.cvn;
     }
-    if (!STRICT) {
-        k.n0f = d2f(n0);
+    if constexpr (N32) {
+        k.n0f = in32[0];
         k.K32 = d2f(k.K);
-    }
-    if (N32) {
 #pragma unroll
-        for (int i = 0; i < G; i++) {
-            k.S32[i] = d2f(S[i]);
-            s.n32[i] = d2f(s.N[i]);
-            s.N[i] = f2d(s.n32[i]);
-        }
+        for (int i = 0; i < G; i++) k.S32[i] = in32[1 + i];
+    } else if (!STRICT) {
+        k.n0f = d2f(n0);
     }
     double rem = span;                          // span - tau, tau = 0 in the first sub-cycle
     for (;;) {
@@ -2087,6 +2085,10 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         bool last = true;
         // e^p (the fast forms reuse it in every trial of this sub-cycle)
         const double ep0 = STRICT ? 0.0 : fma(-k.cvn, s.xHI, k.cvn2) * s.T;
+        // x_HI and 1 - x_HI in FP32, once per sub-cycle (the pre-test, the
+        // FP32 photon update and the recombination photons)
+        const float xh32 = STRICT ? 0.0f : d2f(s.xHI);
+        const float xl32 = STRICT ? 0.0f : d2f(1.0 - s.xHI);
         // FP32 pre-test of the estimate's skip (fast forms).  heat and
         // cooling are >= 0, so |rate| <= heat + cool, and q = rem (heat +
         // cool) / e is a sum of products of non-negative FP32 numbers in which
@@ -2097,10 +2099,10 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         // and the results, are those of the FP64 test
         bool pre_skip = false;
         if (!STRICT && !ph.isothermal && use_est) {
-            const float xh = fabsf(d2f(s.xHI)), xl = fabsf(d2f(1.0 - s.xHI));
+            const float xh = fabsf(xh32), xl = fabsf(xl32);
             float hsum = 0.0f;
 #pragma unroll
-            for (int i = 0; i < G; i++) hsum = fmaf(ph.hK[i], fabsf(d2f(s.N[i])), hsum);
+            for (int i = 0; i < G; i++) hsum = fmaf(ph.hK[i], fabsf(N32 ? s.n32[i] : d2f(s.N[i])), hsum);
             constexpr float KB15I = (float)(1.0 / (1.5 * rtd::KB));
             const float kr = fabsf(d2f(r.kR)) * KB15I, kc = fabsf(d2f(r.kC)) * KB15I;
             const float cool = (k.n0f * xl) * fmaf(xl, kr, xh * kc);
@@ -2145,17 +2147,14 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         double ep, e1;
         FT rd[G];
         float rec32 = 0.0f;
-        if (N32 && !ph.ots) {
-            const float x32 = d2f(1.0 - s.xHI);
-            rec32 = (d2f(r.aA) - r.aB32) * (x32 * x32) * k.K32;
-        }
+        if (N32 && !ph.ots) rec32 = (d2f(r.aA) - r.aB32) * (xl32 * xl32) * k.K32;
         for (int h = 0;; h++) {
             if (STRICT) {
                 chem_trial<G, true>(ph, B.nunit, B.inv_nunit, n0, S, r, alpha, s, dtau, o, ep, e1);
             } else {
                 ep = ep0;
                 chem_trial_fast<G, DEFER, N32, FT>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd,
-                                                   rec32);
+                                                   rec32, xh32);
             }
             if (ph.isothermal) break;
             const bool finite = STRICT ? isfinite(e1) : finite_bits(e1);
@@ -2237,6 +2236,20 @@ __device__ __forceinline__ void cosmo_out(double a, double a1, Cell<G> &s)
         }
     }
     s.T = s.T * (a * a);
+}
+
+// FP32 copies of the rescaled n0, S and N for the FP32 photon update (N
+// rounded to FP32, s.N its exact double), after cosmo_in
+template <int G>
+__device__ __forceinline__ void cosmo_32(Cell<G> &s, const double *S, double n0, float *in32)
+{
+    in32[0] = d2f(n0);
+#pragma unroll
+    for (int i = 0; i < G; i++) {
+        in32[1 + i] = d2f(S[i]);
+        s.n32[i] = d2f(s.N[i]);
+        s.N[i] = f2d(s.n32[i]);
+    }
 }
 
 // Diagnostics of a set of cells: two FP64 sums (ionised fraction, photons),
@@ -2439,6 +2452,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             }
             item_src = lo < B.nsrc && B.src_cell[lo] < c0 + RTD_CHEM_LANE_CELLS * RTD_CHEM_ITEM;
         }
+        unsigned fmb = 0u;                               // FP32 state: max |F|/N, float bits
         // the item's cells: RTD_CHEM_LANE_CELLS rows of 32, one cell of each
         // per lane, in order (the lane's diagnostics summed in that order)
         for (int hrow = 0; hrow < RTD_CHEM_LANE_CELLS; hrow++) {
@@ -2459,11 +2473,17 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             // the split form)
             using FT = typename std::conditional<!STRICT && std::is_same<TU, float>::value, float,
                                                  double>::type;
+            // FP32 photon update (split form): N, n0 and the source terms go
+            // to the chemistry in FP32 as they were read, beside their exact
+            // doubles (no conversion back)
+            constexpr bool N32 = std::is_same<FT, float>::value;
+            float in32[1 + G];
             FT fac[G];
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 const V4<TU> u = STAGE ? rw.U[i][lane] : ld4(Us + (int64_t)i * B.ncell + c);
                 s.N[i] = to_d(u.x);
+                if constexpr (N32) s.n32[i] = u.x;
                 fac[i] = FT(1);
                 if (STRICT) {
                     s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
@@ -2484,19 +2504,27 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             s.xHI = STAGE ? rw.xHI[lane] : B.xHI[c];
             s.T = STAGE ? rw.T[lane] : B.T[c];
             const double n0 = STAGE ? to_d(rw.n0[lane]) : ldn(reinterpret_cast<const TN *>(B.n0), c);
+            if constexpr (N32) in32[0] = STAGE ? (float)rw.n0[lane] : d2f(n0);
             // source term of this cell: sorted unique cells, binary search
             double S[G];
 #pragma unroll
-            for (int i = 0; i < G; i++) S[i] = 0.0;
+            for (int i = 0; i < G; i++) {
+                S[i] = 0.0;
+                in32[1 + i] = 0.0f;
+            }
             if (item_src) {
                 int lo = 0, hi = B.nsrc - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (B.src_cell[mid] < c) lo = mid + 1; else hi = mid;
                 }
-                if (B.src_cell[lo] == c)
+                if (B.src_cell[lo] == c) {
 #pragma unroll
-                    for (int i = 0; i < G; i++) S[i] = B.src_S[(int64_t)lo * G + i];
+                    for (int i = 0; i < G; i++) {
+                        S[i] = B.src_S[(int64_t)lo * G + i];
+                        if constexpr (N32) in32[1 + i] = d2f(S[i]);
+                    }
+                }
             }
             int ncyc = 0;
             unsigned int err = 0;
@@ -2508,18 +2536,19 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 ca = ph.acos[ctl->step];
                 ca1 = ph.acos[ctl->step + 1];
                 cosmo_in<G, STRICT>(ca, s, S, n0c, span, B.dt);
+                if constexpr (N32) cosmo_32<G>(s, S, n0c, in32);
             }
             // the warm cut holds for every sub-cycle when n0 times the whole
             // step is within its bound (in FP32; an overflow to Inf fails)
-            const bool warm_cut = !STRICT && d2f(n0c) * d2f(span) <= RTD_TAB_NDMAX;
+            const bool warm_cut = !STRICT && (N32 ? in32[0] : d2f(n0c)) * d2f(span) <= RTD_TAB_NDMAX;
             if (ph.nsub > 0) {
                 const double h = span / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
                     err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
-                                                             warm_cut);
+                                                             warm_cut, in32);
             } else {
                 err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
-                                                         warm_cut);
+                                                         warm_cut, in32);
             }
             if (ph.cosmo) {
                 cosmo_out<G, STRICT>(ca, ca1, s);
@@ -2527,6 +2556,13 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                     const FT fr = from_d<FT>(ca / ca1);
 #pragma unroll
                     for (int i = 0; i < G; i++) fac[i] = fac[i] * fr;
+                }
+                if constexpr (N32) {
+#pragma unroll
+                    for (int i = 0; i < G; i++) {       // the stored N, rounded once
+                        s.n32[i] = d2f(s.N[i]);
+                        s.N[i] = f2d(s.n32[i]);
+                    }
                 }
             }
             if (!finite_bits(s.xHI) || !finite_bits(s.T)) err |= RTD_ERR_NONFINITE;
@@ -2536,7 +2572,10 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 V4<TU> o;
-                o.x = from_d<TU>(s.N[i]);
+                // N: its FP32 value where the chemistry kept one (s.N is its
+                // exact double), else rounded from s.N
+                if constexpr (N32) o.x = s.n32[i];
+                else o.x = from_d<TU>(s.N[i]);
                 if (STRICT) {
                     o.y = from_d<TU>(s.F[i][0]); o.z = from_d<TU>(s.F[i][1]); o.w = from_d<TU>(s.F[i][2]);
                 } else {
@@ -2545,7 +2584,8 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                     o.y = u.y * fi; o.z = u.z * fi; o.w = u.w * fi;
                 }
                 st4(U + (int64_t)i * B.ncell + c, o);
-                ph_tot = i == 0 ? to_d(o.x) : ph_tot + to_d(o.x);
+                const double oxd = N32 ? s.N[i] : to_d(o.x);
+                ph_tot = i == 0 ? oxd : ph_tot + oxd;
                 if (o.x > flux_nmin<TU>()) {
                     const TU rn = TU(1) / o.x;
                     const TU ux = o.y * rn, uy = o.z * rn, uz = o.w * rn;
@@ -2558,7 +2598,16 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             DiagAcc vc;
             vc.X = 1.0 - s.xHI;
             vc.ph = ph_tot;
-            vc.fbits = (unsigned long long)__double_as_longlong(to_d(sqrt(f2max)));
+            // largest |F|/N: in FP32 state its float bits are kept over the
+            // item (non-negative floats order like their bits) and widened
+            // once per item
+            if constexpr (sizeof(TU) == 4) {
+                const unsigned fb = fbits(sqrt(f2max));
+                fmb = fb > fmb ? fb : fmb;
+                vc.fbits = 0ull;
+            } else {
+                vc.fbits = dbits(sqrt(f2max));
+            }
             // xHI < 0.5 on the integer pipe: doubles order like their bits
             // as signed integers (negative values below every positive one)
             vc.count = (long long)dbits(s.xHI) < (long long)dbits(0.5) ? 1ull : 0ull;
@@ -2567,6 +2616,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             else diag_add(v, vc);
         }
         }
+        if constexpr (sizeof(TU) == 4) v.fbits = dbits(f2d(ffrom(fmb)));
         // FP64 sums: each lane's values go to the item's fixed slots (summed
         // per group); the integer fields are reduced across the warp
         db.lane[it * (2 * RTD_CHEM_ITEM) + lane] = v.X;
@@ -2661,11 +2711,14 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         Cell<G> s;
         // the refined cell's radiation is not kept (fac only as in k_chem)
         using FT = typename std::conditional<!STRICT && std::is_same<TU, float>::value, float, double>::type;
+        constexpr bool N32 = std::is_same<FT, float>::value;   // FP32 photon update (split form)
+        float in32[1 + G];
         FT fac[G];
 #pragma unroll
         for (int i = 0; i < G; i++) {
             const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
             s.N[i] = to_d(u.x);
+            if constexpr (N32) s.n32[i] = u.x;
             fac[i] = FT(1);
             if (STRICT) {
                 s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
@@ -2674,32 +2727,46 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         s.xHI = F.xHI[f];
         s.T = F.T[f];
         const double n0 = ldn(reinterpret_cast<const TN *>(F.n0), f);
+        if constexpr (N32) {
+            if constexpr (std::is_same<TN, float>::value) in32[0] = reinterpret_cast<const float *>(F.n0)[f];
+            else in32[0] = d2f(n0);
+        }
         double S[G];
 #pragma unroll
-        for (int i = 0; i < G; i++) S[i] = 0.0;
+        for (int i = 0; i < G; i++) {
+            S[i] = 0.0;
+            in32[1 + i] = 0.0f;
+        }
         if (B.nsrc > 0) {
             int lo = 0, hi = B.nsrc - 1;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (B.src_cell[mid] < c) lo = mid + 1; else hi = mid;
             }
-            if (B.src_cell[lo] == c)
+            if (B.src_cell[lo] == c) {
 #pragma unroll
-                for (int i = 0; i < G; i++) S[i] = B.src_S[(int64_t)lo * G + i];
+                for (int i = 0; i < G; i++) {
+                    S[i] = B.src_S[(int64_t)lo * G + i];
+                    if constexpr (N32) in32[1 + i] = d2f(S[i]);
+                }
+            }
         }
         int ncyc = 0;
         unsigned int err = 0;
         double span = B.dt, n0c = n0;
-        if (ph.cosmo) cosmo_in<G, STRICT>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
-        const bool warm_cut = !STRICT && d2f(n0c) * d2f(span) <= RTD_TAB_NDMAX;
+        if (ph.cosmo) {
+            cosmo_in<G, STRICT>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
+            if constexpr (N32) cosmo_32<G>(s, S, n0c, in32);
+        }
+        const bool warm_cut = !STRICT && (N32 ? in32[0] : d2f(n0c)) * d2f(span) <= RTD_TAB_NDMAX;
         if (ph.nsub > 0) {
             const double h = span / ph.nsub;
             for (int q = 0; q < ph.nsub; q++)
                 err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
-                                                         warm_cut);
+                                                         warm_cut, in32);
         } else {
             err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
-                                                     warm_cut);
+                                                     warm_cut, in32);
         }
         if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
         if (!finite_bits(s.xHI) || !finite_bits(s.T)) err |= RTD_ERR_NONFINITE;

@@ -2120,9 +2120,10 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
                 rate = heat - cooling(r, n0, s.xHI);
                 e = eint(s.xHI, n0, s.T);
             } else {
-                double hs = B.hN[0] * s.N[0];
+                // N32: s.N is formed by the trials; here N from its FP32 copy
+                double hs = B.hN[0] * (N32 ? f2d(s.n32[0]) : s.N[0]);
 #pragma unroll
-                for (int i = 1; i < G; i++) hs = fma(B.hN[i], s.N[i], hs);
+                for (int i = 1; i < G; i++) hs = fma(B.hN[i], N32 ? f2d(s.n32[i]) : s.N[i], hs);
                 hs = hs * n0;
                 const double x = 1.0 - s.xHI;
                 rate = fma(s.xHI, hs, -(k.n02 * x * fma(x, r.kR, s.xHI * r.kC)));
@@ -2482,8 +2483,10 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
 #pragma unroll
             for (int i = 0; i < G; i++) {
                 const V4<TU> u = STAGE ? rw.U[i][lane] : ld4(Us + (int64_t)i * B.ncell + c);
-                s.N[i] = to_d(u.x);
+                // N32: s.N is first formed by the trials (or by the rescaling
+                // of supercomoving units)
                 if constexpr (N32) s.n32[i] = u.x;
+                else s.N[i] = to_d(u.x);
                 fac[i] = FT(1);
                 if (STRICT) {
                     s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
@@ -2535,6 +2538,10 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (ph.cosmo) {
                 ca = ph.acos[ctl->step];
                 ca1 = ph.acos[ctl->step + 1];
+                if constexpr (N32) {
+#pragma unroll
+                    for (int i = 0; i < G; i++) s.N[i] = f2d(s.n32[i]);
+                }
                 cosmo_in<G, STRICT>(ca, s, S, n0c, span, B.dt);
                 if constexpr (N32) cosmo_32<G>(s, S, n0c, in32);
             }
@@ -2717,8 +2724,8 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
 #pragma unroll
         for (int i = 0; i < G; i++) {
             const V4<TU> u = ld4(Us + (int64_t)i * B.ncell + c);
-            s.N[i] = to_d(u.x);
             if constexpr (N32) s.n32[i] = u.x;
+            else s.N[i] = to_d(u.x);
             fac[i] = FT(1);
             if (STRICT) {
                 s.F[i][0] = to_d(u.y); s.F[i][1] = to_d(u.z); s.F[i][2] = to_d(u.w);
@@ -2755,6 +2762,10 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
         unsigned int err = 0;
         double span = B.dt, n0c = n0;
         if (ph.cosmo) {
+            if constexpr (N32) {
+#pragma unroll
+                for (int i = 0; i < G; i++) s.N[i] = f2d(s.n32[i]);
+            }
             cosmo_in<G, STRICT>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
             if constexpr (N32) cosmo_32<G>(s, S, n0c, in32);
         }

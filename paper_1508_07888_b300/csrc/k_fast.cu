@@ -150,15 +150,27 @@ cudaError_t transport_fast(bool fp64, const Launch &L, int zc, const rtd::Phys &
     return cudaGetLastError();
 }
 
+// dynamic shared memory of the chemistry kernels (staged rows); the limit
+// is raised once per process and device at set-up (chem_occupancy_fast),
+// before any launch or capture
+template <int G, typename T>
+static void chem_attr()
+{
+    cudaFuncSetAttribute((const void *)rtk::k_chem<G, T, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rtk::chem_smem_bytes<G, T, T, false>());
+}
+
 template <int G>
 static void chem_g(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl, const rtd::DiagBuf &db)
 {
     if (fp64) {
         auto k = rtk::k_chem<G, double, double, false>;
-        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db, L.grab);
+        k<<<L.grid, RTD_CHEM_BLOCK, rtk::chem_smem_bytes<G, double, double, false>(), L.stream>>>(
+            L.boxes, L.nboxes, L.nitems, ph, ctl, db, L.grab);
     } else {
         auto k = rtk::k_chem<G, float, float, false>;
-        k<<<L.grid, RTD_CHEM_BLOCK, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, ctl, db, L.grab);
+        k<<<L.grid, RTD_CHEM_BLOCK, rtk::chem_smem_bytes<G, float, float, false>(), L.stream>>>(
+            L.boxes, L.nboxes, L.nitems, ph, ctl, db, L.grab);
     }
 }
 
@@ -276,8 +288,12 @@ cudaError_t fill_tune_state(void *U, int64_t n, cudaStream_t s)
 int chem_occupancy_fast(bool fp64, int G)
 {
 #define OCC_G(g)                                                                                \
-    (fp64 ? occ((const void *)rtk::k_chem<g, double, double, false>, RTD_CHEM_BLOCK, 0)          \
-          : occ((const void *)rtk::k_chem<g, float, float, false>, RTD_CHEM_BLOCK, 0))
+    (fp64 ? (chem_attr<g, double>(),                                                            \
+             occ((const void *)rtk::k_chem<g, double, double, false>, RTD_CHEM_BLOCK,           \
+                 rtk::chem_smem_bytes<g, double, double, false>()))                             \
+          : (chem_attr<g, float>(),                                                             \
+             occ((const void *)rtk::k_chem<g, float, float, false>, RTD_CHEM_BLOCK,             \
+                 rtk::chem_smem_bytes<g, float, float, false>())))
     switch (G) {
     case 1: return OCC_G(1);
     case 2: return OCC_G(2);

@@ -2378,6 +2378,21 @@ __device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf
     }
 }
 
+// Staged inputs of one row of 32 cells of a chemistry work item (the fast
+// forms): U* of every group, x_HI, T, n0; two rows per warp in dynamic
+// shared memory
+template <int G, typename TU, typename TN>
+struct ChemRow {
+    V4<TU> U[G][RTD_CHEM_ITEM];
+    double xHI[RTD_CHEM_ITEM], T[RTD_CHEM_ITEM];
+    TN n0[RTD_CHEM_ITEM];
+};
+template <int G, typename TU, typename TN, bool STRICT>
+constexpr size_t chem_smem_bytes()
+{
+    return STRICT ? 0 : sizeof(ChemRow<G, TU, TN>) * 2 * (RTD_CHEM_BLOCK / 32);
+}
+
 // One work item = RTD_CHEM_LANE_CELLS x RTD_CHEM_ITEM (4 x 32) consecutive
 // cells of one box and one warp, each lane taking one cell of every row of
 // 32 in turn; warps draw items independently (no block barrier).
@@ -2394,19 +2409,15 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
 {
     const int lane = threadIdx.x & 31;
     const RateCoef *tab = (ph.rtab && !ph.rates_const) ? ph.rtab : nullptr;
-    // split form: each row of 32 cells' inputs (U* of every group, x_HI, T,
+    // fast forms: each row of 32 cells' inputs (U* of every group, x_HI, T,
     // n0) is staged into the warp's shared-memory buffers by cp.async while
     // the lanes work on the previous row, so the DRAM latency of a cell's
     // loads is hidden without registers; a lane reads back only what it
     // copied itself
-    constexpr bool STAGE = !STRICT && sizeof(TU) == 4 && sizeof(TN) == 4;
-    struct Row {
-        V4<TU> U[G][RTD_CHEM_ITEM];
-        double xHI[RTD_CHEM_ITEM], T[RTD_CHEM_ITEM];
-        TN n0[RTD_CHEM_ITEM];
-    };
-    __shared__ __align__(16) Row rows[STAGE ? RTD_CHEM_BLOCK / 32 : 1][STAGE ? 2 : 1];
-    Row *wrow = rows[STAGE ? (threadIdx.x >> 5) : 0];
+    constexpr bool STAGE = !STRICT;
+    using Row = ChemRow<G, TU, TN>;
+    extern __shared__ __align__(16) unsigned char chem_smem_raw[];
+    Row *wrow = reinterpret_cast<Row *>(chem_smem_raw) + (STAGE ? 2 * (threadIdx.x >> 5) : 0);
     // items are handed out `grab` at a time from a counter, so warps that
     // draw cheap cells (cold gas) take more of them; the order of the work
     // does not enter any result
@@ -2433,10 +2444,11 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (hr < RTD_CHEM_LANE_CELLS && cs < B.ncell) {
                 Row &r = wrow[hr & 1];
 #pragma unroll
-                for (int i = 0; i < G; i++) cp_async16(&r.U[i][lane], Us + (int64_t)i * B.ncell + cs);
+                for (int i = 0; i < G; i++) cp_cell(&r.U[i][lane], Us + (int64_t)i * B.ncell + cs);
                 cp_async8(&r.xHI[lane], B.xHI + cs);
                 cp_async8(&r.T[lane], B.T + cs);
-                cp_async4(&r.n0[lane], reinterpret_cast<const TN *>(B.n0) + cs);
+                if constexpr (sizeof(TN) == 4) cp_async4(&r.n0[lane], reinterpret_cast<const TN *>(B.n0) + cs);
+                else cp_async8(&r.n0[lane], reinterpret_cast<const TN *>(B.n0) + cs);
             }
             cp_async_commit();
         };

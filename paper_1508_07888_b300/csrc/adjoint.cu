@@ -282,9 +282,11 @@ k_chem_adj(const BoxDev *__restrict__ boxes, Phys ph, const double *__restrict__
             if (ph.nsub > 0) {
                 const double h = B.dt / ph.nsub;
                 for (int k = 0; k < ph.nsub; k++)
-                    chem_span<G, false, TraceBuf<G>>(ph, tab, B, n0, S, w, h, false, ncyc, &tr);
+                    chem_span<G, false, TraceBuf<G>, double>(ph, tab, B, n0, S, w, h, false, ncyc, &tr, nullptr, false,
+                                                   nullptr, d2f(h));
             } else {
-                chem_span<G, false, TraceBuf<G>>(ph, tab, B, n0, S, w, B.dt, true, ncyc, &tr);
+                chem_span<G, false, TraceBuf<G>, double>(ph, tab, B, n0, S, w, B.dt, true, ncyc, &tr, nullptr, false,
+                                               nullptr, d2f(B.dt));
             }
         };
         replay(0);

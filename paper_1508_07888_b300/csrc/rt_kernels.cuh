@@ -1755,6 +1755,7 @@ struct Rates {
     double kR;             // cooling per n_e n_HII: recombination + bremsstrahlung
     double kC;             // cooling per n_e n_HI: collisional ionisation + excitation
     float aB32;            // alpha_B in FP32 (the split form's recombination photons)
+    float kC32;            // kC in FP32 (the fast forms' pre-test), formed where kC is
 };
 
 __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
@@ -1764,6 +1765,7 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
         r.aA = ph.alphaA; r.aB = ph.alphaB; r.beta = ph.beta;
         r.kR = 0.0; r.kC = 0.0;
         r.aB32 = d2f(r.aB);
+        r.kC32 = 0.0f;
         return r;
     }
     const double l = 2.0 * rtd::T_HI / T;
@@ -1786,6 +1788,7 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
     const double cce = 7.5e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1.0e5));
     r.kR = crec + cff;
     r.kC = cci + cce;
+    r.kC32 = d2f(r.kC);
     r.aB32 = d2f(r.aB);
     return r;
 }
@@ -1852,9 +1855,11 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, 
         r.beta = exp(tab_eval(a + 3, t, t32) - rtd::T_HI * invT);
         const double cce = exp(tab_eval(a + 4, t, t32) - 118348.0 * invT);
         r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
+        r.kC32 = d2f(r.kC);
     } else {
         r.beta = 0.0;
         r.kC = 0.0;
+        r.kC32 = 0.0f;
     }
     return r;
 }
@@ -1963,17 +1968,17 @@ struct CellK {
 // heating and cooling sums stay FP64
 // rec32 (N32 only): the recombination photons of group 1 per unit time in
 // FP32, (alpha_A - alpha_B) x^2 n0^2 / nunit, formed once per sub-cycle (it
-// depends on the sub-cycle's start state only); xh32: x_HI in FP32
+// depends on the sub-cycle's start state only); xh32: x_HI in FP32; dt32:
+// dtau in FP32
 template <int G, bool DEFER, bool N32, typename FT>
 __device__ __forceinline__ void chem_trial_fast(const Phys &ph, const BoxDev &B, const CellK<G> &k,
                                                 double n0, const double *S, const Rates &r,
                                                 double alpha, const Cell<G> &s, double e0,
                                                 double dtau, Cell<G> &o, double &e1, FT *rdo,
-                                                float rec32, float xh32)
+                                                float rec32, float xh32, float dt32)
 {
     const double x = 1.0 - s.xHI;
     if constexpr (N32) {
-        const float dt32 = d2f(dtau);
         const float q32 = (xh32 * k.n0f) * dt32;
 #pragma unroll
         for (int i = 0; i < G; i++) {
@@ -2051,11 +2056,14 @@ __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
 // its exact double.  Every float <-> double conversion costs FP64-pipe
 // issue slots (its rare-case instruction is issued, predicated, with the
 // warp), so values that arrive in FP32 are not converted back and forth.
+// span32 (fast forms): span in FP32 (negative: unknown, the pre-test then
+// never decides and the FP64 test does).
 template <int G, bool STRICT, class Trace = NoTrace, typename FT = double>
 __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,
                                   int &ncyc, Trace *tr = nullptr, FT *fac = nullptr,
-                                  bool warm_cut = false, const float *in32 = nullptr)
+                                  bool warm_cut = false, const float *in32 = nullptr,
+                                  float span32 = -1.0f)
 {
     constexpr bool DEFER = !STRICT && std::is_same<Trace, NoTrace>::value;
     constexpr bool N32 = DEFER && std::is_same<FT, float>::value;
@@ -2077,11 +2085,15 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         k.n0f = d2f(n0);
     }
     double rem = span;                          // span - tau, tau = 0 in the first sub-cycle
+    float rem32 = span32;                       // rem in FP32 (fast forms)
     for (;;) {
         const Rates r = tab ? rates_tab<STRICT>(ph, tab, s.T, !STRICT && warm_cut, N32 && !ph.ots)
                             : rates_at(ph, s.T);
         const double alpha = ph.ots ? r.aB : r.aA;
         double dtau = rem;
+        // dtau in FP32 (the FP32 photon update): rem32, halved exactly with
+        // dtau (both stay far above FP32's normal range)
+        float dt32 = rem32;
         bool last = true;
         // e^p (the fast forms reuse it in every trial of this sub-cycle)
         const double ep0 = STRICT ? 0.0 : fma(-k.cvn, s.xHI, k.cvn2) * s.T;
@@ -2104,9 +2116,9 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
 #pragma unroll
             for (int i = 0; i < G; i++) hsum = fmaf(ph.hK[i], fabsf(N32 ? s.n32[i] : d2f(s.N[i])), hsum);
             constexpr float KB15I = (float)(1.0 / (1.5 * rtd::KB));
-            const float kr = fabsf(d2f(r.kR)) * KB15I, kc = fabsf(d2f(r.kC)) * KB15I;
+            const float kr = fabsf(d2f(r.kR)) * KB15I, kc = fabsf(r.kC32) * KB15I;
             const float cool = (k.n0f * xl) * fmaf(xl, kr, xh * kc);
-            const float q = (d2f(rem) * fmaf(xh * B.nunit_f, hsum, cool)) *
+            const float q = (rem32 * fmaf(xh * B.nunit_f, hsum, cool)) *
                             __frcp_rn((2.0f - xh) * d2f(s.T));
             pre_skip = q >= 0.0f && q <= 0.999f;
         }
@@ -2141,7 +2153,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
                                         (long long)dbits(fabs(e)) >= (long long)dbits(lim));
             if (!skip) {
                 const double est = STRICT ? fabs(e / rate) : fabs(e) * rcp_nr(ar);
-                if (est < rem) { dtau = est; last = false; }
+                if (est < rem) { dtau = est; dt32 = d2f(est); last = false; }
             }
         }
         Cell<G> o;
@@ -2155,7 +2167,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
             } else {
                 ep = ep0;
                 chem_trial_fast<G, DEFER, N32, FT>(ph, B, k, n0, S, r, alpha, s, ep0, dtau, o, e1, rd,
-                                                   rec32, xh32);
+                                                   rec32, xh32, dt32);
             }
             if (ph.isothermal) break;
             const bool finite = STRICT ? isfinite(e1) : finite_bits(e1);
@@ -2168,6 +2180,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
             if (STRICT ? de <= tol : (long long)dbits(de) <= (long long)dbits(tol)) break;
             if (h >= ph.max_halvings) { err |= RTD_ERR_SUBCYCLE; break; }
             dtau = 0.5 * dtau;
+            dt32 = 0.5f * dt32;
             last = false;
         }
         if (tr) tr->push(s, dtau);
@@ -2180,6 +2193,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         if (last) break;
         tau = tau + dtau;
         rem = span - tau;
+        rem32 = d2f(rem);
         if (ncyc >= RTD_MAXCYC) { err |= RTD_ERR_SUBCYCLE; break; }
     }
     return err;
@@ -2559,15 +2573,17 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             }
             // the warm cut holds for every sub-cycle when n0 times the whole
             // step is within its bound (in FP32; an overflow to Inf fails)
-            const bool warm_cut = !STRICT && (N32 ? in32[0] : d2f(n0c)) * d2f(span) <= RTD_TAB_NDMAX;
+            const float span32 = STRICT ? 0.0f : d2f(span);
+            const bool warm_cut = !STRICT && (N32 ? in32[0] : d2f(n0c)) * span32 <= RTD_TAB_NDMAX;
             if (ph.nsub > 0) {
                 const double h = span / ph.nsub;
+                const float h32 = STRICT ? 0.0f : d2f(h);
                 for (int k = 0; k < ph.nsub; k++)
                     err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
-                                                             warm_cut, in32);
+                                                             warm_cut, in32, h32);
             } else {
                 err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
-                                                         warm_cut, in32);
+                                                         warm_cut, in32, span32);
             }
             if (ph.cosmo) {
                 cosmo_out<G, STRICT>(ca, ca1, s);
@@ -2781,15 +2797,17 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
             cosmo_in<G, STRICT>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
             if constexpr (N32) cosmo_32<G>(s, S, n0c, in32);
         }
-        const bool warm_cut = !STRICT && (N32 ? in32[0] : d2f(n0c)) * d2f(span) <= RTD_TAB_NDMAX;
+        const float span32 = STRICT ? 0.0f : d2f(span);
+        const bool warm_cut = !STRICT && (N32 ? in32[0] : d2f(n0c)) * span32 <= RTD_TAB_NDMAX;
         if (ph.nsub > 0) {
             const double h = span / ph.nsub;
+            const float h32 = STRICT ? 0.0f : d2f(h);
             for (int q = 0; q < ph.nsub; q++)
                 err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
-                                                         warm_cut, in32);
+                                                         warm_cut, in32, h32);
         } else {
             err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
-                                                     warm_cut, in32);
+                                                     warm_cut, in32, span32);
         }
         if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
         if (!finite_bits(s.xHI) || !finite_bits(s.T)) err |= RTD_ERR_NONFINITE;

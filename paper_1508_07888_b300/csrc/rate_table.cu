@@ -95,7 +95,9 @@ static float eval_aB32(const rtd::RateCoef *a, float t32)
 // polynomial in |t| <= 1: a few ulp of float), when both exp(-c/T) factors
 // are exactly zero in double below RTD_TAB_TCUT, and when the terms they make
 // are below 2^-60 of what they enter below RTD_TAB_TWARM at n0 dtau <=
-// RTD_TAB_NDMAX
+// RTD_TAB_NDMAX.  Entry 3's b32 holds an upper bound of kR over the
+// interval in FP32 (the largest fit value at 257 points, 1e-3 above it,
+// rounded up), checked against the kernel's evaluation at the check points.
 bool build_rate_table(bool ots, rtd::RateCoef *out)
 {
     const int N = RTD_TAB_NC;
@@ -149,6 +151,17 @@ bool build_rate_table(bool ots, rtd::RateCoef *out)
         }
         rtd::RateCoef *a = out + (size_t)j * RTD_TAB_NF;
         for (int i = 0; i < 3; i++) a[i].b32 = (float)aBm[i];
+        LD kmax = 0;
+        for (int k = 0; k <= 256; k++) {
+            const LD v = fit(2, lo + (hi - lo) * k / 256.0L, ots);
+            kmax = v > kmax ? v : kmax;
+        }
+        kmax *= 1.001L;
+        float kb = (float)kmax;
+        if ((LD)kb < kmax) kb = std::nextafterf(kb, INFINITY);
+        a[3].b32 = kb;
+        for (int k = 0; k <= 16; k++)
+            if (!(eval_coef(a[2], -1.0 + k / 8.0, (float)(-1.0 + k / 8.0)) <= (double)kb)) return false;
         for (int k = 0; k <= 16; k++) {
             const double t = -1.0 + k / 8.0;
             const LD ex = fit(1, lo + ((LD)t + 1) * 0.5L * (hi - lo), ots);

@@ -65,7 +65,9 @@ struct RateCoef {
     double c0, c1, c2;
     float c3, c4, c5;
     float b32;      // entries 0, 1, 2 of an interval: c0, c1, c2 of alpha_B's polynomial in
-                    // FP32 (with entry 1's c3 .. c5, alpha_B wholly in FP32); 0 in entries 3, 4
+                    // FP32 (with entry 1's c3 .. c5, alpha_B wholly in FP32); entry 3: an
+                    // upper bound of kR over the interval in FP32 (the fast forms'
+                    // pre-test); 0 in entry 4
 };
 
 // physical constants (cgs)

@@ -1756,6 +1756,7 @@ struct Rates {
     double kC;             // cooling per n_e n_HI: collisional ionisation + excitation
     float aB32;            // alpha_B in FP32 (the split form's recombination photons)
     float kC32;            // kC in FP32 (the fast forms' pre-test), formed where kC is
+    float kR32;            // an upper bound of kR in FP32 (the fast forms' pre-test)
 };
 
 __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
@@ -1766,6 +1767,7 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
         r.kR = 0.0; r.kC = 0.0;
         r.aB32 = d2f(r.aB);
         r.kC32 = 0.0f;
+        r.kR32 = 0.0f;
         return r;
     }
     const double l = 2.0 * rtd::T_HI / T;
@@ -1789,6 +1791,7 @@ __device__ __forceinline__ Rates rates_at(const Phys &ph, double T)
     r.kR = crec + cff;
     r.kC = cci + cce;
     r.kC32 = d2f(r.kC);
+    r.kR32 = d2f(r.kR);
     r.aB32 = d2f(r.aB);
     return r;
 }
@@ -1850,6 +1853,7 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, 
     }
     r.aA = ph.ots ? r.aB : tab_eval(a, t, t32);
     r.kR = tab_eval(a + 2, t, t32);
+    r.kR32 = __ldg(&a[3].b32);                 // bound over the interval (no conversion)
     if (dbits(T) >= (warm ? dbits(RTD_TAB_TWARM) : dbits(RTD_TAB_TCUT))) {   // T >= cut (both positive)
         const double invT = STRICT ? 1.0 / T : rcp_nr(T);
         r.beta = exp(tab_eval(a + 3, t, t32) - rtd::T_HI * invT);
@@ -2105,7 +2109,8 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
         // cooling are >= 0, so |rate| <= heat + cool, and q = rem (heat +
         // cool) / e is a sum of products of non-negative FP32 numbers in which
         // n0 and kB cancel (each a few ulp; an underflowed term is below any
-        // part of q that matters); 1 - x_HI comes from its FP64 value.  q <=
+        // part of q that matters; kR enters as an upper bound over its table
+        // interval, which only raises q); 1 - x_HI comes from its FP64 value.  q <=
         // 0.999 therefore implies |e| >= rem |rate| (1 + 1e-13), the skip the
         // FP64 test below takes, which is then not evaluated: the decisions,
         // and the results, are those of the FP64 test
@@ -2116,7 +2121,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
 #pragma unroll
             for (int i = 0; i < G; i++) hsum = fmaf(ph.hK[i], fabsf(N32 ? s.n32[i] : d2f(s.N[i])), hsum);
             constexpr float KB15I = (float)(1.0 / (1.5 * rtd::KB));
-            const float kr = fabsf(d2f(r.kR)) * KB15I, kc = fabsf(r.kC32) * KB15I;
+            const float kr = fabsf(r.kR32) * KB15I, kc = fabsf(r.kC32) * KB15I;
             const float cool = (k.n0f * xl) * fmaf(xl, kr, xh * kc);
             const float q = (rem32 * fmaf(xh * B.nunit_f, hsum, cool)) *
                             __frcp_rn((2.0f - xh) * d2f(s.T));

@@ -29,7 +29,7 @@ def bound_q(rem, xHI, T, n0, nunit, N, hK, kR, kC):
     for h, n in zip(hK, N):
         hsum = fmaf(F(h), F(abs(n)), hsum)
     kb15i = F(1.0 / (1.5 * KB))
-    kr = F(F(abs(kR)) * kb15i)
+    kr = F(F(abs(kR)) * kb15i)           # kR here: the kernel's FP32 upper bound of kR
     kc = F(F(abs(kC)) * kb15i)
     cool = F(F(F(n0) * xl) * fmaf(xl, kr, F(xh * kc)))
     num = fmaf(F(xh * F(nunit)), hsum, cool)
@@ -79,7 +79,10 @@ def test_pretest_implies_the_fp64_skip():
             if heat > 0 and cool > 0:
                 N = [n * cool / heat * (1.0 + rng.uniform(-1e-9, 1e-9)) for n in N]
                 N = [float(F(n)) for n in N]
-        q = bound_q(rem, xHI, T, n0, nunit, N, hK, kR, kC)
+        # the kernel's kR in the pre-test: an upper bound over its table
+        # interval (up to ~1% above kR, rounded up in FP32)
+        kRb = float(np.nextafter(F(kR * (1.0 + rng.uniform(0.0, 1e-2))), np.float32(np.inf)))
+        q = bound_q(rem, xHI, T, n0, nunit, N, hK, kRb, kC)
         if q >= 0.0 and q <= F(0.999):
             hits += 1
             assert fp64_skips(rem, xHI, T, n0, nunit, N, hN, kR, kC), (k, q)

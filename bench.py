@@ -610,14 +610,18 @@ def peaks():
         return None
 
 
-def chem_flops_per_subcycle(G: int, ots: bool, split: bool = True) -> float:
+def chem_flops_per_subcycle(G: int, ots: bool, split: bool = True, adaptive: bool = True) -> float:
     """Algorithmic FP64 flops of one accepted chemistry sub-cycle (a5-a8 and
     the rate fits), counted from the formulas as written.  The split form
     runs the photon update of each group (1 + c sigma x_HI n0 dtau: 4, (N + S
     dtau)/den: 3, F/den: 3) in FP32, 10 G flops that are not FP64 work, and
     the recombination photons of group 1 ((alpha_A - alpha_B) x^2 n0^2 /
-    nunit: 7 flops, absent with OTS) too.  OTS also drops the alpha_A fit (7)."""
+    nunit: 7 flops, absent with OTS) too.  OTS also drops the alpha_A fit (7).
+    The dtau estimate |e / (H - Lambda)| (4 G + 19) belongs to adaptive
+    sub-cycling only: with a fixed number of sub-cycles there is none."""
     base = 111.0 - (14.0 if ots else (7.0 if split else 0.0))
+    if not adaptive:
+        base -= 19.0 + 4.0 * G
     return (12.0 if split else 22.0) * G + base
 
 
@@ -703,7 +707,8 @@ def config_table():
                                                  "hbm_frac": gbs / hbm}
             c = per.get("chemistry")
             if c and not w.rates_const:
-                fl = chem_flops_per_subcycle(G, w.ots, prec == B.RT_PREC_SPLIT) * cells * mean_sub
+                fl = chem_flops_per_subcycle(G, w.ots, prec == B.RT_PREC_SPLIT,
+                                             adaptive=w.nsub == 0) * cells * mean_sub
                 tf = fl / (c * 1e-3) / 1e12
                 row["chemistry_roofline"] = {"bound": "alu", "achieved": tf, "peak": f64,
                                              "unit": "TFLOP/s", "frac": tf / f64}

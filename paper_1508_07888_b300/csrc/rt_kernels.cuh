@@ -2060,8 +2060,9 @@ __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
 // its exact double.  Every float <-> double conversion costs FP64-pipe
 // issue slots (its rare-case instruction is issued, predicated, with the
 // warp), so values that arrive in FP32 are not converted back and forth.
-// span32 (fast forms): span in FP32 (negative: unknown, the pre-test then
-// never decides and the FP64 test does).
+// span32 (fast forms): span in FP32, required with the FP32 photon update
+// (its dtau); elsewhere a negative value means unknown, and the pre-test
+// then never decides (the FP64 test does).
 template <int G, bool STRICT, class Trace = NoTrace, typename FT = double>
 __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,

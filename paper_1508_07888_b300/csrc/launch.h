@@ -71,6 +71,8 @@ cudaError_t fill_tune_state(void *U, int64_t n, cudaStream_t s);
 
 // rate tables of the chemistry kernel (rate_table.cu); false = unusable
 bool build_rate_table(bool ots, rtd::RateCoef *out);
+// 2^(j/64), j = 0..63, as pairs hi + lo of doubles (the fast forms' exp)
+void build_exp2_table(double2 *out);
 constexpr size_t rate_table_entries() { return (size_t)RTD_TAB_NF * RTD_TAB_NINT; }
 
 // reverse-mode kernels of one FP64 step on a periodic single box (adjoint.cu)

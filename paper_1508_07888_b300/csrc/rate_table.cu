@@ -69,6 +69,18 @@ LD fit(int f, LD T, bool ots)
 
 namespace rtl {
 
+// 2^(j/64) in long double (64-bit significand), split into the double hi
+// nearest to it and the double lo nearest to the rest: hi + lo agrees with
+// 2^(j/64) to about 2^-64 relative
+void build_exp2_table(double2 *out)
+{
+    for (int j = 0; j < 64; j++) {
+        const LD v = exp2l((LD)j / 64.0L);
+        const double hi = (double)v;
+        out[j] = make_double2(hi, (double)(v - (LD)hi));
+    }
+}
+
 static_assert(RTD_TAB_NC == 6, "the coefficient layout holds degree 5: c0 .. c2 double, c3 .. c5 float");
 
 // the kernel's evaluation of one polynomial at t (t32: t in float)

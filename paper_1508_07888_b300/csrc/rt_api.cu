@@ -693,7 +693,14 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 if (!p->rates_const) {
                     std::vector<rtd::RateCoef> tab(rtl::rate_table_entries());
                     if (rtl::build_rate_table(p->ots != 0, tab.data())) {
-                        CU(h, cudaMalloc(&h->d_rtab, sizeof(rtd::RateCoef) * tab.size()));
+                        // the 2^(j/64) table of the fast forms' exp follows the rate table
+                        const size_t tb = sizeof(rtd::RateCoef) * tab.size();
+                        double2 e2[64];
+                        rtl::build_exp2_table(e2);
+                        CU(h, cudaMalloc(&h->d_rtab, tb + sizeof(e2)));
+                        CU(h, cudaMemcpy(reinterpret_cast<char *>(h->d_rtab) + tb, e2, sizeof(e2),
+                                         cudaMemcpyHostToDevice));
+                        h->ph.e2t = reinterpret_cast<const double2 *>(reinterpret_cast<char *>(h->d_rtab) + tb);
                         CU(h, cudaMemcpy(h->d_rtab, tab.data(), sizeof(rtd::RateCoef) * tab.size(),
                                          cudaMemcpyHostToDevice));
                         h->ph.rtab = h->d_rtab;

@@ -88,6 +88,7 @@ struct Phys {
     double lnfit[5];              // ln of the rate-fit scales 0.522, 2.740, 0.354, 0.541, 2.250
     double ln2THI;                // ln(2 T_HI)
     const RateCoef *rtab;         // rate table [RTD_TAB_NINT][RTD_TAB_NF] or null
+    const double2 *e2t;           // 2^(j/64) as pairs (hi, lo), j = 0..63 (the fast forms' exp), or null
     int flux;                     // RTD_FLUX_GLF / RTD_FLUX_HLL
     const float *hll_f;           // HLL wave speeds [RTD_HLL_NF + 1][RTD_HLL_NM + 1], FP32 copy
     const double *hll_d;          // the same in FP64

@@ -121,6 +121,16 @@ __host__ __device__ __forceinline__ float d2f(double d)
     return (float)d;
 }
 
+// any lane of the warp's active ones (host: the lane itself)
+__host__ __device__ __forceinline__ bool vote_any(bool p)
+{
+#ifdef __CUDA_ARCH__
+    return __any_sync(__activemask(), p);
+#else
+    return p;
+#endif
+}
+
 // finite (not NaN or Inf) from the exponent bits, on the integer pipe
 __host__ __device__ __forceinline__ bool finite_bits(double d)
 {
@@ -149,6 +159,44 @@ __device__ __forceinline__ double rcp_nr(double d)
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
     const double e = fma(-d, y, 1.0);
     return fma(y, fma(e, e, e), y);
+}
+
+// exp(x) of the fast forms' chemistry: the table-driven method of P. T. P.
+// Tang (ACM TOMS 15(2), 1989).  With k = round(64 x / ln2), j = k mod 64,
+// m = floor(k / 64) and r = x - k ln2/64 (ln2/64 as the pair L1 + L2,
+// |r| <= ln2/128 + tiny), exp(x) = 2^m 2^(j/64) e^r: 2^(j/64) is the pair
+// hi + lo of e2t[j], e^r - 1 its degree-5 Taylor polynomial (truncation
+// below 4e-17 relative), 2^m added to the exponent field.  Within one ulp
+// of exp(x) (host test over 2e6 arguments against expl).  |x| >= 512 and
+// NaN take the library exp, behind a warp vote so the fast path issues
+// none of its instructions.
+__host__ __device__ __forceinline__ double exp_tab(double x, const double2 *e2t)
+{
+    constexpr double INV = 0x1.71547652b82fep+6;        // 64 / ln2
+    constexpr double SH = 0x1.8p52;                     // round-to-integer shifter
+    constexpr double L1 = 0x1.62e42fefa39efp-7;         // ln2/64 = L1 + L2
+    constexpr double L2 = 0x1.abc9e3b39803fp-62;
+    const double kd = fma(x, INV, SH);
+    const int k = (int)(unsigned)dbits(kd);             // round(64 x / ln2), low word
+    const double kf = kd - SH;
+    double r = fma(-kf, L1, x);
+    r = fma(-kf, L2, r);
+    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = fma(r, q, 1.0 / 6.0);
+    q = fma(r, q, 0.5);
+    const double p = fma(r * r, q, r);                  // e^r - 1
+#ifdef __CUDA_ARCH__
+    const double2 t = __ldg(e2t + (k & 63));
+#else
+    const double2 t = e2t[k & 63];
+#endif
+    const double y = t.x + fma(t.x, p, t.y);            // 2^(j/64) e^r, in [0.99, 2.02)
+    double e = dfrom(dbits(y) + ((unsigned long long)(long long)(k >> 6) << 52));
+    const bool far = (dbits(x) & 0x7fffffffffffffffull) >= 0x4080000000000000ull;   // |x| >= 512, NaN
+    if (vote_any(far)) {
+        if (far) e = exp(x);
+    }
+    return e;
 }
 
 __device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
@@ -1856,8 +1904,10 @@ __device__ __forceinline__ Rates rates_tab(const Phys &ph, const RateCoef *tab, 
     r.kR32 = __ldg(&a[3].b32);                 // bound over the interval (no conversion)
     if (dbits(T) >= (warm ? dbits(RTD_TAB_TWARM) : dbits(RTD_TAB_TCUT))) {   // T >= cut (both positive)
         const double invT = STRICT ? 1.0 / T : rcp_nr(T);
-        r.beta = exp(tab_eval(a + 3, t, t32) - rtd::T_HI * invT);
-        const double cce = exp(tab_eval(a + 4, t, t32) - 118348.0 * invT);
+        const double ab = tab_eval(a + 3, t, t32) - rtd::T_HI * invT;
+        const double ac = tab_eval(a + 4, t, t32) - 118348.0 * invT;
+        r.beta = STRICT ? exp(ab) : exp_tab(ab, ph.e2t);
+        const double cce = STRICT ? exp(ac) : exp_tab(ac, ph.e2t);
         r.kC = rtd::KB * rtd::T_HI * r.beta + cce;
         r.kC32 = d2f(r.kC);
     } else {

@@ -6,7 +6,9 @@
 //   2. d2f (double -> float, round to nearest even) against the conversion,
 //      on exponents around the float range with exact ties, near-ties and
 //      carries into the exponent, in the normal and the subnormal results;
-//   3. the rate table (rate_table.cu) evaluated the kernel's way (interval
+//   3. exp_tab (the fast forms' exp, Tang's table-driven method) against expl
+//      on 2e6 arguments, in ulps of the result, and its 2^(j/64) table;
+//   4. the rate table (rate_table.cu) evaluated the kernel's way (interval
 //      and local variable from T's bits, the polynomial's tail in FP32)
 //      against the rate fits in long double at random temperatures.
 #include <cmath>
@@ -83,6 +85,32 @@ int main()
                 chk(rtk::dfrom(((unsigned long long)s << 63) | (ex << 52) | m));
     printf("d2f: %llu mismatches over %llu doubles\n", bad2, n);
     fails += bad2 != 0;
+
+    {   // the fast forms' exp (Tang's table-driven method) against expl, in ulps of the result
+        double2 e2[64];
+        rtl::build_exp2_table(e2);
+        // 2^(1/64), 2^(32/64), 2^(63/64) as hi + lo (60-digit decimal arithmetic); the
+        // table is built in long double, so its lo parts agree to about 2^-64
+        const double ref[3][2] = {{0x1.02c9a3e778061p+0, -0x1.19083535b085dp-56},
+                                  {0x1.6a09e667f3bcdp+0, -0x1.bdd3413b26456p-54},
+                                  {0x1.fa7c1819e90d8p+0, 0x1.74853f3a5931ep-55}};
+        const int rj[3] = {1, 32, 63};
+        bool tab_ok = e2[0].x == 1.0 && e2[0].y == 0.0;
+        for (int i = 0; i < 3; i++)
+            tab_ok = tab_ok && e2[rj[i]].x == ref[i][0] && std::fabs(e2[rj[i]].y - ref[i][1]) <= std::ldexp(1.0, -62);
+        std::uniform_real_distribution<double> ux(-600.0, 60.0);
+        double worst = 0;
+        for (int k = 0; k < 2000000; k++) {
+            const double x = k < 1000 ? -511.99 + k * 0.5 : ux(g);
+            const double a = rtk::exp_tab(x, e2);
+            const LD ex = expl((LD)x);
+            const double ulp = std::ldexp(1.0, std::ilogb((double)ex) - 52);
+            worst = std::fmax(worst, (double)(fabsl((LD)a - ex) / (LD)ulp));
+        }
+        printf("exp_tab: max error %.3f ulp over 2e6 arguments in [-600, 60]; table %s\n", worst,
+               tab_ok ? "ok" : "WRONG");
+        fails += !(worst <= 1.0 && tab_ok);
+    }
 
     for (int ots = 0; ots < 2; ots++) {
         std::vector<rtd::RateCoef> tab(rtl::rate_table_entries());

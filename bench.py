@@ -877,7 +877,9 @@ def main():
             "fp64_form": fp64, "e2e": e2e, "cpu_baseline": cpu,
             "ensemble": ens, "adjoint": adj, "crta": crta, "hll": hll, "cosmo": cosmo,
             "reion256": r256,
-            "gpu_launches": int(sum(v["launches"] for v in kern.values())),
+            # the profiled transport and chemistry launches, plus the one launch per
+            # rt_step call (one per bench step) that forms the chemistry's per-cell constants
+            "gpu_launches": int(sum(v["launches"] for v in kern.values())) + args.steps,
             "clocks": clk, "final_diag": dict(zip(B.DIAG_NAMES, diag)),
         }
         print(json.dumps(out), flush=True)

@@ -174,6 +174,16 @@ static void chem_g(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ct
     }
 }
 
+cudaError_t cconst_fast(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::CellConst *cc)
+{
+    const int grid = (int)std::min<int64_t>((L.nitems + 7) / 8, 4096);
+    if (fp64)
+        rtk::k_cconst<double><<<grid, 256, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, cc);
+    else
+        rtk::k_cconst<float><<<grid, 256, 0, L.stream>>>(L.boxes, L.nboxes, L.nitems, ph, cc);
+    return cudaGetLastError();
+}
+
 cudaError_t chem_fast(bool fp64, int G, const Launch &L, const rtd::Phys &ph, rtd::Ctl *ctl,
                       const rtd::DiagBuf &db)
 {

@@ -93,5 +93,7 @@ void set_thread_error(const char *msg);
 int transport_occupancy(bool fp64, bool strict, int variant = 0, int flux = RTD_FLUX_GLF, bool tma = false,
                         int gpb = 1);
 int chem_occupancy(bool fp64, bool strict, int G);
+// the fast forms' per-cell chemistry constants from n0 (before the steps of a call)
+cudaError_t cconst_fast(bool fp64, const Launch &L, const rtd::Phys &ph, rtd::CellConst *cc);
 
 }  // namespace rtl

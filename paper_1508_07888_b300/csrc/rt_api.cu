@@ -61,6 +61,7 @@ struct rt_handle {
     rtd::DiagPart *d_gpart = nullptr;        // per-group partials
     unsigned *d_gdone = nullptr;             // per-group item counters
     rtd::RateCoef *d_rtab = nullptr;         // rate table (null: fits evaluated directly)
+    rtd::CellConst *d_cc = nullptr;          // fast forms: per-cell chemistry constants (k_cconst)
     double *d_hll_d = nullptr;               // HLL wave speeds (FP64, FP32 copies)
     float *d_hll_f = nullptr;
     float4 *d_hll_f4 = nullptr;
@@ -143,6 +144,7 @@ static void release(rt_handle *h)
     cudaFree(h->d_fines);
     for (auto q : h->d_fparent) cudaFree(q);
     cudaFree(h->d_rtab);
+    cudaFree(h->d_cc);
     cudaFree(h->d_lastdiag);
     cudaFree(h->d_ctl);
     cudaFreeHost(h->h_ctl);
@@ -531,6 +533,10 @@ static int tune_chem(rt_handle *h, int tune, int dev)
                 CU(h, cudaEventCreate(&e0));
                 CU(h, cudaEventCreate(&e1));
                 const rtd::DiagBuf db{h->d_partials, h->d_lanes, h->d_gpart, h->d_gdone, h->d_done, h->d_lastdiag};
+                {
+                    rtl::Launch Lk{tbox, h->nboxes, h->ncitems, 1, h->s};
+                    CU(h, rtl::cconst_fast(h->fp64, Lk, h->ph, h->d_cc));
+                }
                 float best_ms = 0.f;
                 for (int k = 0; k < kChemCandidates; k++) {
                     int grid, grab;
@@ -683,6 +689,11 @@ extern "C" int rt_create(rt_handle **hout, const rt_params *p, const rt_box *box
                 CU(h, cudaMalloc(&h->d_boxes, sizeof(rtd::BoxDev) * nboxes));
                 CU(h, cudaMemcpy(h->d_boxes, h->bdev.data(), sizeof(rtd::BoxDev) * nboxes,
                                  cudaMemcpyHostToDevice));
+                if (!h->strict) {
+                    CU(h, cudaMalloc(&h->d_cc, sizeof(rtd::CellConst) * citem * RTD_CHEM_LANE_CELLS *
+                                                   RTD_CHEM_ITEM));
+                    h->ph.cc = h->d_cc;
+                }
                 CU(h, cudaMalloc(&h->d_partials, sizeof(rtd::DiagPart) * citem));
                 CU(h, cudaMalloc(&h->d_lanes, sizeof(double) * 2 * RTD_CHEM_ITEM * citem));
                 CU(h, cudaMalloc(&h->d_gpart, sizeof(rtd::DiagPart) * cgroup));
@@ -998,6 +1009,10 @@ static int step_chunk(rt_handle *h, int nsteps, double *hist)
     CU(h, cudaEventRecord(h->ev_in, h->user));
     CU(h, cudaStreamWaitEvent(h->s, h->ev_in, 0));
     CU(h, cudaMemcpyAsync(h->d_ctl, c, sizeof(rtd::Ctl), cudaMemcpyHostToDevice, h->s));
+    if (!h->strict) {                    // the chemistry's per-cell constants from n0, once per call
+        rtl::Launch Lk{h->d_boxes, h->nboxes, h->ncitems, 1, h->s};
+        CU(h, rtl::cconst_fast(h->fp64, Lk, h->ph, h->d_cc));
+    }
     if (h->p.cosmo) {                    // a at the start of every step of this chunk
         const double dt_com = h->bdev[0].dt;
         h->h_acos[0] = h->a_now;
@@ -1142,6 +1157,10 @@ extern "C" int rt_adjoint(rt_handle *h, const void *U0, const double *xHI0, cons
         c->chem_next = 0;
         c->chem_fin = 0;
         CU(h, cudaMemcpyAsync(h->d_ctl, c, sizeof(rtd::Ctl), cudaMemcpyHostToDevice, s));
+        if (!h->strict) {                // the chemistry's per-cell constants from n0
+            rtl::Launch Lk{h->d_boxes, h->nboxes, h->ncitems, 1, s};
+            CU(h, rtl::cconst_fast(h->fp64, Lk, h->ph, h->d_cc));
+        }
         // forward from (U0, xHI0, T0) with a checkpoint every ck steps
         CU(h, cudaMemcpyAsync(D.U, U0, bU, cudaMemcpyDeviceToDevice, s));
         CU(h, cudaMemcpyAsync(D.xHI, xHI0, bS, cudaMemcpyDeviceToDevice, s));

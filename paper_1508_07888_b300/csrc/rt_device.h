@@ -75,6 +75,16 @@ constexpr double KB = 1.380649e-16;         // erg/K
 constexpr double EV = 1.602176634e-12;      // erg
 constexpr double T_HI = 157807.0;           // K, temperature scale of the rate fits
 
+// Per-cell constants of the fast forms' chemistry (n0 is static within an
+// rt_step call): formed once per call by k_cconst, read by k_chem with the
+// cell's other inputs.  n0, n0^2, n0^2 / nunit (0 with OTS), (3/2) kB n0 and
+// 3 kB n0 in FP64, n0^2 / nunit in FP32.  Indexed by work item x 128 + the
+// cell's place in the item.
+struct CellConst {
+    double n0, n02, K, cvn, cvn2;
+    float K32, pad;
+};
+
 // Parameters shared by every box (kernel argument, by value).
 struct Phys {
     int G;
@@ -89,6 +99,7 @@ struct Phys {
     double ln2THI;                // ln(2 T_HI)
     const RateCoef *rtab;         // rate table [RTD_TAB_NINT][RTD_TAB_NF] or null
     const double2 *e2t;           // 2^(j/64) as pairs (hi, lo), j = 0..63 (the fast forms' exp), or null
+    const CellConst *cc;          // per-cell chemistry constants of the fast forms (k_cconst)
     int flux;                     // RTD_FLUX_GLF / RTD_FLUX_HLL
     const float *hll_f;           // HLL wave speeds [RTD_HLL_NF + 1][RTD_HLL_NM + 1], FP32 copy
     const double *hll_d;          // the same in FP64

@@ -23,6 +23,7 @@
 namespace rtk {
 
 using rtd::BoxDev;
+using rtd::CellConst;
 using rtd::Ctl;
 using rtd::DiagBuf;
 using rtd::DiagPart;
@@ -2014,6 +2015,21 @@ struct CellK {
     float K32;          // K in FP32
 };
 
+// the per-cell constants of the fast forms from n0 (k_cconst, supercomoving
+// units, the fine level): the operations chem_span used to form per call
+__device__ __forceinline__ CellConst cell_const(const Phys &ph, const BoxDev &B, double n0)
+{
+    CellConst c;
+    c.n0 = n0;
+    c.n02 = n0 * n0;
+    c.K = ph.ots ? 0.0 : c.n02 * B.inv_nunit;
+    c.cvn = (1.5 * rtd::KB) * n0;
+    c.cvn2 = 2.0 * c.cvn;
+    c.K32 = d2f(c.K);
+    c.pad = 0.0f;
+    return c;
+}
+
 // DEFER: F is not carried through the trial (nothing in the chemistry reads
 // it; it only scales by 1/den), the scale of each group goes to rd[] instead.
 // N32 (split form): the photon update of a5, N <- (N + S dtau)/(1 + c
@@ -2112,20 +2128,26 @@ __device__ __forceinline__ void take(Cell<G> &s, const Cell<G> &o)
 // warp), so values that arrive in FP32 are not converted back and forth.
 // span32 (fast forms): span in FP32, required with the FP32 photon update
 // (its dtau); elsewhere a negative value means unknown, and the pre-test
-// then never decides (the FP64 test does).
+// then never decides (the FP64 test does).  kc (fast forms without a trace,
+// required there): the cell's constants from n0 (cell_const).
 template <int G, bool STRICT, class Trace = NoTrace, typename FT = double>
 __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const BoxDev &B, double n0,
                                   const double *S, Cell<G> &s, double span, bool use_est,
                                   int &ncyc, Trace *tr = nullptr, FT *fac = nullptr,
                                   bool warm_cut = false, const float *in32 = nullptr,
-                                  float span32 = -1.0f)
+                                  float span32 = -1.0f, const CellConst *kc = nullptr)
 {
     constexpr bool DEFER = !STRICT && std::is_same<Trace, NoTrace>::value;
     constexpr bool N32 = DEFER && std::is_same<FT, float>::value;
     unsigned int err = 0;
     double tau = 0.0;
     CellK<G> k;
-    if (!STRICT) {
+    if constexpr (DEFER) {                      // the caller's per-cell constants
+        k.n02 = kc->n02;
+        k.K = kc->K;
+        k.cvn = kc->cvn;
+        k.cvn2 = kc->cvn2;
+    } else if (!STRICT) {
         k.n02 = n0 * n0;
         k.K = ph.ots ? 0.0 : k.n02 * B.inv_nunit;
         k.cvn = (1.5 * rtd::KB) * n0;
@@ -2133,7 +2155,7 @@ __device__ unsigned int chem_span(const Phys &ph, const RateCoef *tab, const Box
     }
     if constexpr (N32) {
         k.n0f = in32[0];
-        k.K32 = d2f(k.K);
+        k.K32 = kc->K32;
 #pragma unroll
         for (int i = 0; i < G; i++) k.S32[i] = in32[1 + i];
     } else if (!STRICT) {
@@ -2449,11 +2471,12 @@ __device__ __forceinline__ void reduce_box(const BoxDev &B, int b, const DiagBuf
 }
 
 // Staged inputs of one row of 32 cells of a chemistry work item (the fast
-// forms): U* of every group, x_HI, T, n0; two rows per warp in dynamic
-// shared memory
+// forms): U* of every group, the cells' constants, x_HI, T, n0; two rows per
+// warp in dynamic shared memory
 template <int G, typename TU, typename TN>
 struct ChemRow {
     V4<TU> U[G][RTD_CHEM_ITEM];
+    CellConst cc[RTD_CHEM_ITEM];
     double xHI[RTD_CHEM_ITEM], T[RTD_CHEM_ITEM];
     TN n0[RTD_CHEM_ITEM];
 };
@@ -2515,6 +2538,14 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 Row &r = wrow[hr & 1];
 #pragma unroll
                 for (int i = 0; i < G; i++) cp_cell(&r.U[i][lane], Us + (int64_t)i * B.ncell + cs);
+                {
+                    const char *cg = reinterpret_cast<const char *>(
+                        ph.cc + it * (RTD_CHEM_LANE_CELLS * RTD_CHEM_ITEM) + hr * RTD_CHEM_ITEM + lane);
+                    char *cd = reinterpret_cast<char *>(&r.cc[lane]);
+                    cp_async16(cd, cg);
+                    cp_async16(cd + 16, cg + 16);
+                    cp_async16(cd + 32, cg + 32);
+                }
                 cp_async8(&r.xHI[lane], B.xHI + cs);
                 cp_async8(&r.T[lane], B.T + cs);
                 if constexpr (sizeof(TN) == 4) cp_async4(&r.n0[lane], reinterpret_cast<const TN *>(B.n0) + cs);
@@ -2588,7 +2619,10 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
             if (nclamp) atomicAdd(&ctl->nclamp, nclamp);
             s.xHI = STAGE ? rw.xHI[lane] : B.xHI[c];
             s.T = STAGE ? rw.T[lane] : B.T[c];
-            const double n0 = STAGE ? to_d(rw.n0[lane]) : ldn(reinterpret_cast<const TN *>(B.n0), c);
+            // fast forms: n0 and its constants as k_cconst formed them
+            const double n0 = STAGE ? rw.cc[lane].n0 : ldn(reinterpret_cast<const TN *>(B.n0), c);
+            CellConst kcv;
+            if constexpr (STAGE) kcv = rw.cc[lane];
             if constexpr (N32) in32[0] = STAGE ? (float)rw.n0[lane] : d2f(n0);
             // source term of this cell: sorted unique cells, binary search
             double S[G];
@@ -2626,6 +2660,7 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 }
                 cosmo_in<G, STRICT>(ca, s, S, n0c, span, B.dt);
                 if constexpr (N32) cosmo_32<G>(s, S, n0c, in32);
+                if constexpr (STAGE) kcv = cell_const(ph, B, n0c);
             }
             // the warm cut holds for every sub-cycle when n0 times the whole
             // step is within its bound (in FP32; an overflow to Inf fails)
@@ -2636,10 +2671,10 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
                 const float h32 = STRICT ? 0.0f : d2f(h);
                 for (int k = 0; k < ph.nsub; k++)
                     err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
-                                                             warm_cut, in32, h32);
+                                                             warm_cut, in32, h32, &kcv);
             } else {
                 err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
-                                                         warm_cut, in32, span32);
+                                                         warm_cut, in32, span32, &kcv);
             }
             if (ph.cosmo) {
                 cosmo_out<G, STRICT>(ca, ca1, s);
@@ -2763,6 +2798,28 @@ k_chem(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, Ct
 
 
 
+// The fast forms' per-cell chemistry constants from the boxes' n0 (once per
+// rt_step call; n0 is static within a call), in the chemistry's item order:
+// one warp per item of RTD_CHEM_LANE_CELLS rows of 32 cells.
+template <typename TN>
+__global__ void __launch_bounds__(256)
+k_cconst(const BoxDev *__restrict__ boxes, int nboxes, int64_t nitems, Phys ph, CellConst *cc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nw) {
+        const BoxDev &B = boxes[find_box(boxes, nboxes, it, true)];
+        const int64_t li = it - B.citem0;
+#pragma unroll
+        for (int r = 0; r < RTD_CHEM_LANE_CELLS; r++) {
+            const int64_t c = (li * RTD_CHEM_LANE_CELLS + r) * RTD_CHEM_ITEM + lane;
+            if (c < B.ncell)
+                cc[it * (RTD_CHEM_LANE_CELLS * RTD_CHEM_ITEM) + r * RTD_CHEM_ITEM + lane] =
+                    cell_const(ph, B, ldn(reinterpret_cast<const TN *>(B.n0), c));
+        }
+    }
+}
+
 // CRTA fine level (Sec. 5): one work item = 32 refined cells of one box, one
 // warp.  Each refined cell takes its parent's post-transport N, F (the field
 // the coarse chemistry used, still in U*) and source term, its own density
@@ -2853,6 +2910,8 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
             cosmo_in<G, STRICT>(ph.acos[ctl->step], s, S, n0c, span, B.dt);
             if constexpr (N32) cosmo_32<G>(s, S, n0c, in32);
         }
+        CellConst kcv;
+        if constexpr (!STRICT) kcv = cell_const(ph, B, n0c);
         const float span32 = STRICT ? 0.0f : d2f(span);
         const bool warm_cut = !STRICT && (N32 ? in32[0] : d2f(n0c)) * span32 <= RTD_TAB_NDMAX;
         if (ph.nsub > 0) {
@@ -2860,10 +2919,10 @@ k_chem_fine(const BoxDev *__restrict__ boxes, const FineDev *__restrict__ fines,
             const float h32 = STRICT ? 0.0f : d2f(h);
             for (int q = 0; q < ph.nsub; q++)
                 err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, h, false, ncyc, nullptr, fac,
-                                                         warm_cut, in32, h32);
+                                                         warm_cut, in32, h32, &kcv);
         } else {
             err |= chem_span<G, STRICT, NoTrace, FT>(ph, tab, B, n0c, S, s, span, true, ncyc, nullptr, fac,
-                                                     warm_cut, in32, span32);
+                                                     warm_cut, in32, span32, &kcv);
         }
         if (ph.cosmo) s.T = s.T * (ph.acos[ctl->step] * ph.acos[ctl->step]);
         if (!finite_bits(s.xHI) || !finite_bits(s.T)) err |= RTD_ERR_NONFINITE;
